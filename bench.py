@@ -1,0 +1,298 @@
+"""Benchmark: cylindrical-FDTD cell-updates per second of one TopOpt iteration
+(forward + adjoint run with all DFTs, focal transform and gradient chain) on
+the wide-zone workload: r in [200, 215] lambda, n = 4000, 300 x 320 x 160
+cells, 3 wavelengths, conic filter + tanh projection (beta = 8), focal
+distance 300 lambda, 20000 time steps per run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Multi-GPU (torchrun, one rank per GPU): each rank
+solves its own zone (independent problems, no collective in the data path):
+weak scaling, value = all ranks' cell-updates / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cyl-FDTD Gcell-upd/s (fwd+adj TopOpt iteration)"
+UNIT = "Gcell-upd/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    return ap.parse_args()
+
+
+def workload(n_steps):
+    from zda_inputs import zone_cfg2
+    return zone_cfg2(n_steps=n_steps)
+
+
+def config(spec, n_steps):
+    return {"workload": "wide zone r=[200,215], n=4000, 300x320x160 cells, 3 wavelengths, "
+                        "forward+adjoint TopOpt iteration",
+            "n_steps_per_run": n_steps, "cells": spec.cells, "runs_per_step": 2,
+            "design_pixels": spec.n_r_design * spec.n_phi,
+            "l2": "no flush: field state 1.5 GB and DFT accumulators 0.36 GB exceed the 129 MB L2"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_sample(n_sample_steps, threads=None):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the same
+    workload: the forward run's time loop with all DFTs on the full grid for
+    n_sample_steps steps (setup included)."""
+    import oracle as O
+    from zda_inputs import rho_for
+    spec = workload(n_sample_steps)
+    rho = rho_for(spec, 2)
+    O.build()
+    t = time.perf_counter()
+    O.forward(spec, rho, nthreads=threads or 0)
+    dt = time.perf_counter() - t
+    cores = threads or os.cpu_count()
+    return {"value": spec.cells * n_sample_steps / dt / 1e9, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": "FP64 oracle forward run, %d time steps of the 300x320x160 grid with the "
+                      "monitor and design-volume DFTs at 6 signed frequencies (%.1f s)" % (n_sample_steps, dt)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec = workload(a.time_steps)
+    for _ in range(a.warmup):
+        oracle_sample(2)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        vals.append(oracle_sample(a.cpu_sample_steps))
+    elapsed = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": config(spec, a.time_steps),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def algorithmic_bytes_e(spec, nq):
+    """Bytes the E-update launch must move per time step: read E and H (6 complex
+    FP32 components), write E (3), the CPML auxiliaries in the slabs (read +
+    write), the design-volume DFT (3 components x nq frequencies, read +
+    write) and the monitor DFT (2 x nq)."""
+    cells = spec.cells
+    plane = spec.n_r * spec.n_phi
+    b = cells * 9 * 8
+    b += 2 * spec.pml_z * plane * 2 * 16                          # E_r, E_phi z-psi
+    b += (spec.pml_r_in + spec.pml_r_out) * spec.n_phi * spec.n_z * 2 * 16   # E_phi, E_z r-psi
+    b += plane * (spec.design_k1 - spec.design_k0 + 1) * 3 * nq * 16
+    b += plane * 2 * nq * 16
+    return b
+
+
+def algorithmic_bytes_h(spec):
+    plane = spec.n_r * spec.n_phi
+    b = spec.cells * 9 * 8
+    b += 2 * spec.pml_z * plane * 2 * 16
+    b += (spec.pml_r_in + spec.pml_r_out) * spec.n_phi * spec.n_z * 2 * 16
+    return b
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2501_07979_gb300 import Zone
+    from zda_inputs import rho_for
+
+    spec = workload(a.time_steps)
+    zone = Zone(spec, device=local)
+    rho = torch.tensor(rho_for(spec, 2 + rank), dtype=torch.float32, device="cuda:%d" % local)
+    rho_host = rho.cpu().pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(a.warmup):
+        zone.iteration(rho)
+    barrier()
+    zone.set_timing(50)
+    launches0 = zone.launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    I = None
+    for _ in range(a.steps):
+        I, g = zone.iteration(rho)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = zone.launches - launches0
+    ms = e0.elapsed_time(e1) / a.steps
+    h_ms, e_ms, n_timed = zone.timing()
+    zone.set_timing(0)
+    t = torch.tensor([ms], dtype=torch.float64, device=rho.device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    updates = 2.0 * spec.n_steps * spec.cells            # forward + adjoint run
+    value = updates * world / (ms_max * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    barrier()
+    te = time.perf_counter()
+    n_e2e = max(1, min(a.steps, 2))
+    for _ in range(n_e2e):
+        I_h, g_h = zone.iteration(rho_host, host=True)
+    barrier()
+    e2e_s = (time.perf_counter() - te) / n_e2e
+    te_t = torch.tensor([e2e_s], dtype=torch.float64, device=rho.device)
+    if dist is not None:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    nq = zone.n_freq
+    px = spec.n_r_design * spec.n_phi * 4
+    e2e = {"value": updates * world / float(te_t.item()) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": px + nq * 16,
+           "d2h_bytes_per_step": px + nq * 16 + 4}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    e_avg_ms = e_ms / max(n_timed, 1)
+    h_avg_ms = h_ms / max(n_timed, 1)
+    be, bh = algorithmic_bytes_e(spec, nq), algorithmic_bytes_h(spec)
+    ach_e = be / (e_avg_ms * 1e-3) / 1e9
+    ach_h = bh / (h_avg_ms * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get("k_update_e")
+        except ValueError:
+            traffic = None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(spec, spec.n_steps),
+            "roofline": {"bound": "hbm", "kernel": "k_update_e", "achieved": ach_e, "peak": peak,
+                         "unit": "GB/s", "frac": ach_e / peak, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": be, "avg_launch_ms": e_avg_ms,
+                         "sampled_launches": n_timed,
+                         "h_update": {"achieved": ach_h, "frac": ach_h / peak, "avg_launch_ms": h_avg_ms,
+                                      "algorithmic_bytes_per_launch": bh}},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "focal_intensity": I}
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(a.cpu_sample_steps)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

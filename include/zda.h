@@ -1,0 +1,201 @@
+/*
+ * zda.h -- C ABI of libzda: the GPU zone solver of the zoned discrete
+ * axisymmetry (ZDA) metalens method (arXiv 2501.07979).
+ *
+ * One call family per step of the method:
+ *   zone geometry ............ section "Zoned discrete axisymmetry (ZDA)",
+ *                              Eqs. 1-2 (n-fold wedge, tau = 2 pi / n)
+ *   Yee time loop ............ section "Differentiable FDTD in cylindrical
+ *                              coordinates", Eqs. 3-5 (Bloch-reduced curl,
+ *                              stretched-coordinate PMLs in r and z)
+ *   density -> permittivity .. Eq. 6 plus the conic and binarisation filters
+ *                              ("Results and Discussion")
+ *   focal intensity .......... "Results and Discussion" (focal-spot far-field
+ *                              intensity of a normally incident plane wave,
+ *                              m = +-1) and Eq. 9's focal intensity I
+ *   adjoint gradient ......... section "Differentiable FDTD": hybrid
+ *                              time/frequency adjoint, all frequencies from
+ *                              one forward and one adjoint run
+ *
+ * Units: c = eps0 = mu0 = 1 and lambda0 = 1 (lengths in lambda0, times in
+ * lambda0 / c).
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are device pointers (e.g. from torch tensors) on
+ *    the zone's device; pointers named *_host (or documented as host) are
+ *    host memory.  The caller owns all memory it passes; the library never
+ *    frees or retains caller memory past the call, except the workspace
+ *    bound with zda_zone_bind_workspace, which it uses until the zone is
+ *    destroyed or another workspace is bound.
+ *  - The library allocates no device memory of its own.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *    is enqueued on it.  Calls that return host results (zda_forward's
+ *    focal_out, zda_iteration's outputs) synchronise that stream before
+ *    returning; others return once the work is enqueued.
+ *  - Every call returns a zda_status; nothing aborts, traps or exits.  On
+ *    error, zda_last_error() returns a message for the calling thread.
+ *  - Complex arrays are interleaved (re, im) floats or doubles.
+ *  - A zone object is not thread-safe; calls on one zone must not overlap.
+ */
+#ifndef ZDA_H
+#define ZDA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZDA_OK = 0,
+    ZDA_ERR_ARG = -1,        /* invalid argument or descriptor */
+    ZDA_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    ZDA_ERR_OOM = -3,        /* workspace too small / host allocation failed */
+    ZDA_ERR_TIMEOUT = -4,    /* a bounded device-side wait gave up */
+    ZDA_ERR_NONFINITE = -5,  /* NaN or Inf in the focal phasors (solver blew up) */
+    ZDA_ERR_STATE = -6       /* call out of order (e.g. adjoint before forward) */
+} zda_status;
+
+#define ZDA_MAX_LAYERS 8
+#define ZDA_MAX_FREQ 16      /* signed frequencies = 2 x wavelengths */
+
+typedef struct zda_ctx zda_ctx;
+typedef struct zda_zone zda_zone;
+
+/* Zone descriptor (plain data, copied at zda_zone_create).
+ * The simulated domain is r in [r_lo, r_lo + n_r dr], one wedge
+ * phi in [0, 2 pi / n_fold) with n_phi cells (Bloch-periodic with phase
+ * e^{i m 2pi/n_fold}), z in [0, n_z dz].  pml_* cells of CPML line the r and
+ * z ends (PEC behind them).  The design / monitor annulus is
+ * r in [r_lo + pml_r_in dr, r_lo + (n_r - pml_r_out) dr].
+ * Layer l (permittivity layer_eps[l]) covers z-cells k >= layer_k0[l] up to
+ * the next layer's start; z-cells [design_k0, design_k1) are the design layer
+ * with eps = eps_lo + rho~ (eps_hi - eps_lo) over the design annulus (Eq. 6)
+ * and eps_lo inside the r-PMLs.  The plane-wave source sheet sits on the
+ * E_r/E_phi plane source_k, the monitor on plane monitor_k (both above the
+ * z-PML).  dt = courant / sqrt(1/dr^2 + 1/(r_lo dphi)^2 + 1/dz^2).
+ * filter_radius <= 0 disables the conic filter, beta <= 0 the projection.
+ * focal is the focal distance above the top of the design layer. */
+typedef struct {
+    double r_lo, dr, dz;
+    int n_r, n_phi, n_z;
+    int n_fold, m;
+    int pml_r_in, pml_r_out, pml_z;
+    int n_layers;
+    int layer_k0[ZDA_MAX_LAYERS];
+    double layer_eps[ZDA_MAX_LAYERS];
+    int design_k0, design_k1;
+    double eps_lo, eps_hi;
+    int source_k, monitor_k;
+    double courant;
+    int n_steps;
+    double filter_radius, beta, eta;
+    double focal;
+} zda_zone_desc;
+
+/* Derived sizes and layouts, filled by zda_zone_query. */
+typedef struct {
+    double dt, dphi, tau;
+    int n_freq;            /* 2 x wavelengths: +w_0..+w_{L-1}, -w_0..-w_{L-1} */
+    int n_r_design;        /* n_r - pml_r_in - pml_r_out */
+    int design_nk;         /* design_k1 - design_k0 + 1 E planes in the DFT box */
+    size_t workspace_bytes;
+    long long cells;       /* n_r n_phi n_z */
+} zda_zone_info;
+
+/* Library context bound to one CUDA device (cudaSetDevice is called by the
+ * library on entry to every call that takes a ctx or zone). */
+zda_status zda_ctx_create(zda_ctx **out, int device);
+void zda_ctx_destroy(zda_ctx *ctx);
+
+/* Create a zone (validates the descriptor, computes the FP64 host tables of
+ * the geometry).  Wavelengths default to {1.0}; pulse to f0 = 1,
+ * sigma_t = 0.5, t0 = 2. */
+zda_status zda_zone_create(zda_ctx *ctx, const zda_zone_desc *desc, zda_zone **out);
+void zda_zone_destroy(zda_zone *zone);
+
+/* Design wavelengths (lambda0 units), 1 <= n_lambda <= ZDA_MAX_FREQ/2.  The
+ * signed frequency list is +2pi/lambda_l then -2pi/lambda_l (the m = +1 run
+ * carries the m = -1 field as its conjugate at -w). */
+zda_status zda_set_wavelengths(zda_zone *zone, const double *lambda_host, int n_lambda);
+
+/* Source pulse g(t) = cos(2 pi f0 (t - t0)) exp(-(t - t0)^2 / (2 sigma_t^2)). */
+zda_status zda_set_pulse(zda_zone *zone, double f0, double sigma_t, double t0);
+
+/* Sizes / layouts (workspace_bytes depends on wavelengths and n_steps). */
+zda_status zda_zone_query(const zda_zone *zone, zda_zone_info *info);
+zda_status zda_zone_workspace_bytes(const zda_zone *zone, size_t *bytes);
+
+/* Bind caller-allocated device memory (>= workspace_bytes, 256-byte aligned)
+ * as the zone's workspace: fields, CPML auxiliaries, DFT accumulators and
+ * tables.  Re-bind after changing wavelengths or n_steps. */
+zda_status zda_zone_bind_workspace(zda_zone *zone, void *workspace_dev, size_t bytes);
+
+/* Forward solve (one FDTD run): rho_dev [n_r_design][n_phi] floats in [0,1]
+ * at the (r, phi) design-pixel centres -> conic filter -> projection ->
+ * Eq. 6 eps -> n_steps Yee steps with the m = +1 plane-wave source and
+ * running DFTs (monitor plane and design volume) -> on-axis focal phasors.
+ * focal_out_host: n_freq complex doubles S_q (interleaved), q in the signed
+ * frequency order; the focal intensity is I = 2 sum_q |S_q|^2.  Keeps the
+ * forward DFTs in the workspace for zda_adjoint. */
+zda_status zda_forward(zda_zone *zone, const float *rho_dev, double *focal_out_host, void *stream);
+
+/* Adjoint run (second FDTD run) and gradient: dI_dfocal_host holds n_freq
+ * complex doubles (dI/dRe S_q, dI/dIm S_q) for any real objective I(S);
+ * grad_rho_dev [n_r_design][n_phi] floats receives dI/drho.  Requires a
+ * preceding zda_forward with the same rho (ZDA_ERR_STATE otherwise). */
+zda_status zda_adjoint(zda_zone *zone, const double *dI_dfocal_host, float *grad_rho_dev, void *stream);
+
+/* One TopOpt iteration of the summed focal intensity I = 2 sum |S_q|^2:
+ * forward, dI/dS = 4 S, adjoint.  host_buffers != 0: rho and grad_rho are
+ * HOST pointers and the call copies them to / from the workspace on
+ * `stream`; otherwise they are device pointers.  I_out_host: 1 double. */
+zda_status zda_iteration(zda_zone *zone, const float *rho, double *I_out_host, float *grad_rho,
+                         int host_buffers, void *stream);
+
+/* Step-level entry points (each step of the path on its own). */
+
+/* Conic filter + tanh projection: rho_dev -> rho_tilde_dev (both
+ * [n_r_design][n_phi]). */
+zda_status zda_filter_project(zda_zone *zone, const float *rho_dev, float *rho_tilde_dev, void *stream);
+
+/* Transposed chain: given rho_dev (the forward input) and g_tilde_dev =
+ * dI/drho~, write dI/drho = F^T (P'(F rho) g_tilde) to grad_rho_dev. */
+zda_status zda_filter_project_backward(zda_zone *zone, const float *rho_dev, const float *g_tilde_dev,
+                                       float *grad_rho_dev, void *stream);
+
+/* On-axis near-to-far transform of a monitor-plane DFT given by the caller:
+ * monitor_dft_dev complex floats [n_freq][2][n_r][n_phi] (E_r, E_phi sites)
+ * -> focal_out_host n_freq complex doubles (synchronises the stream). */
+zda_status zda_focal_transform(zda_zone *zone, const float *monitor_dft_dev, double *focal_out_host,
+                               void *stream);
+
+/* Copies of internal state after zda_forward / zda_adjoint (complex floats):
+ *   zda_copy_fields:  [6][n_r][n_phi][n_z]  E_r, E_phi, E_z, H_r, H_phi, H_z
+ *   zda_copy_monitor_dft: [n_freq][2][n_r][n_phi]
+ *   zda_copy_design_dft:  [n_freq][3][n_r][n_phi][design_nk]; which = 0
+ *                         forward run, 1 adjoint run. */
+zda_status zda_copy_fields(zda_zone *zone, float *out_dev, void *stream);
+zda_status zda_copy_monitor_dft(zda_zone *zone, float *out_dev, void *stream);
+zda_status zda_copy_design_dft(zda_zone *zone, int which, float *out_dev, void *stream);
+
+/* Number of kernel launches the library issued since the zone was created
+ * (for launch accounting in benchmarks). */
+long long zda_zone_launch_count(const zda_zone *zone);
+
+/* Kernel timing with CUDA events recorded on the launching stream: with
+ * every > 0, every every-th time step's H-update and E-update launches are
+ * bracketed by events (a ring of 64 samples; the host waits for a sample
+ * 64 samples old before reusing its slot).  every = 0 turns it off.
+ * zda_zone_timing waits for pending samples and returns the summed
+ * durations (ms) and the number of sampled launch pairs, then resets. */
+zda_status zda_zone_set_timing(zda_zone *zone, int every);
+zda_status zda_zone_timing(zda_zone *zone, double *h_ms_host, double *e_ms_host, long long *count_host);
+
+/* Thread-local message of the last error ("" if none). */
+const char *zda_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZDA_H */

@@ -1,0 +1,840 @@
+// Host side of the libzda C ABI (declared in include/zda.h).
+//
+// The library computes its coefficient tables in FP64 on the host (radii,
+// CPML profiles, layer permittivities, source phases, pulse samples, DFT
+// twiddles e^{i w t} dt, the broadband adjoint pulse matrix, the
+// Rayleigh-Sommerfeld radial weights) and uploads them into the caller's
+// workspace; every per-cell and per-step operation runs in the kernels of
+// zda_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "zda.h"
+#include "zda_internal.h"
+
+using cd = std::complex<double>;
+
+static thread_local std::string g_err;
+
+static zda_status fail(zda_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ZDA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+struct zda_ctx {
+    int device;
+};
+
+namespace {
+
+struct Layout {           // byte offsets inside the workspace
+    size_t fields, psi_z, psi_r, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
+        norm, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
+        ph_h, pulse, twiddle, adj_time, Gr, Gp, emph_n, emph_h, wt, beta_r, beta_p, g_in, partial, S,
+        status, total;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct zda_zone {
+    zda_ctx *ctx = nullptr;
+    zda_zone_desc d{};
+    double dt = 0, dphi = 0, tau = 0;
+    int nq = 2, nrd = 0, nk = 0, i_d0 = 0, i_d1 = 0, di_max = 0, dj_max = 0;
+    std::vector<double> lambda{1.0};
+    double f0 = 1.0, sigma = 0.5, t0 = 2.0;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L{};
+    bool tables_dirty = true;
+    bool have_forward = false;
+    bool adjoint_ok = false;        // the broadband adjoint pulse matrix was invertible
+    long long launches = 0;
+    // optional CUDA-event timing of every `time_every`-th H/E launch pair
+    int time_every = 0;
+    std::vector<cudaEvent_t> ev;    // ring of (before H, between, after E) triples
+    std::vector<char> ev_pending;
+    int ev_next = 0;
+    double t_h_ms = 0, t_e_ms = 0;
+    long long t_count = 0;
+    ~zda_zone();
+};
+
+static void timing_drain_slot(zda_zone &z, int slot)
+{
+    if (!z.ev_pending[slot]) return;
+    cudaEventSynchronize(z.ev[3 * slot + 2]);
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, z.ev[3 * slot], z.ev[3 * slot + 1]);
+    cudaEventElapsedTime(&b, z.ev[3 * slot + 1], z.ev[3 * slot + 2]);
+    z.t_h_ms += a;
+    z.t_e_ms += b;
+    z.t_count++;
+    z.ev_pending[slot] = 0;
+}
+
+static void timing_release(zda_zone &z)
+{
+    for (size_t s = 0; s < z.ev_pending.size(); ++s) timing_drain_slot(z, (int)s);
+    for (cudaEvent_t e : z.ev) cudaEventDestroy(e);
+    z.ev.clear();
+    z.ev_pending.clear();
+    z.time_every = 0;
+}
+
+zda_zone::~zda_zone() { timing_release(*this); }
+
+// ------------------------------------------------------------------ tables
+static double layer_eps_at(const zda_zone_desc &d, int k)
+{
+    double e = d.layer_eps[0];
+    for (int l = 0; l < d.n_layers; ++l)
+        if (k >= d.layer_k0[l]) e = d.layer_eps[l];
+    return e;
+}
+
+// Convolutional PML (kappa = 1): sigma = sigma_max x^3 with
+// sigma_max = -4 ln(1e-8) / (2 d), alpha = 0.05 (2 pi f0) (1 - x);
+// b = exp(-(sigma + alpha) dt), c = sigma / (sigma + alpha) (b - 1);
+// x = depth into the PML / its thickness.
+static void cpml_table(const zda_zone &z, double lo, double hi, int n_in, int n_out, double h,
+                       const std::vector<double> &pos, std::vector<float> &b, std::vector<float> &c)
+{
+    const double a_max = 0.05 * 2.0 * M_PI * z.f0;
+    b.assign(pos.size(), 0.f);
+    c.assign(pos.size(), 0.f);
+    for (size_t t = 0; t < pos.size(); ++t) {
+        const double x0 = pos[t];
+        double x = 0.0, thick = h;
+        if (n_in > 0 && x0 < lo + n_in * h) { thick = n_in * h; x = (lo + thick - x0) / thick; }
+        if (n_out > 0 && x0 > hi - n_out * h) { thick = n_out * h; x = (x0 - (hi - thick)) / thick; }
+        x = std::min(std::max(x, 0.0), 1.0);
+        if (x <= 0.0) continue;
+        const double smax = -4.0 * std::log(1e-8) / (2.0 * thick);
+        const double sg = smax * x * x * x, al = a_max * (1.0 - x);
+        const double bb = std::exp(-(sg + al) * z.dt);
+        b[t] = (float)bb;
+        c[t] = (float)(sg / (sg + al) * (bb - 1.0));
+    }
+}
+
+// Complex Gauss-Jordan inverse with partial pivoting (n <= ZDA_MAX_FREQ).
+static bool invert(std::vector<cd> &A, int n, double tiny)
+{
+    std::vector<cd> inv(n * n, 0.0);
+    for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::abs(A[r * n + col]) > std::abs(A[piv * n + col])) piv = r;
+        if (std::abs(A[piv * n + col]) <= tiny) return false;
+        for (int t = 0; t < n; ++t) {
+            std::swap(A[col * n + t], A[piv * n + t]);
+            std::swap(inv[col * n + t], inv[piv * n + t]);
+        }
+        const cd p = A[col * n + col];
+        for (int t = 0; t < n; ++t) { A[col * n + t] /= p; inv[col * n + t] /= p; }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const cd f = A[r * n + col];
+            if (f == 0.0) continue;
+            for (int t = 0; t < n; ++t) {
+                A[r * n + t] -= f * A[col * n + t];
+                inv[r * n + t] -= f * inv[col * n + t];
+            }
+        }
+    }
+    A = inv;
+    return true;
+}
+
+static double omega_q(const zda_zone &z, int q)
+{
+    const int nl = (int)z.lambda.size();
+    const double w = 2.0 * M_PI / z.lambda[q % nl];
+    return q < nl ? w : -w;
+}
+
+static void compute_layout(zda_zone &z)
+{
+    const zda_zone_desc &d = z.d;
+    const size_t nr = d.n_r, np = d.n_phi, nz = d.n_z, Q = z.nq, T = d.n_steps;
+    const size_t ncell = nr * np * nz, plane = nr * np;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
+    Layout &L = z.L;
+    L.fields = take(6 * ncell * sizeof(float2));
+    L.psi_z = take(4 * plane * 2 * d.pml_z * sizeof(float2));
+    L.psi_r = take(4 * (size_t)(d.pml_r_in + d.pml_r_out) * np * nz * sizeof(float2));
+    L.mon = take(Q * 2 * plane * sizeof(float2));
+    L.des_f = take(Q * 3 * plane * z.nk * sizeof(float2));
+    L.des_a = take(Q * 3 * plane * z.nk * sizeof(float2));
+    L.rho_in = take((size_t)z.nrd * np * sizeof(float));
+    L.rho_bar = take((size_t)z.nrd * np * sizeof(float));
+    L.rho_t = take((size_t)z.nrd * np * sizeof(float));
+    L.rb = take(3 * plane * sizeof(float));
+    L.site_grad = take(3 * plane * z.nk * sizeof(float));
+    L.g_t = take((size_t)z.nrd * np * sizeof(float));
+    L.g_rho = take((size_t)z.nrd * np * sizeof(float));
+    L.norm = take((size_t)z.nrd * sizeof(float));
+    L.inv_r_n = take((nr + 1) * sizeof(float));
+    L.inv_r_h = take(nr * sizeof(float));
+    L.br_n = take((nr + 1) * sizeof(float));
+    L.cr_n = take((nr + 1) * sizeof(float));
+    L.br_h = take(nr * sizeof(float));
+    L.cr_h = take(nr * sizeof(float));
+    L.bz_n = take((nz + 1) * sizeof(float));
+    L.cz_n = take((nz + 1) * sizeof(float));
+    L.bz_h = take(nz * sizeof(float));
+    L.cz_h = take(nz * sizeof(float));
+    L.a_n = take(nz * sizeof(float));
+    L.d_n = take(nz * sizeof(float));
+    L.a_c = take(nz * sizeof(float));
+    L.d_c = take(nz * sizeof(float));
+    L.ph_n = take(np * sizeof(float2));
+    L.ph_h = take(np * sizeof(float2));
+    L.pulse = take(T * sizeof(float));
+    L.twiddle = take(T * Q * sizeof(float2));
+    L.adj_time = take(T * Q * sizeof(float2));
+    L.Gr = take(Q * nr * sizeof(double2));
+    L.Gp = take(Q * nr * sizeof(double2));
+    L.emph_n = take(np * sizeof(double2));
+    L.emph_h = take(np * sizeof(double2));
+    L.wt = take(Q * sizeof(float));
+    L.beta_r = take(Q * nr * sizeof(float2));
+    L.beta_p = take(Q * nr * sizeof(float2));
+    L.g_in = take(Q * sizeof(double2));
+    L.partial = take(Q * nr * sizeof(double2));
+    L.S = take(Q * sizeof(double2));
+    L.status = take(sizeof(int) * 4);
+    L.total = off;
+}
+
+template <class T> static T *P(const zda_zone &z, size_t off) { return (T *)(z.ws + off); }
+
+static zda_status upload(zda_zone &z)
+{
+    const zda_zone_desc &d = z.d;
+    const int nr = d.n_r, np = d.n_phi, nz = d.n_z, Q = z.nq, T = d.n_steps;
+    std::vector<float> f;
+    auto put = [&](size_t off, const void *src, size_t bytes) -> cudaError_t {
+        return cudaMemcpy(z.ws + off, src, bytes, cudaMemcpyHostToDevice);
+    };
+    // radii
+    std::vector<float> irn(nr + 1), irh(nr);
+    for (int i = 0; i <= nr; ++i) irn[i] = (float)(1.0 / (d.r_lo + i * d.dr));
+    for (int i = 0; i < nr; ++i) irh[i] = (float)(1.0 / (d.r_lo + (i + 0.5) * d.dr));
+    CUDA_TRY(put(z.L.inv_r_n, irn.data(), irn.size() * 4));
+    CUDA_TRY(put(z.L.inv_r_h, irh.data(), irh.size() * 4));
+    // CPML
+    {
+        std::vector<double> rn(nr + 1), rh(nr), zn(nz + 1), zh(nz);
+        for (int i = 0; i <= nr; ++i) rn[i] = d.r_lo + i * d.dr;
+        for (int i = 0; i < nr; ++i) rh[i] = d.r_lo + (i + 0.5) * d.dr;
+        for (int k = 0; k <= nz; ++k) zn[k] = k * d.dz;
+        for (int k = 0; k < nz; ++k) zh[k] = (k + 0.5) * d.dz;
+        const double rhi = d.r_lo + nr * d.dr, zhi = nz * d.dz;
+        std::vector<float> b, c;
+        cpml_table(z, d.r_lo, rhi, d.pml_r_in, d.pml_r_out, d.dr, rn, b, c);
+        CUDA_TRY(put(z.L.br_n, b.data(), b.size() * 4));
+        CUDA_TRY(put(z.L.cr_n, c.data(), c.size() * 4));
+        cpml_table(z, d.r_lo, rhi, d.pml_r_in, d.pml_r_out, d.dr, rh, b, c);
+        CUDA_TRY(put(z.L.br_h, b.data(), b.size() * 4));
+        CUDA_TRY(put(z.L.cr_h, c.data(), c.size() * 4));
+        cpml_table(z, 0.0, zhi, d.pml_z, d.pml_z, d.dz, zn, b, c);
+        CUDA_TRY(put(z.L.bz_n, b.data(), b.size() * 4));
+        CUDA_TRY(put(z.L.cz_n, c.data(), c.size() * 4));
+        cpml_table(z, 0.0, zhi, d.pml_z, d.pml_z, d.dz, zh, b, c);
+        CUDA_TRY(put(z.L.bz_h, b.data(), b.size() * 4));
+        CUDA_TRY(put(z.L.cz_h, c.data(), c.size() * 4));
+    }
+    // permittivity at node planes (E_r, E_phi: cells k-1, k) and cell planes
+    // (E_z: cell k): eps = a + d * (transverse density average)
+    {
+        const double de = d.eps_hi - d.eps_lo;
+        auto design = [&](int k) { return k >= d.design_k0 && k < d.design_k1; };
+        auto base = [&](int k) { return design(k) ? d.eps_lo : layer_eps_at(d, k); };
+        std::vector<float> an(nz), dn(nz), ac(nz), dc(nz);
+        for (int k = 0; k < nz; ++k) {
+            const int km = std::max(k - 1, 0);
+            an[k] = (float)(0.5 * (base(km) + base(k)));
+            dn[k] = (float)(0.5 * de * ((design(km) ? 1 : 0) + (design(k) ? 1 : 0)));
+            ac[k] = (float)base(k);
+            dc[k] = (float)(design(k) ? de : 0.0);
+        }
+        CUDA_TRY(put(z.L.a_n, an.data(), nz * 4));
+        CUDA_TRY(put(z.L.d_n, dn.data(), nz * 4));
+        CUDA_TRY(put(z.L.a_c, ac.data(), nz * 4));
+        CUDA_TRY(put(z.L.d_c, dc.data(), nz * 4));
+    }
+    // phases
+    {
+        std::vector<float2> pn(np), ph(np);
+        std::vector<double2> en(np), eh(np);
+        for (int j = 0; j < np; ++j) {
+            const double a = d.m * j * z.dphi, b = d.m * (j + 0.5) * z.dphi;
+            pn[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+            ph[j] = make_float2((float)std::cos(b), (float)std::sin(b));
+            en[j] = make_double2(std::cos(j * z.dphi), -std::sin(j * z.dphi));
+            eh[j] = make_double2(std::cos((j + 0.5) * z.dphi), -std::sin((j + 0.5) * z.dphi));
+        }
+        CUDA_TRY(put(z.L.ph_n, pn.data(), np * 8));
+        CUDA_TRY(put(z.L.ph_h, ph.data(), np * 8));
+        CUDA_TRY(put(z.L.emph_n, en.data(), np * 16));
+        CUDA_TRY(put(z.L.emph_h, eh.data(), np * 16));
+    }
+    // pulse, twiddles, adjoint pulse matrix
+    {
+        std::vector<float> pl(T);
+        for (int n = 0; n < T; ++n) {
+            const double u = (n + 0.5) * z.dt - z.t0;
+            pl[n] = (float)(std::cos(2 * M_PI * z.f0 * u) * std::exp(-u * u / (2 * z.sigma * z.sigma)));
+        }
+        CUDA_TRY(put(z.L.pulse, pl.data(), (size_t)T * 4));
+        std::vector<float2> tw((size_t)T * Q);
+        for (int n = 0; n < T; ++n)
+            for (int q = 0; q < Q; ++q) {
+                const cd v = std::exp(cd(0, omega_q(z, q) * (n + 1) * z.dt)) * z.dt;
+                tw[(size_t)n * Q + q] = make_float2((float)v.real(), (float)v.imag());
+            }
+        CUDA_TRY(put(z.L.twiddle, tw.data(), tw.size() * 8));
+        // Broadband adjoint profiles: zero-mean first differences of
+        // e^{+i w_l (t - 6 sigma)} Gaussians (centred at -w_l), combined with
+        // the inverse of their discrete DFT matrix at -w_j so the profile of
+        // column q has DFT delta_qj at -w_j.
+        const double t0a = 6.0 * z.sigma;
+        std::vector<cd> g((size_t)T * Q);
+        for (int l = 0; l < Q; ++l) {
+            auto p = [&](int n) {
+                const double u = n * z.dt - t0a;
+                return std::exp(cd(0, omega_q(z, l) * u)) * std::exp(-u * u / (2 * z.sigma * z.sigma));
+            };
+            cd prev = p(0);
+            for (int n = 0; n < T; ++n) {
+                const cd nx = p(n + 1);
+                g[(size_t)n * Q + l] = nx - prev;
+                prev = nx;
+            }
+        }
+        std::vector<cd> Gm((size_t)Q * Q, 0.0);     // Gm[l][j] = sum_n g_l[n] e^{-i w_j t_{n+1/2}} dt
+        for (int n = 0; n < T; ++n) {
+            const double t = (n + 0.5) * z.dt;
+            for (int jq = 0; jq < Q; ++jq) {
+                const cd e = std::exp(cd(0, -omega_q(z, jq) * t)) * z.dt;
+                for (int l = 0; l < Q; ++l) Gm[(size_t)l * Q + jq] += g[(size_t)n * Q + l] * e;
+            }
+        }
+        double gscale = 0.0;
+        for (const cd &v : Gm) gscale = std::max(gscale, std::abs(v));
+        z.adjoint_ok = gscale > 0 && invert(Gm, Q, 1e-9 * gscale);
+        std::vector<float2> at((size_t)T * Q, make_float2(0.f, 0.f));
+        if (z.adjoint_ok) {
+            for (int n = 0; n < T; ++n)
+                for (int q = 0; q < Q; ++q) {
+                    cd s = 0.0;
+                    for (int l = 0; l < Q; ++l) s += Gm[(size_t)q * Q + l] * g[(size_t)n * Q + l];
+                    at[(size_t)n * Q + q] = make_float2((float)s.real(), (float)s.imag());
+                }
+        }
+        CUDA_TRY(put(z.L.adj_time, at.data(), at.size() * 8));
+    }
+    // Rayleigh-Sommerfeld (first kind) on-axis weights for the m = +1 run:
+    // G(r) = (n/2) K(R) r dphi w_quad, K = (1/2pi)(z/R)(1/R - ik) e^{ikR}/R,
+    // z = f - (z_monitor - z_design_top), k = 2 pi sqrt(eps_monitor) / lambda;
+    // E_r sites: midpoint over the annulus cells, E_phi sites: trapezoid over
+    // its nodes, times -i (S = c+ collects u_r - i u_phi); -w entries conjugate.
+    {
+        const double zf = d.focal - (d.monitor_k * d.dz - d.design_k1 * d.dz);
+        const double ntop = std::sqrt(layer_eps_at(d, d.monitor_k));
+        std::vector<double2> gr((size_t)Q * nr), gp((size_t)Q * nr);
+        std::vector<float> wt(Q);
+        for (int q = 0; q < Q; ++q) {
+            const double kk = 2 * M_PI * ntop / z.lambda[q % z.lambda.size()];
+            auto G = [&](double r) {
+                const double R = std::sqrt(zf * zf + r * r);
+                const cd K = (1.0 / (2 * M_PI)) * (zf / R) * (1.0 / R - cd(0, kk)) * std::exp(cd(0, kk * R)) / R;
+                return 0.5 * d.n_fold * K * r * z.dphi;
+            };
+            const bool neg = q >= (int)z.lambda.size();
+            for (int i = 0; i < nr; ++i) {
+                cd a = 0.0, b = 0.0;
+                if (i >= z.i_d0 && i < z.i_d1) a = G(d.r_lo + (i + 0.5) * d.dr) * d.dr;
+                if (i >= z.i_d0 && i <= z.i_d1) {
+                    const double wq = (i == z.i_d0 || i == z.i_d1) ? 0.5 * d.dr : d.dr;
+                    b = G(d.r_lo + i * d.dr) * wq;
+                }
+                if (neg) { a = std::conj(a); b = std::conj(b); }
+                b *= cd(0, -1);
+                gr[(size_t)q * nr + i] = make_double2(a.real(), a.imag());
+                gp[(size_t)q * nr + i] = make_double2(b.real(), b.imag());
+            }
+            wt[q] = (float)(2.0 * std::sin(omega_q(z, q) * z.dt / 2) / z.dt);
+        }
+        CUDA_TRY(put(z.L.Gr, gr.data(), gr.size() * 16));
+        CUDA_TRY(put(z.L.Gp, gp.data(), gp.size() * 16));
+        CUDA_TRY(put(z.L.wt, wt.data(), Q * 4));
+    }
+    z.tables_dirty = false;
+    return ZDA_OK;
+}
+
+static zda_status derive(zda_zone &z)
+{
+    const zda_zone_desc &d = z.d;
+    if (d.n_r < 2 || d.n_phi < 1 || d.n_z < 2 || d.n_fold < 1 || d.dr <= 0 || d.dz <= 0 || d.r_lo <= 0)
+        return fail(ZDA_ERR_ARG, "annular zone needs n_r>=2, n_phi>=1, n_z>=2, n_fold>=1, dr,dz>0, r_lo>0");
+    if (d.pml_r_in < 0 || d.pml_r_out < 0 || d.pml_z < 0 || d.pml_r_in + d.pml_r_out >= d.n_r ||
+        2 * d.pml_z >= d.n_z)
+        return fail(ZDA_ERR_ARG, "PML widths do not fit the grid");
+    if (d.n_layers < 1 || d.n_layers > ZDA_MAX_LAYERS) return fail(ZDA_ERR_ARG, "n_layers out of range");
+    if (d.design_k0 < 1 || d.design_k1 <= d.design_k0 || d.design_k1 >= d.n_z)
+        return fail(ZDA_ERR_ARG, "design layer must satisfy 1 <= design_k0 < design_k1 < n_z");
+    if (d.source_k < 1 || d.source_k >= d.n_z || d.monitor_k < 1 || d.monitor_k >= d.n_z)
+        return fail(ZDA_ERR_ARG, "source_k / monitor_k outside the grid");
+    if (d.n_steps < 1 || d.courant <= 0 || d.courant > 1) return fail(ZDA_ERR_ARG, "bad n_steps / courant");
+    if (d.eps_lo <= 0 || d.eps_hi <= 0) return fail(ZDA_ERR_ARG, "permittivities must be positive");
+    for (int l = 0; l < d.n_layers; ++l)
+        if (d.layer_eps[l] <= 0) return fail(ZDA_ERR_ARG, "layer permittivities must be positive");
+    z.tau = 2 * M_PI / d.n_fold;
+    z.dphi = z.tau / d.n_phi;
+    z.dt = d.courant / std::sqrt(1.0 / (d.dr * d.dr) + 1.0 / std::pow(d.r_lo * z.dphi, 2) + 1.0 / (d.dz * d.dz));
+    z.nq = 2 * (int)z.lambda.size();
+    z.i_d0 = d.pml_r_in;
+    z.i_d1 = d.n_r - d.pml_r_out;
+    z.nrd = z.i_d1 - z.i_d0;
+    z.nk = d.design_k1 - d.design_k0 + 1;
+    if (d.filter_radius > 0) {
+        z.di_max = (int)std::floor(d.filter_radius / d.dr);
+        const double rc0 = d.r_lo + (z.i_d0 + 0.5) * d.dr;
+        z.dj_max = (int)std::floor(d.filter_radius / (rc0 * z.dphi));
+    } else {
+        z.di_max = z.dj_max = 0;
+    }
+    compute_layout(z);
+    z.tables_dirty = true;
+    z.have_forward = false;
+    return ZDA_OK;
+}
+
+static zda_status ready(zda_zone *z)
+{
+    if (!z) return fail(ZDA_ERR_ARG, "null zone");
+    if (!z->ws) return fail(ZDA_ERR_STATE, "no workspace bound");
+    if (z->ws_bytes < z->L.total) return fail(ZDA_ERR_OOM, "workspace smaller than zda_zone_workspace_bytes");
+    CUDA_TRY(cudaSetDevice(z->ctx->device));
+    if (z->tables_dirty) return upload(*z);
+    return ZDA_OK;
+}
+
+static zda::StepParams step_params(zda_zone &z)
+{
+    using namespace zda;
+    const zda_zone_desc &d = z.d;
+    const size_t ncell = (size_t)d.n_r * d.n_phi * d.n_z;
+    StepParams p{};
+    p.nr = d.n_r; p.nphi = d.n_phi; p.nz = d.n_z;
+    p.pr_in = d.pml_r_in; p.pr_out = d.pml_r_out; p.pz = d.pml_z;
+    p.dt = (float)z.dt;
+    p.inv_dr = (float)(1.0 / d.dr); p.inv_dz = (float)(1.0 / d.dz); p.inv_dphi = (float)(1.0 / z.dphi);
+    const double ph = d.m * z.tau;
+    p.bloch = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    p.bloch_inv = make_float2((float)std::cos(ph), (float)-std::sin(ph));
+    float2 *F = P<float2>(z, z.L.fields);
+    p.f = Fields{F, F + ncell, F + 2 * ncell, F + 3 * ncell, F + 4 * ncell, F + 5 * ncell};
+    const size_t nzs = (size_t)d.n_r * d.n_phi * 2 * d.pml_z;
+    float2 *Z = P<float2>(z, z.L.psi_z);
+    const size_t nrs = (size_t)(d.pml_r_in + d.pml_r_out) * d.n_phi * d.n_z;
+    float2 *R = P<float2>(z, z.L.psi_r);
+    p.psi = Psi{Z, Z + nzs, R, R + nrs, Z + 2 * nzs, Z + 3 * nzs, R + 2 * nrs, R + 3 * nrs};
+    p.t = Tables{P<float>(z, z.L.inv_r_n), P<float>(z, z.L.inv_r_h), P<float>(z, z.L.br_n),
+                 P<float>(z, z.L.cr_n), P<float>(z, z.L.br_h), P<float>(z, z.L.cr_h), P<float>(z, z.L.bz_n),
+                 P<float>(z, z.L.cz_n), P<float>(z, z.L.bz_h), P<float>(z, z.L.cz_h), P<float>(z, z.L.a_n),
+                 P<float>(z, z.L.d_n), P<float>(z, z.L.a_c), P<float>(z, z.L.d_c), P<float2>(z, z.L.ph_n),
+                 P<float2>(z, z.L.ph_h), P<float>(z, z.L.pulse), P<float2>(z, z.L.twiddle),
+                 P<float2>(z, z.L.adj_time)};
+    const size_t plane = (size_t)d.n_r * d.n_phi;
+    float *rb = P<float>(z, z.L.rb);
+    p.rb_r = rb; p.rb_p = rb + plane; p.rb_z = rb + 2 * plane;
+    p.beta_r = P<float2>(z, z.L.beta_r);
+    p.beta_p = P<float2>(z, z.L.beta_p);
+    p.nq = z.nq;
+    p.src_scale = (float)(0.5 / d.dz);
+    p.des_k0 = d.design_k0;
+    p.des_nk = z.nk;
+    return p;
+}
+
+static zda::FilterParams filter_params(const zda_zone &z)
+{
+    zda::FilterParams fp{};
+    const zda_zone_desc &d = z.d;
+    fp.nrd = z.nrd; fp.nphi = d.n_phi; fp.di_max = z.di_max; fp.dj_max = z.dj_max;
+    fp.dr = (float)d.dr; fp.dphi = (float)z.dphi; fp.R = (float)d.filter_radius;
+    fp.r_c0 = (float)(d.r_lo + (z.i_d0 + 0.5) * d.dr);
+    fp.beta = (float)d.beta; fp.eta = (float)d.eta;
+    fp.filter_on = d.filter_radius > 0 ? 1 : 0;
+    return fp;
+}
+
+// rho (device, design grid) -> rho_bar, rho_t, rb_* in the workspace
+static zda_status run_filter(zda_zone &z, const float *rho_dev, cudaStream_t s)
+{
+    const zda::FilterParams fp = filter_params(z);
+    float *norm = P<float>(z, z.L.norm);
+    if (fp.filter_on) { zda::launch_filter_norm(fp, norm, s); z.launches++; }
+    zda::launch_filter_project(fp, rho_dev, norm, P<float>(z, z.L.rho_bar), P<float>(z, z.L.rho_t), s);
+    const size_t plane = (size_t)z.d.n_r * z.d.n_phi;
+    float *rb = P<float>(z, z.L.rb);
+    zda::launch_rho_bar(P<float>(z, z.L.rho_t), z.d.n_r, z.d.n_phi, z.i_d0, z.i_d1, rb, rb + plane,
+                        rb + 2 * plane, s);
+    z.launches += 2;
+    CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
+static zda_status clear_state(zda_zone &z, cudaStream_t s)
+{
+    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields, 0, z.L.psi_r - z.L.fields, s));      // fields, psi_z
+    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.psi_r, 0, z.L.mon - z.L.psi_r, s));          // psi_r
+    return ZDA_OK;
+}
+
+static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
+{
+    const int R = (int)z.ev_pending.size();
+    for (int n = 0; n < z.d.n_steps; ++n) {
+        const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
+        int slot = 0;
+        if (timed) {
+            slot = z.ev_next;
+            z.ev_next = (z.ev_next + 1) % R;
+            timing_drain_slot(z, slot);
+            CUDA_TRY(cudaEventRecord(z.ev[3 * slot], s));
+        }
+        zda::launch_update_h(p, s);
+        if (timed) CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 1], s));
+        zda::launch_update_e(p, n, s);
+        if (timed) {
+            CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 2], s));
+            z.ev_pending[slot] = 1;
+        }
+    }
+    z.launches += 2LL * z.d.n_steps;
+    CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
+static zda_status focal(zda_zone &z, const float2 *mon, double *out_host, cudaStream_t s)
+{
+    int *status = P<int>(z, z.L.status);
+    CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    zda::launch_focal_partial(mon, P<double2>(z, z.L.Gr), P<double2>(z, z.L.Gp), P<double2>(z, z.L.emph_n),
+                              P<double2>(z, z.L.emph_h), z.nq, z.d.n_r, z.d.n_phi, P<double2>(z, z.L.partial), s);
+    zda::launch_focal_sum(P<double2>(z, z.L.partial), z.nq, z.d.n_r, P<double2>(z, z.L.S), status, s);
+    z.launches += 2;
+    CUDA_TRY(cudaGetLastError());
+    int st = 0;
+    CUDA_TRY(cudaMemcpyAsync(out_host, z.ws + z.L.S, z.nq * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) return fail(ZDA_ERR_NONFINITE, "non-finite focal phasor (the time loop diverged)");
+    return ZDA_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *zda_last_error(void) { return g_err.c_str(); }
+
+zda_status zda_ctx_create(zda_ctx **out, int device)
+{
+    if (!out) return fail(ZDA_ERR_ARG, "null out");
+    int n = 0;
+    CUDA_TRY(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(ZDA_ERR_ARG, "device index out of range");
+    CUDA_TRY(cudaSetDevice(device));
+    *out = new zda_ctx{device};
+    return ZDA_OK;
+}
+
+void zda_ctx_destroy(zda_ctx *ctx) { delete ctx; }
+
+zda_status zda_zone_create(zda_ctx *ctx, const zda_zone_desc *desc, zda_zone **out)
+{
+    if (!ctx || !desc || !out) return fail(ZDA_ERR_ARG, "null argument");
+    zda_zone *z = new zda_zone();
+    z->ctx = ctx;
+    z->d = *desc;
+    zda_status st = derive(*z);
+    if (st != ZDA_OK) { delete z; return st; }
+    *out = z;
+    return ZDA_OK;
+}
+
+void zda_zone_destroy(zda_zone *zone) { delete zone; }
+
+zda_status zda_set_wavelengths(zda_zone *z, const double *lambda, int n)
+{
+    if (!z || !lambda || n < 1 || 2 * n > ZDA_MAX_FREQ) return fail(ZDA_ERR_ARG, "bad wavelengths");
+    for (int l = 0; l < n; ++l)
+        if (!(lambda[l] > 0)) return fail(ZDA_ERR_ARG, "wavelengths must be positive");
+    z->lambda.assign(lambda, lambda + n);
+    return derive(*z);
+}
+
+zda_status zda_set_pulse(zda_zone *z, double f0, double sigma_t, double t0)
+{
+    if (!z || !(f0 > 0) || !(sigma_t > 0)) return fail(ZDA_ERR_ARG, "bad pulse");
+    z->f0 = f0; z->sigma = sigma_t; z->t0 = t0;
+    z->tables_dirty = true;
+    z->have_forward = false;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_query(const zda_zone *z, zda_zone_info *info)
+{
+    if (!z || !info) return fail(ZDA_ERR_ARG, "null argument");
+    info->dt = z->dt; info->dphi = z->dphi; info->tau = z->tau;
+    info->n_freq = z->nq; info->n_r_design = z->nrd; info->design_nk = z->nk;
+    info->workspace_bytes = z->L.total;
+    info->cells = (long long)z->d.n_r * z->d.n_phi * z->d.n_z;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_workspace_bytes(const zda_zone *z, size_t *bytes)
+{
+    if (!z || !bytes) return fail(ZDA_ERR_ARG, "null argument");
+    *bytes = z->L.total;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_bind_workspace(zda_zone *z, void *ws, size_t bytes)
+{
+    if (!z || !ws) return fail(ZDA_ERR_ARG, "null argument");
+    if (((uintptr_t)ws) & 255) return fail(ZDA_ERR_ARG, "workspace must be 256-byte aligned");
+    if (bytes < z->L.total) return fail(ZDA_ERR_OOM, "workspace smaller than zda_zone_workspace_bytes");
+    z->ws = (char *)ws;
+    z->ws_bytes = bytes;
+    z->tables_dirty = true;
+    z->have_forward = false;
+    return ZDA_OK;
+}
+
+zda_status zda_filter_project(zda_zone *z, const float *rho, float *rho_t, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!rho || !rho_t) return fail(ZDA_ERR_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    z->have_forward = false;          // the permittivity tables now follow this rho
+    st = run_filter(*z, rho, s);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(rho_t, z->ws + z->L.rho_t, (size_t)z->nrd * z->d.n_phi * 4, cudaMemcpyDeviceToDevice, s));
+    return ZDA_OK;
+}
+
+zda_status zda_filter_project_backward(zda_zone *z, const float *rho, const float *g_t, float *g_rho, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!rho || !g_t || !g_rho) return fail(ZDA_ERR_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    z->have_forward = false;          // the permittivity tables now follow this rho
+    st = run_filter(*z, rho, s);
+    if (st) return st;
+    const zda::FilterParams fp = filter_params(*z);
+    zda::launch_filter_project_backward(fp, P<float>(*z, z->L.rho_bar), P<float>(*z, z->L.norm), g_t, g_rho, s);
+    z->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
+zda_status zda_forward(zda_zone *z, const float *rho, double *focal_out, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!rho || !focal_out) return fail(ZDA_ERR_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    z->have_forward = false;
+    st = run_filter(*z, rho, s);
+    if (st) return st;
+    st = clear_state(*z, s);
+    if (st) return st;
+    const size_t plane = (size_t)z->d.n_r * z->d.n_phi;
+    CUDA_TRY(cudaMemsetAsync(z->ws + z->L.mon, 0, z->nq * 2 * plane * sizeof(float2), s));
+    CUDA_TRY(cudaMemsetAsync(z->ws + z->L.des_f, 0, z->nq * 3 * plane * z->nk * sizeof(float2), s));
+    zda::StepParams p = step_params(*z);
+    p.src_mode = zda::SRC_PLANE_WAVE;
+    p.src_k = z->d.source_k;
+    p.mon_k = z->d.monitor_k;
+    p.mon = P<float2>(*z, z->L.mon);
+    p.des = P<float2>(*z, z->L.des_f);
+    st = time_loop(*z, p, s);
+    if (st) return st;
+    st = focal(*z, P<float2>(*z, z->L.mon), focal_out, s);
+    if (st) return st;
+    z->have_forward = true;
+    return ZDA_OK;
+}
+
+zda_status zda_adjoint(zda_zone *z, const double *dI, float *grad_rho, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!dI || !grad_rho) return fail(ZDA_ERR_ARG, "null pointer");
+    if (!z->have_forward) return fail(ZDA_ERR_STATE, "zda_adjoint needs a preceding zda_forward");
+    if (!z->adjoint_ok)
+        return fail(ZDA_ERR_ARG, "n_steps too short: the broadband adjoint pulses do not fit the run");
+    cudaStream_t s = (cudaStream_t)stream;
+    const zda_zone_desc &d = z->d;
+    const size_t plane = (size_t)d.n_r * d.n_phi;
+    CUDA_TRY(cudaMemcpyAsync(z->ws + z->L.g_in, dI, z->nq * sizeof(double2), cudaMemcpyHostToDevice, s));
+    const double vol = d.dr * z->dphi * d.dz;
+    zda::launch_adjoint_profiles(P<double2>(*z, z->L.g_in), P<double2>(*z, z->L.Gr), P<double2>(*z, z->L.Gp),
+                                 P<float>(*z, z->L.wt), z->nq, d.n_r, d.r_lo, d.dr, vol, P<float2>(*z, z->L.beta_r),
+                                 P<float2>(*z, z->L.beta_p), s);
+    z->launches++;
+    st = clear_state(*z, s);
+    if (st) return st;
+    CUDA_TRY(cudaMemsetAsync(z->ws + z->L.des_a, 0, z->nq * 3 * plane * z->nk * sizeof(float2), s));
+    zda::StepParams p = step_params(*z);
+    p.src_mode = zda::SRC_ADJOINT;
+    p.src_k = d.monitor_k;
+    p.mon_k = -1;
+    p.mon = nullptr;
+    p.des = P<float2>(*z, z->L.des_a);
+    st = time_loop(*z, p, s);
+    if (st) return st;
+    zda::launch_site_gradient(P<float2>(*z, z->L.des_f), P<float2>(*z, z->L.des_a), P<float>(*z, z->L.wt), z->nq,
+                              d.n_r, d.n_phi, z->nk, d.r_lo, d.dr, vol, P<float>(*z, z->L.site_grad), s);
+    zda::launch_cell_gradient(P<float>(*z, z->L.site_grad), d.n_r, d.n_phi, z->nk, z->i_d0, z->nrd,
+                              (float)(d.eps_hi - d.eps_lo), P<float>(*z, z->L.g_t), s);
+    const zda::FilterParams fp = filter_params(*z);
+    zda::launch_filter_project_backward(fp, P<float>(*z, z->L.rho_bar), P<float>(*z, z->L.norm),
+                                        P<float>(*z, z->L.g_t), grad_rho, s);
+    z->launches += 3;
+    CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
+zda_status zda_iteration(zda_zone *z, const float *rho, double *I_out, float *grad_rho, int host_buffers,
+                         void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!rho || !I_out || !grad_rho) return fail(ZDA_ERR_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = (size_t)z->nrd * z->d.n_phi * sizeof(float);
+    const float *rho_dev = rho;
+    float *g_dev = grad_rho;
+    if (host_buffers) {
+        CUDA_TRY(cudaMemcpyAsync(z->ws + z->L.rho_in, rho, nb, cudaMemcpyHostToDevice, s));
+        rho_dev = P<float>(*z, z->L.rho_in);
+        g_dev = P<float>(*z, z->L.g_rho);
+    }
+    std::vector<double> S(2 * z->nq), g(2 * z->nq);
+    st = zda_forward(z, rho_dev, S.data(), stream);
+    if (st) return st;
+    double I = 0;
+    for (int q = 0; q < z->nq; ++q) {
+        I += 2.0 * (S[2 * q] * S[2 * q] + S[2 * q + 1] * S[2 * q + 1]);
+        g[2 * q] = 4.0 * S[2 * q];
+        g[2 * q + 1] = 4.0 * S[2 * q + 1];
+    }
+    st = zda_adjoint(z, g.data(), g_dev, stream);
+    if (st) return st;
+    if (host_buffers) CUDA_TRY(cudaMemcpyAsync(grad_rho, g_dev, nb, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *I_out = I;
+    return ZDA_OK;
+}
+
+zda_status zda_focal_transform(zda_zone *z, const float *mon, double *out, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!mon || !out) return fail(ZDA_ERR_ARG, "null pointer");
+    return focal(*z, (const float2 *)mon, out, (cudaStream_t)stream);
+}
+
+zda_status zda_copy_fields(zda_zone *z, float *out, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!out) return fail(ZDA_ERR_ARG, "null pointer");
+    const size_t n = 6 * (size_t)z->d.n_r * z->d.n_phi * z->d.n_z * sizeof(float2);
+    CUDA_TRY(cudaMemcpyAsync(out, z->ws + z->L.fields, n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return ZDA_OK;
+}
+
+zda_status zda_copy_monitor_dft(zda_zone *z, float *out, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!out) return fail(ZDA_ERR_ARG, "null pointer");
+    const size_t n = (size_t)z->nq * 2 * z->d.n_r * z->d.n_phi * sizeof(float2);
+    CUDA_TRY(cudaMemcpyAsync(out, z->ws + z->L.mon, n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return ZDA_OK;
+}
+
+zda_status zda_copy_design_dft(zda_zone *z, int which, float *out, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!out || (which != 0 && which != 1)) return fail(ZDA_ERR_ARG, "bad argument");
+    const size_t n = (size_t)z->nq * 3 * z->d.n_r * z->d.n_phi * z->nk * sizeof(float2);
+    CUDA_TRY(cudaMemcpyAsync(out, z->ws + (which ? z->L.des_a : z->L.des_f), n, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    return ZDA_OK;
+}
+
+long long zda_zone_launch_count(const zda_zone *z) { return z ? z->launches : -1; }
+
+zda_status zda_zone_set_timing(zda_zone *z, int every)
+{
+    if (!z || every < 0) return fail(ZDA_ERR_ARG, "bad argument");
+    CUDA_TRY(cudaSetDevice(z->ctx->device));
+    timing_release(*z);
+    z->t_h_ms = z->t_e_ms = 0;
+    z->t_count = 0;
+    if (every == 0) return ZDA_OK;
+    const int R = 64;
+    z->ev.resize(3 * R);
+    for (auto &e : z->ev) CUDA_TRY(cudaEventCreate(&e));
+    z->ev_pending.assign(R, 0);
+    z->ev_next = 0;
+    z->time_every = every;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_timing(zda_zone *z, double *h_ms, double *e_ms, long long *count)
+{
+    if (!z || !h_ms || !e_ms || !count) return fail(ZDA_ERR_ARG, "null argument");
+    CUDA_TRY(cudaSetDevice(z->ctx->device));
+    for (size_t s = 0; s < z->ev_pending.size(); ++s) timing_drain_slot(*z, (int)s);
+    *h_ms = z->t_h_ms;
+    *e_ms = z->t_e_ms;
+    *count = z->t_count;
+    z->t_h_ms = z->t_e_ms = 0;
+    z->t_count = 0;
+    return ZDA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the libzda translation units.
+// Device layout (all complex values are float2 = (re, im)):
+//   fields       E_r, E_phi, E_z, H_r, H_phi, H_z: [n_r][n_phi][n_z], z fastest
+//   z-CPML psi   [n_r][n_phi][2 pml_z]        (lower slab, then upper slab)
+//   r-CPML psi   [pml_r_in + pml_r_out][n_phi][n_z]
+//   monitor DFT  [Q][2][n_r][n_phi]
+//   design DFT   [Q][3][n_r][n_phi][nk]      (nk design planes fastest)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace zda {
+
+__host__ __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 c_fma(float2 a, float2 b, float2 acc) {   // acc + a b
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Per-position coefficient tables (device pointers into the workspace).
+struct Tables {
+    const float *inv_r_n, *inv_r_h;            // 1/r_i (n_r+1), 1/r_{i+1/2} (n_r)
+    const float *br_n, *cr_n, *br_h, *cr_h;    // CPML b, c at r nodes / half nodes
+    const float *bz_n, *cz_n, *bz_h, *cz_h;    // CPML b, c at z nodes / half nodes
+    const float *a_n, *d_n, *a_c, *d_c;        // eps = a[k] + d[k] rhobar at node / cell planes
+    const float2 *ph_n, *ph_h;                 // e^{i m phi_j}, e^{i m phi_{j+1/2}}
+    const float *pulse;                        // g(t_{n+1/2})          [T]
+    const float2 *twiddle;                     // e^{i w_q t_{n+1}} dt  [T][Q]
+    const float2 *adj_time;                    // adjoint profiles k_q  [T][Q]
+};
+
+struct Fields { float2 *Er, *Ep, *Ez, *Hr, *Hp, *Hz; };
+struct Psi { float2 *hr_z, *hp_z, *hp_r, *hz_r, *er_z, *ep_z, *ep_r, *ez_r; };
+
+enum { SRC_NONE = 0, SRC_PLANE_WAVE = 1, SRC_ADJOINT = 2 };
+
+struct StepParams {
+    int nr, nphi, nz;
+    int pr_in, pr_out, pz;
+    float dt, inv_dr, inv_dz, inv_dphi;
+    float2 bloch, bloch_inv;                   // e^{+-i m tau}
+    Fields f;
+    Psi psi;
+    Tables t;
+    const float *rb_r, *rb_p, *rb_z;           // transverse density averages [n_r][n_phi]
+    int src_mode, src_k;
+    float src_scale;                           // 1/(2 dz) for the plane wave
+    const float2 *beta_r, *beta_p;             // adjoint radial profiles [Q][n_r]
+    int nq;
+    int mon_k;                                 // < 0: no monitor DFT
+    float2 *mon;
+    int des_k0, des_nk;                        // des_nk == 0: no design DFT
+    float2 *des;
+};
+
+// kernels (zda_kernels.cu)
+void launch_update_h(const StepParams &p, cudaStream_t s);
+void launch_update_e(const StepParams &p, int n, cudaStream_t s);
+
+struct FilterParams {
+    int nrd, nphi, di_max, dj_max;
+    float dr, dphi, R, r_c0;                   // r_c(i) = r_c0 + i dr
+    float beta, eta;                           // beta <= 0: no projection
+    int filter_on;
+};
+void launch_filter_norm(const FilterParams &fp, float *norm, cudaStream_t s);
+void launch_filter_project(const FilterParams &fp, const float *rho, const float *norm, float *rho_bar,
+                           float *rho_t, cudaStream_t s);
+void launch_filter_project_backward(const FilterParams &fp, const float *rho_bar, const float *norm,
+                                    const float *g_t, float *g_rho, cudaStream_t s);
+void launch_rho_bar(const float *rho_t, int nr, int nphi, int i_d0, int i_d1, float *rb_r, float *rb_p,
+                    float *rb_z, cudaStream_t s);
+
+void launch_focal_partial(const float2 *mon, const double2 *Gr, const double2 *Gp, const double2 *emph_n,
+                          const double2 *emph_h, int nq, int nr, int nphi, double2 *partial, cudaStream_t s);
+void launch_focal_sum(const double2 *partial, int nq, int nr, double2 *S, int *status, cudaStream_t s);
+void launch_adjoint_profiles(const double2 *g, const double2 *Gr, const double2 *Gp, const float *wt, int nq,
+                             int nr, double r_lo, double dr, double vol_scale, float2 *beta_r, float2 *beta_p,
+                             cudaStream_t s);
+void launch_site_gradient(const float2 *des_f, const float2 *des_a, const float *wt, int nq, int nr, int nphi,
+                          int nk, double r_lo, double dr, double vol_scale, float *site_grad, cudaStream_t s);
+void launch_cell_gradient(const float *site_grad, int nr, int nphi, int nk, int i_d0, int nrd, float deps,
+                          float *g_t, cudaStream_t s);
+void launch_fill_status_check(const float *x, size_t n, int *status, cudaStream_t s);
+
+}  // namespace zda

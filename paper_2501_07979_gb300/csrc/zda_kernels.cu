@@ -1,0 +1,595 @@
+// CUDA kernels of libzda (sm_103a).
+//
+// Time loop (section "Differentiable FDTD in cylindrical coordinates",
+// Eqs. 3-5): fields are stored in Bloch-periodic form psi = u e^{i m phi},
+// so Eq. 5's im/r terms are plain phi-differences and the wedge wraps with
+// e^{+-i m tau}.  Yee sites: E_r(i+1/2,j,k) E_phi(i,j+1/2,k) E_z(i,j,k+1/2),
+// H_r(i,j+1/2,k+1/2) H_phi(i+1/2,j,k+1/2) H_z(i+1/2,j+1/2,k); PEC behind the
+// CPMLs.  The update kernels map one thread to one Yee cell with lanes along
+// z (coalesced 256-byte rows per component); the j, k neighbours come from
+// L1 and the i neighbours from L2.  CPML auxiliaries live only in the PML
+// slabs; the plane-wave / adjoint sources and the running DFTs are fused
+// into the E update.
+#include "zda_internal.h"
+
+namespace zda {
+
+#define ZDA_BX 32
+#define ZDA_BY 8
+
+__device__ __forceinline__ int zslab(int k, int nz, int pz) {
+    if (k < pz) return k;
+    if (k >= nz - pz) return k - (nz - 2 * pz);
+    return -1;
+}
+__device__ __forceinline__ int rslab(int i, int nr, int pin, int pout) {
+    if (i < pin) return i;
+    if (i >= nr - pout) return i - (nr - pin - pout);
+    return -1;
+}
+
+// ------------------------------------------------------------------ H update
+// H^{n+1/2} = H^{n-1/2} - dt curl E^n  (Eq. 3 with mu = 1)
+__global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_h(const StepParams p)
+{
+    const int k = blockIdx.x * ZDA_BX + threadIdx.x;
+    const int j = blockIdx.y * ZDA_BY + threadIdx.y;
+    const int i = blockIdx.z;
+    if (k >= p.nz || j >= p.nphi) return;
+    const int nz = p.nz, nphi = p.nphi;
+    const size_t sj = (size_t)nz, si = (size_t)nphi * nz;
+    const size_t c = (size_t)i * si + (size_t)j * sj + k;
+    const float2 zero = make_float2(0.f, 0.f);
+
+    const float2 er = p.f.Er[c], ep = p.f.Ep[c], ez = p.f.Ez[c];
+    float2 ez_jp, er_jp;
+    if (j + 1 < nphi) {
+        ez_jp = p.f.Ez[c + sj];
+        er_jp = p.f.Er[c + sj];
+    } else {                                   // wrap: psi(phi + tau) = e^{i m tau} psi(phi)
+        const size_t c0 = c - (size_t)(nphi - 1) * sj;
+        ez_jp = c_mul(p.bloch, p.f.Ez[c0]);
+        er_jp = c_mul(p.bloch, p.f.Er[c0]);
+    }
+    const bool kin = k + 1 < nz, iin = i + 1 < p.nr;
+    const float2 ep_kp = kin ? p.f.Ep[c + 1] : zero;
+    const float2 er_kp = kin ? p.f.Er[c + 1] : zero;
+    const float2 ez_ip = iin ? p.f.Ez[c + si] : zero;
+    const float2 ep_ip = iin ? p.f.Ep[c + si] : zero;
+    const float irn = __ldg(p.t.inv_r_n + i), irh = __ldg(p.t.inv_r_h + i);
+    const int kz = zslab(k, nz, p.pz);
+    const int ir = rslab(i, p.nr, p.pr_in, p.pr_out);
+    const float dt = p.dt;
+
+    // H_r(i, j+1/2, k+1/2): (1/r) dE_z/dphi - dE_phi/dz
+    {
+        const float2 dph = c_scale(c_sub(ez_jp, ez), irn * p.inv_dphi);
+        float2 dz = c_scale(c_sub(ep_kp, ep), p.inv_dz);
+        if (kz >= 0) {
+            const size_t ix = ((size_t)i * nphi + j) * (2 * p.pz) + kz;
+            float2 ps = c_add(c_scale(p.psi.hr_z[ix], __ldg(p.t.bz_h + k)), c_scale(dz, __ldg(p.t.cz_h + k)));
+            p.psi.hr_z[ix] = ps;
+            dz = c_add(dz, ps);
+        }
+        const float2 h = p.f.Hr[c];
+        p.f.Hr[c] = c_sub(h, c_scale(c_sub(dph, dz), dt));
+    }
+    // H_phi(i+1/2, j, k+1/2): dE_r/dz - dE_z/dr
+    {
+        float2 dz = c_scale(c_sub(er_kp, er), p.inv_dz);
+        float2 drr = c_scale(c_sub(ez_ip, ez), p.inv_dr);
+        if (kz >= 0) {
+            const size_t ix = ((size_t)i * nphi + j) * (2 * p.pz) + kz;
+            float2 ps = c_add(c_scale(p.psi.hp_z[ix], __ldg(p.t.bz_h + k)), c_scale(dz, __ldg(p.t.cz_h + k)));
+            p.psi.hp_z[ix] = ps;
+            dz = c_add(dz, ps);
+        }
+        if (ir >= 0) {
+            const size_t ix = ((size_t)ir * nphi + j) * nz + k;
+            float2 ps = c_add(c_scale(p.psi.hp_r[ix], __ldg(p.t.br_h + i)), c_scale(drr, __ldg(p.t.cr_h + i)));
+            p.psi.hp_r[ix] = ps;
+            drr = c_add(drr, ps);
+        }
+        const float2 h = p.f.Hp[c];
+        p.f.Hp[c] = c_sub(h, c_scale(c_sub(dz, drr), dt));
+    }
+    // H_z(i+1/2, j+1/2, k): (1/r) d(r E_phi)/dr - (1/r) dE_r/dphi
+    //   (r_{i+1} E(i+1) - r_i E(i)) / (r_{i+1/2} dr) = (E(i+1)-E(i))/dr + (E(i+1)+E(i)) / (2 r_{i+1/2})
+    {
+        float2 drr = c_add(c_scale(c_sub(ep_ip, ep), p.inv_dr), c_scale(c_add(ep_ip, ep), 0.5f * irh));
+        const float2 dph = c_scale(c_sub(er_jp, er), irh * p.inv_dphi);
+        if (ir >= 0) {
+            const size_t ix = ((size_t)ir * nphi + j) * nz + k;
+            float2 ps = c_add(c_scale(p.psi.hz_r[ix], __ldg(p.t.br_h + i)), c_scale(drr, __ldg(p.t.cr_h + i)));
+            p.psi.hz_r[ix] = ps;
+            drr = c_add(drr, ps);
+        }
+        const float2 h = p.f.Hz[c];
+        p.f.Hz[c] = c_sub(h, c_scale(c_sub(drr, dph), dt));
+    }
+}
+
+// ------------------------------------------------------------------ E update
+// E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})  (Eq. 4), then the
+// running DFT X_q += E^{n+1} e^{i w_q t_{n+1}} dt.
+__global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_e(const StepParams p, const int n)
+{
+    const int k = blockIdx.x * ZDA_BX + threadIdx.x;
+    const int j = blockIdx.y * ZDA_BY + threadIdx.y;
+    const int i = blockIdx.z;
+    if (k >= p.nz || j >= p.nphi) return;
+    const int nz = p.nz, nphi = p.nphi, nr = p.nr;
+    const size_t sj = (size_t)nz, si = (size_t)nphi * nz;
+    const size_t c = (size_t)i * si + (size_t)j * sj + k;
+    const float2 zero = make_float2(0.f, 0.f);
+
+    const float2 hr = p.f.Hr[c], hp = p.f.Hp[c], hz = p.f.Hz[c];
+    float2 hz_jm, hr_jm;
+    if (j > 0) {
+        hz_jm = p.f.Hz[c - sj];
+        hr_jm = p.f.Hr[c - sj];
+    } else {                                   // psi(phi - tau) = e^{-i m tau} psi(phi)
+        const size_t c1 = c + (size_t)(nphi - 1) * sj;
+        hz_jm = c_mul(p.bloch_inv, p.f.Hz[c1]);
+        hr_jm = c_mul(p.bloch_inv, p.f.Hr[c1]);
+    }
+    const float2 hp_km = (k > 0) ? p.f.Hp[c - 1] : zero;
+    const float2 hr_km = (k > 0) ? p.f.Hr[c - 1] : zero;
+    const float2 hz_im = (i > 0) ? p.f.Hz[c - si] : zero;
+    const float2 hp_im = (i > 0) ? p.f.Hp[c - si] : zero;
+    const float irn = __ldg(p.t.inv_r_n + i), irh = __ldg(p.t.inv_r_h + i);
+    const int kz = zslab(k, nz, p.pz);
+    const int ir = rslab(i, nr, p.pr_in, p.pr_out);
+    const float dt = p.dt;
+    const size_t ij = (size_t)i * nphi + j;
+
+    float2 jr = zero, jp = zero;
+    if (k == p.src_k) {
+        if (p.src_mode == SRC_PLANE_WAVE) {
+            // m = +1 part of an x-polarised sheet: (1/2, i/2) e^{i m phi} g(t) / dz
+            const float a = __ldg(p.t.pulse + n) * p.src_scale;
+            const float2 pn = p.t.ph_n[j], ph = p.t.ph_h[j];
+            jr = c_scale(pn, a);
+            jp = make_float2(-ph.y * a, ph.x * a);
+        } else if (p.src_mode == SRC_ADJOINT) {
+            float2 sr = zero, sp = zero;
+            const float2 *kt = p.t.adj_time + (size_t)n * p.nq;
+            for (int q = 0; q < p.nq; ++q) {
+                const float2 kq = kt[q];
+                sr = c_fma(p.beta_r[(size_t)q * nr + i], kq, sr);
+                sp = c_fma(p.beta_p[(size_t)q * nr + i], kq, sp);
+            }
+            jr = c_mul(p.t.ph_n[j], sr);
+            jp = c_mul(p.t.ph_h[j], sp);
+        }
+    }
+
+    float2 er = p.f.Er[c], ep = p.f.Ep[c], ez = p.f.Ez[c];
+    // E_r(i+1/2, j, k): (1/r) dH_z/dphi - dH_phi/dz ; PEC at k = 0
+    if (k > 0) {
+        const float2 dph = c_scale(c_sub(hz, hz_jm), irh * p.inv_dphi);
+        float2 dz = c_scale(c_sub(hp, hp_km), p.inv_dz);
+        if (kz >= 0) {
+            const size_t ix = ij * (2 * p.pz) + kz;
+            float2 ps = c_add(c_scale(p.psi.er_z[ix], __ldg(p.t.bz_n + k)), c_scale(dz, __ldg(p.t.cz_n + k)));
+            p.psi.er_z[ix] = ps;
+            dz = c_add(dz, ps);
+        }
+        const float ie = 1.0f / (__ldg(p.t.a_n + k) + __ldg(p.t.d_n + k) * __ldg(p.rb_r + ij));
+        er = c_add(er, c_scale(c_sub(c_sub(dph, dz), jr), dt * ie));
+        p.f.Er[c] = er;
+    }
+    // E_phi(i, j+1/2, k): dH_r/dz - dH_z/dr ; PEC at i = 0 and k = 0
+    if (i > 0 && k > 0) {
+        float2 dz = c_scale(c_sub(hr, hr_km), p.inv_dz);
+        float2 drr = c_scale(c_sub(hz, hz_im), p.inv_dr);
+        if (kz >= 0) {
+            const size_t ix = ij * (2 * p.pz) + kz;
+            float2 ps = c_add(c_scale(p.psi.ep_z[ix], __ldg(p.t.bz_n + k)), c_scale(dz, __ldg(p.t.cz_n + k)));
+            p.psi.ep_z[ix] = ps;
+            dz = c_add(dz, ps);
+        }
+        if (ir >= 0) {
+            const size_t ix = ((size_t)ir * nphi + j) * nz + k;
+            float2 ps = c_add(c_scale(p.psi.ep_r[ix], __ldg(p.t.br_n + i)), c_scale(drr, __ldg(p.t.cr_n + i)));
+            p.psi.ep_r[ix] = ps;
+            drr = c_add(drr, ps);
+        }
+        const float ie = 1.0f / (__ldg(p.t.a_n + k) + __ldg(p.t.d_n + k) * __ldg(p.rb_p + ij));
+        ep = c_add(ep, c_scale(c_sub(c_sub(dz, drr), jp), dt * ie));
+        p.f.Ep[c] = ep;
+    }
+    // E_z(i, j, k+1/2): (1/r) d(r H_phi)/dr - (1/r) dH_r/dphi ; PEC at i = 0
+    //   (r_{i+1/2} H(i+1/2) - r_{i-1/2} H(i-1/2)) / (r_i dr) = (H - H_im)/dr + (H + H_im) / (2 r_i)
+    if (i > 0) {
+        float2 drr = c_add(c_scale(c_sub(hp, hp_im), p.inv_dr), c_scale(c_add(hp, hp_im), 0.5f * irn));
+        const float2 dph = c_scale(c_sub(hr, hr_jm), irn * p.inv_dphi);
+        if (ir >= 0) {
+            const size_t ix = ((size_t)ir * nphi + j) * nz + k;
+            float2 ps = c_add(c_scale(p.psi.ez_r[ix], __ldg(p.t.br_n + i)), c_scale(drr, __ldg(p.t.cr_n + i)));
+            p.psi.ez_r[ix] = ps;
+            drr = c_add(drr, ps);
+        }
+        const float ie = 1.0f / (__ldg(p.t.a_c + k) + __ldg(p.t.d_c + k) * __ldg(p.rb_z + ij));
+        ez = c_add(ez, c_scale(c_sub(drr, dph), dt * ie));
+        p.f.Ez[c] = ez;
+    }
+
+    // running DFTs of E^{n+1}
+    if (p.mon && k == p.mon_k) {
+        const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
+        const size_t plane = (size_t)nr * nphi;
+        for (int q = 0; q < p.nq; ++q) {
+            const float2 w = tw[q];
+            float2 *m0 = p.mon + ((size_t)q * 2) * plane + ij;
+            float2 *m1 = m0 + plane;
+            *m0 = c_fma(er, w, *m0);
+            *m1 = c_fma(ep, w, *m1);
+        }
+    }
+    if (p.des) {
+        const int kk = k - p.des_k0;
+        if (kk >= 0 && kk < p.des_nk) {
+            const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
+            const size_t comp = (size_t)nr * nphi * p.des_nk;
+            float2 *d = p.des + ij * p.des_nk + kk;
+            for (int q = 0; q < p.nq; ++q) {
+                const float2 w = tw[q];
+                float2 *d0 = d + (size_t)q * 3 * comp;
+                d0[0] = c_fma(er, w, d0[0]);
+                d0[comp] = c_fma(ep, w, d0[comp]);
+                d0[2 * comp] = c_fma(ez, w, d0[2 * comp]);
+            }
+        }
+    }
+}
+
+void launch_update_h(const StepParams &p, cudaStream_t s)
+{
+    dim3 b(ZDA_BX, ZDA_BY), g((p.nz + ZDA_BX - 1) / ZDA_BX, (p.nphi + ZDA_BY - 1) / ZDA_BY, p.nr);
+    k_update_h<<<g, b, 0, s>>>(p);
+}
+
+void launch_update_e(const StepParams &p, int n, cudaStream_t s)
+{
+    dim3 b(ZDA_BX, ZDA_BY), g((p.nz + ZDA_BX - 1) / ZDA_BX, (p.nphi + ZDA_BY - 1) / ZDA_BY, p.nr);
+    k_update_e<<<g, b, 0, s>>>(p, n);
+}
+
+// ------------------------------------------------ density -> rho~ (conic + tanh)
+// Conic filter on the curvilinear wedge: weight max(0, 1 - d/R),
+// d^2 = (di dr)^2 + (r_c dj dphi)^2 with r_c the output pixel's radius; phi
+// wraps (the density repeats every wedge); taps beyond the design's r-edges
+// are dropped and the weights renormalised.  Then the tanh projection.
+__device__ __forceinline__ float cone_w(const FilterParams &fp, int i, int di, int dj)
+{
+    const float rc = fp.r_c0 + i * fp.dr;
+    const float a = di * fp.dr, b = rc * dj * fp.dphi;
+    return fmaxf(0.f, 1.f - sqrtf(a * a + b * b) / fp.R);
+}
+
+__device__ __forceinline__ float proj(const FilterParams &fp, float x)
+{
+    if (fp.beta <= 0.f) return x;
+    const float te = tanhf(fp.beta * fp.eta);
+    return (te + tanhf(fp.beta * (x - fp.eta))) / (te + tanhf(fp.beta * (1.f - fp.eta)));
+}
+
+__device__ __forceinline__ float proj_grad(const FilterParams &fp, float x)
+{
+    if (fp.beta <= 0.f) return 1.f;
+    const float te = tanhf(fp.beta * fp.eta);
+    const float ch = coshf(fp.beta * (x - fp.eta));
+    return fp.beta / (ch * ch) / (te + tanhf(fp.beta * (1.f - fp.eta)));
+}
+
+__global__ void k_filter_norm(const FilterParams fp, float *norm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= fp.nrd) return;
+    float s = 0.f;
+    for (int di = -fp.di_max; di <= fp.di_max; ++di) {
+        if (i + di < 0 || i + di >= fp.nrd) continue;
+        for (int dj = -fp.dj_max; dj <= fp.dj_max; ++dj) s += cone_w(fp, i, di, dj);
+    }
+    norm[i] = s;
+}
+
+__global__ void k_filter_project(const FilterParams fp, const float *__restrict__ rho,
+                                 const float *__restrict__ norm, float *rho_bar, float *rho_t)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= fp.nphi || i >= fp.nrd) return;
+    const int nphi = fp.nphi;
+    float v;
+    if (fp.filter_on) {
+        float s = 0.f;
+        for (int di = -fp.di_max; di <= fp.di_max; ++di) {
+            const int ii = i + di;
+            if (ii < 0 || ii >= fp.nrd) continue;
+            const float *row = rho + (size_t)ii * nphi;
+            for (int dj = -fp.dj_max; dj <= fp.dj_max; ++dj) {
+                const float w = cone_w(fp, i, di, dj);
+                if (w == 0.f) continue;
+                int jj = (j + dj) % nphi;
+                if (jj < 0) jj += nphi;
+                s = fmaf(w, __ldg(row + jj), s);
+            }
+        }
+        v = s / norm[i];
+    } else {
+        v = rho[(size_t)i * nphi + j];
+    }
+    rho_bar[(size_t)i * nphi + j] = v;
+    rho_t[(size_t)i * nphi + j] = proj(fp, v);
+}
+
+// dI/drho[i'][j'] = sum_{di,dj} w(i'-di; di, dj) / norm(i'-di) * P'(rho_bar) g_t  at (i'-di, j'-dj)
+__global__ void k_filter_project_bwd(const FilterParams fp, const float *__restrict__ rho_bar,
+                                     const float *__restrict__ norm, const float *__restrict__ g_t,
+                                     float *g_rho)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= fp.nphi || i >= fp.nrd) return;
+    const int nphi = fp.nphi;
+    if (!fp.filter_on) {
+        const size_t ix = (size_t)i * nphi + j;
+        g_rho[ix] = g_t[ix] * proj_grad(fp, rho_bar[ix]);
+        return;
+    }
+    float s = 0.f;
+    for (int di = -fp.di_max; di <= fp.di_max; ++di) {
+        const int io = i - di;                  // output pixel row that read this input with offset di
+        if (io < 0 || io >= fp.nrd) continue;
+        const float inv_n = 1.f / norm[io];
+        for (int dj = -fp.dj_max; dj <= fp.dj_max; ++dj) {
+            const float w = cone_w(fp, io, di, dj);
+            if (w == 0.f) continue;
+            int jo = (j - dj) % nphi;
+            if (jo < 0) jo += nphi;
+            const size_t ox = (size_t)io * nphi + jo;
+            s = fmaf(w * inv_n, g_t[ox] * proj_grad(fp, rho_bar[ox]), s);
+        }
+    }
+    g_rho[(size_t)i * nphi + j] = s;
+}
+
+void launch_filter_norm(const FilterParams &fp, float *norm, cudaStream_t s)
+{
+    k_filter_norm<<<(fp.nrd + 127) / 128, 128, 0, s>>>(fp, norm);
+}
+void launch_filter_project(const FilterParams &fp, const float *rho, const float *norm, float *rho_bar,
+                           float *rho_t, cudaStream_t s)
+{
+    dim3 g((fp.nphi + 127) / 128, fp.nrd);
+    k_filter_project<<<g, 128, 0, s>>>(fp, rho, norm, rho_bar, rho_t);
+}
+void launch_filter_project_backward(const FilterParams &fp, const float *rho_bar, const float *norm,
+                                    const float *g_t, float *g_rho, cudaStream_t s)
+{
+    dim3 g((fp.nphi + 127) / 128, fp.nrd);
+    k_filter_project_bwd<<<g, 128, 0, s>>>(fp, rho_bar, norm, g_t, g_rho);
+}
+
+// Transverse averages of the cell density (0 in the r-PML columns, where the
+// design layer holds eps_lo): E_r sites average the two phi-neighbour cells,
+// E_phi sites the two r-neighbours, E_z sites four; phi wraps, r clamps.
+__global__ void k_rho_bar(const float *__restrict__ rho_t, int nr, int nphi, int i_d0, int i_d1,
+                          float *rb_r, float *rb_p, float *rb_z)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= nphi || i >= nr) return;
+    auto cell = [&](int ii, int jj) -> float {
+        if (ii < 0) ii = 0;
+        if (jj < 0) jj += nphi;
+        return (ii >= i_d0 && ii < i_d1) ? rho_t[(size_t)(ii - i_d0) * nphi + jj] : 0.f;
+    };
+    const float c00 = cell(i, j), c0m = cell(i, j - 1), cm0 = cell(i - 1, j), cmm = cell(i - 1, j - 1);
+    const size_t ix = (size_t)i * nphi + j;
+    rb_r[ix] = 0.5f * (c0m + c00);
+    rb_p[ix] = 0.5f * (cm0 + c00);
+    rb_z[ix] = 0.25f * (cmm + cm0 + c0m + c00);
+}
+
+void launch_rho_bar(const float *rho_t, int nr, int nphi, int i_d0, int i_d1, float *rb_r, float *rb_p,
+                    float *rb_z, cudaStream_t s)
+{
+    dim3 g((nphi + 127) / 128, nr);
+    k_rho_bar<<<g, 128, 0, s>>>(rho_t, nr, nphi, i_d0, i_d1, rb_r, rb_p, rb_z);
+}
+
+// ------------------------------------------------ near-to-far focal transform
+// S_q = sum_i Gr[q][i] sum_j e^{-i phi_j} E_r(q,i,j) + Gp[q][i] sum_j e^{-i phi_{j+1/2}} E_phi(q,i,j)
+// (Rayleigh-Sommerfeld weights with quadrature, the -i of the E_phi term and
+// the conjugation of the -w entries are in the radial tables).  Warp-shuffle
+// block reductions in FP64; one partial per (q, i), then a per-q sum:
+// deterministic, no atomics.
+__device__ __forceinline__ double2 d_cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ double2 block_sum2(double2 v)
+{
+    __shared__ double2 red[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : make_double2(0.0, 0.0);
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        }
+    return v;
+}
+
+__global__ void k_focal_partial(const float2 *__restrict__ mon, const double2 *__restrict__ Gr,
+                                const double2 *__restrict__ Gp, const double2 *__restrict__ emph_n,
+                                const double2 *__restrict__ emph_h, int nr, int nphi, double2 *partial)
+{
+    const int i = blockIdx.x, q = blockIdx.y;
+    const size_t plane = (size_t)nr * nphi;
+    const float2 *er = mon + (size_t)q * 2 * plane + (size_t)i * nphi;
+    const float2 *ep = er + plane;
+    double2 sr = make_double2(0, 0), sp = make_double2(0, 0);
+    for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
+        const float2 a = er[j], b = ep[j];
+        const double2 pa = d_cmul(emph_n[j], make_double2(a.x, a.y));
+        const double2 pb = d_cmul(emph_h[j], make_double2(b.x, b.y));
+        sr.x += pa.x; sr.y += pa.y;
+        sp.x += pb.x; sp.y += pb.y;
+    }
+    const double2 gr = Gr[(size_t)q * nr + i], gp = Gp[(size_t)q * nr + i];
+    const double2 tr = d_cmul(gr, sr), tp = d_cmul(gp, sp);
+    double2 v = block_sum2(make_double2(tr.x + tp.x, tr.y + tp.y));
+    if (threadIdx.x == 0) partial[(size_t)q * nr + i] = v;
+}
+
+__global__ void k_focal_sum(const double2 *__restrict__ partial, int nr, double2 *S, int *status)
+{
+    const int q = blockIdx.x;
+    double2 v = make_double2(0, 0);
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        const double2 a = partial[(size_t)q * nr + i];
+        v.x += a.x; v.y += a.y;
+    }
+    v = block_sum2(v);
+    if (threadIdx.x == 0) {
+        S[q] = v;
+        if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(status, 1);
+    }
+}
+
+void launch_focal_partial(const float2 *mon, const double2 *Gr, const double2 *Gp, const double2 *emph_n,
+                          const double2 *emph_h, int nq, int nr, int nphi, double2 *partial, cudaStream_t s)
+{
+    dim3 g(nr, nq);
+    k_focal_partial<<<g, 256, 0, s>>>(mon, Gr, Gp, emph_n, emph_h, nr, nphi, partial);
+}
+void launch_focal_sum(const double2 *partial, int nq, int nr, double2 *S, int *status, cudaStream_t s)
+{
+    k_focal_sum<<<nq, 256, 0, s>>>(partial, nr, S, status);
+}
+
+// ------------------------------------------------ adjoint source profiles
+// The transpose of the focal transform gives the sensitivity
+// a_q = conj(g_q) w_q on the monitor sites; the adjoint (+m) run is driven by
+// b_q = i conj(a_q) / (wt_q V) = [i g_q conj(G_q(r)) / (wt_q V(r))] e^{i phi}.
+__global__ void k_adjoint_profiles(const double2 *__restrict__ g, const double2 *__restrict__ Gr,
+                                   const double2 *__restrict__ Gp, const float *__restrict__ wt, int nr,
+                                   double r_lo, double dr, double vol_scale, float2 *beta_r, float2 *beta_p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (i >= nr) return;
+    const double2 gq = g[q];
+    const double w = (double)wt[q];
+    const double Vr = (r_lo + (i + 0.5) * dr) * vol_scale;   // r dr dphi dz
+    const double Vp = (r_lo + i * dr) * vol_scale;
+    const double2 ig = make_double2(-gq.y, gq.x);              // i g
+    const double2 cr = d_cmul(ig, make_double2(Gr[(size_t)q * nr + i].x, -Gr[(size_t)q * nr + i].y));
+    const double2 cp = d_cmul(ig, make_double2(Gp[(size_t)q * nr + i].x, -Gp[(size_t)q * nr + i].y));
+    beta_r[(size_t)q * nr + i] = make_float2((float)(cr.x / (w * Vr)), (float)(cr.y / (w * Vr)));
+    beta_p[(size_t)q * nr + i] = (Vp > 0) ? make_float2((float)(cp.x / (w * Vp)), (float)(cp.y / (w * Vp)))
+                                          : make_float2(0.f, 0.f);
+}
+
+void launch_adjoint_profiles(const double2 *g, const double2 *Gr, const double2 *Gp, const float *wt, int nq,
+                             int nr, double r_lo, double dr, double vol_scale, float2 *beta_r, float2 *beta_p,
+                             cudaStream_t s)
+{
+    dim3 gr((nr + 127) / 128, nq);
+    k_adjoint_profiles<<<gr, 128, 0, s>>>(g, Gr, Gp, wt, nr, r_lo, dr, vol_scale, beta_r, beta_p);
+}
+
+// ------------------------------------------------ gradient overlap
+// dI/deps_s = Re sum_q wt_q^2 V_s E_q(s) conj(A_{qbar}(s)), qbar the index of
+// -w_q (the adjoint +m run carries the Bloch -m adjoint field as its
+// conjugate at the opposite frequency).
+__global__ void k_site_gradient(const float2 *__restrict__ des_f, const float2 *__restrict__ des_a,
+                                const float *__restrict__ wt, int nq, int nr, int nphi, int nk, double r_lo,
+                                double dr, double vol_scale, float *site_grad)
+{
+    const size_t comp = (size_t)nr * nphi * nk;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * comp) return;
+    const int c = (int)(t / comp);
+    const size_t s = t - (size_t)c * comp;
+    const int i = (int)(s / ((size_t)nphi * nk));
+    const int nl = nq / 2;
+    float acc = 0.f;
+    for (int q = 0; q < nq; ++q) {
+        const int qb = (q + nl) % nq;
+        const float2 e = des_f[((size_t)q * 3 + c) * comp + s];
+        const float2 a = des_a[((size_t)qb * 3 + c) * comp + s];
+        const float w2 = wt[q] * wt[q];
+        acc = fmaf(w2, e.x * a.x + e.y * a.y, acc);           // Re(e conj(a))
+    }
+    const double r = (c == 0) ? r_lo + (i + 0.5) * dr : r_lo + i * dr;
+    site_grad[t] = acc * (float)(r * vol_scale);
+}
+
+// Transpose of the site averaging: each design cell (i, j, k) collects a
+// quarter of the gradient of every E site whose permittivity averages it,
+// summed over the design layer's z-cells, times (eps_hi - eps_lo).
+__global__ void k_cell_gradient(const float *__restrict__ sg, int nr, int nphi, int nk, int i_d0, int nrd,
+                                float deps, float *g_t)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ic = blockIdx.y;
+    if (j >= nphi || ic >= nrd) return;
+    const int i = i_d0 + ic;
+    const size_t comp = (size_t)nr * nphi * nk;
+    const int jp = (j + 1 < nphi) ? j + 1 : 0;
+    const bool ip_ok = i + 1 < nr;
+    auto G = [&](int c, int ii, int jj, int kk) -> float {
+        return sg[(size_t)c * comp + ((size_t)ii * nphi + jj) * nk + kk];
+    };
+    float acc = 0.f;
+    for (int kk = 0; kk + 1 < nk; ++kk) {      // design cells k0 .. k1-1 ; E planes k0 .. k1
+        float s = G(0, i, j, kk) + G(0, i, jp, kk) + G(0, i, j, kk + 1) + G(0, i, jp, kk + 1);
+        s += G(1, i, j, kk) + G(1, i, j, kk + 1);
+        s += G(2, i, j, kk) + G(2, i, jp, kk);
+        if (ip_ok) {
+            s += G(1, i + 1, j, kk) + G(1, i + 1, j, kk + 1);
+            s += G(2, i + 1, j, kk) + G(2, i + 1, jp, kk);
+        }
+        acc += 0.25f * s;
+    }
+    g_t[(size_t)ic * nphi + j] = acc * deps;
+}
+
+void launch_site_gradient(const float2 *des_f, const float2 *des_a, const float *wt, int nq, int nr, int nphi,
+                          int nk, double r_lo, double dr, double vol_scale, float *site_grad, cudaStream_t s)
+{
+    const size_t n = (size_t)3 * nr * nphi * nk;
+    k_site_gradient<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(des_f, des_a, wt, nq, nr, nphi, nk, r_lo, dr,
+                                                               vol_scale, site_grad);
+}
+void launch_cell_gradient(const float *site_grad, int nr, int nphi, int nk, int i_d0, int nrd, float deps,
+                          float *g_t, cudaStream_t s)
+{
+    dim3 g((nphi + 127) / 128, nrd);
+    k_cell_gradient<<<g, 128, 0, s>>>(site_grad, nr, nphi, nk, i_d0, nrd, deps, g_t);
+}
+
+__global__ void k_status_check(const float *x, size_t n, int *status)
+{
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; t < n; t += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[t])) { atomicOr(status, 1); return; }
+}
+void launch_fill_status_check(const float *x, size_t n, int *status, cudaStream_t s)
+{
+    k_status_check<<<152, 256, 0, s>>>(x, n, status);
+}
+
+}  // namespace zda

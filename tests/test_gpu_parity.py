@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Element-by-element comparisons on the same seeded inputs: filter and
+projection, the focal transform, forward DFT fields / final fields / focal
+phasors, the adjoint DFT and the gradient, on grids that span several tiles
+with ragged tails, plus the full-size wide-zone grid on a shortened run.
+Tolerances: DFT fields relative L2 <= 1e-4, gradients <= 1e-3 (FP32 device
+arithmetic against FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from zda_inputs import zone_cfg1, zone_cfg2, zone_tiny, smoothed_rho, rho_for
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def _zone(spec):
+    from paper_2501_07979_gb300 import Zone
+    return Zone(spec, device=0)
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def _dev(x):
+    return torch.tensor(np.asarray(x), dtype=torch.float32, device="cuda:0")
+
+
+def _oracle_forward_state(spec, rho):
+    g = O.Geometry(spec)
+    rt = O.rho_tilde(spec, g, rho)
+    eps = O.site_eps(spec, g, rt)
+    t = g.dt * (np.arange(spec.n_steps) + 0.5)
+    mon, des, st = O.run(spec, g, eps, src_pat=O.plane_wave_pattern(spec, g),
+                         src_time=O.pulse(spec, t)[:, None].astype(complex),
+                         twiddle=O.twiddles(g, spec.n_steps),
+                         state=np.zeros((O.N_STATE, spec.n_r, spec.n_phi, spec.n_z), complex))
+    return mon, des, st, O.focal_phasors(spec, g, mon)
+
+
+RAGGED = {
+    "tiny": zone_tiny(n_steps=300),
+    "ragged": zone_tiny(n_r=27, n_phi=7, n_z=45, pml_r_in=3, pml_r_out=5, pml_z=5, n_steps=250,
+                        layer_k0=(0, 15, 19), design_k0=15, design_k1=19, source_k=8, monitor_k=26,
+                        wavelengths=(0.85, 1.0, 1.2), filter_radius=0.2, beta=3.0, pulse_sigma=0.4,
+                        pulse_t0=1.6),
+    "one_phi_cell": zone_tiny(n_phi=1, n_fold=300, n_steps=200, r_lo=8.0),
+    "no_inner_pml": zone_tiny(pml_r_in=0, n_steps=200),
+}
+
+
+# ------------------------------------------------------------------ K6
+@pytest.mark.parametrize("name", ["cfg2", "ragged"])
+def test_filter_project_matches_oracle(name):
+    spec = zone_cfg2(n_steps=10) if name == "cfg2" else RAGGED["ragged"]
+    g = O.Geometry(spec)
+    rho = rho_for(spec, 2)
+    z = _zone(spec)
+    got = z.filter_project(_dev(rho)).cpu().numpy()
+    want = O.project(spec, O.conic_filter(spec, g, rho))
+    assert np.abs(got - want).max() < 5e-6
+
+
+@pytest.mark.parametrize("name", ["cfg2", "ragged"])
+def test_filter_project_backward_matches_oracle(name):
+    spec = zone_cfg2(n_steps=10) if name == "cfg2" else RAGGED["ragged"]
+    g = O.Geometry(spec)
+    rng = np.random.default_rng(9)
+    rho = rho_for(spec, 2)
+    gt = rng.standard_normal(rho.shape)
+    z = _zone(spec)
+    got = z.filter_project_backward(_dev(rho), _dev(gt)).cpu().numpy()
+    want = O.conic_filter_T(spec, g, gt * O.project_grad(spec, O.conic_filter(spec, g, rho)))
+    assert _rel(got, want) < 1e-5
+
+
+# ------------------------------------------------------------------ K10
+@pytest.mark.parametrize("name", ["cfg2", "ragged"])
+def test_focal_transform_matches_oracle(name):
+    spec = zone_cfg2(n_steps=10) if name == "cfg2" else RAGGED["ragged"]
+    g = O.Geometry(spec)
+    rng = np.random.default_rng(4)
+    sh = (g.n_freq, 2, spec.n_r, spec.n_phi)
+    mon = (rng.standard_normal(sh) + 1j * rng.standard_normal(sh)).astype(np.complex64)
+    z = _zone(spec)
+    got = z.focal_transform(torch.tensor(mon, device="cuda:0"))
+    want = O.focal_phasors(spec, g, mon.astype(np.complex128))
+    assert _rel(got, want) < 1e-6
+
+
+# ------------------------------------------------------------------ forward
+@pytest.mark.parametrize("name", ["cfg1"] + list(RAGGED))
+def test_forward_matches_oracle(name):
+    spec = zone_cfg1() if name == "cfg1" else RAGGED[name]
+    rho = rho_for(spec, 1)
+    z = _zone(spec)
+    S = z.forward(_dev(rho))
+    mon, des, st, S_ref = _oracle_forward_state(spec, rho)
+    assert _rel(z.monitor_dft().cpu().numpy(), mon) < FIELD_TOL
+    got_des = np.moveaxis(z.design_dft(0).cpu().numpy(), 4, 2)        # -> [q][c][k][i][j]
+    assert _rel(got_des, des) < FIELD_TOL
+    assert _rel(z.fields().cpu().numpy(), st[:6]) < FIELD_TOL
+    assert _rel(S, S_ref) < FIELD_TOL
+
+
+@pytest.mark.parametrize("value", [0.0, 1.0])
+def test_forward_uniform_density(value):
+    """Degenerate designs: rho = 0 (air layer) and rho = 1 (solid TiO2)."""
+    spec = RAGGED["tiny"]
+    rho = np.full((spec.n_r_design, spec.n_phi), value)
+    z = _zone(spec)
+    S = z.forward(_dev(rho))
+    _, _, _, S_ref = _oracle_forward_state(spec, rho)
+    assert _rel(S, S_ref) < FIELD_TOL
+
+
+def test_forward_is_deterministic():
+    spec = RAGGED["ragged"]
+    z = _zone(spec)
+    r = _dev(rho_for(spec, 3))
+    a = z.forward(r)
+    fa = z.fields().cpu()
+    b = z.forward(r)
+    assert np.array_equal(a, b) and torch.equal(fa, z.fields().cpu())
+
+
+# ------------------------------------------------------------------ adjoint
+GRAD_SPECS = {
+    "tiny2": zone_tiny(n_steps=700, filter_radius=0.25, beta=4.0, wavelengths=(0.9, 1.1),
+                       pulse_sigma=0.4, pulse_t0=1.6),
+    "ragged3": RAGGED["ragged"].replace(n_steps=500),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAD_SPECS))
+def test_gradient_matches_oracle(name):
+    spec = GRAD_SPECS[name]
+    rho = smoothed_rho(spec.n_r_design, spec.n_phi, 5, mode="minmax")
+    z = _zone(spec)
+    S = z.forward(_dev(rho))
+    grad = z.adjoint(4.0 * S).cpu().numpy()
+    I_ref, g_ref, fwd, adj = O.gradient(spec, rho)
+    assert _rel(S, fwd["S"]) < FIELD_TOL
+    got_adj = np.moveaxis(z.design_dft(1).cpu().numpy(), 4, 2)
+    assert _rel(got_adj, adj["des_adj"]) < GRAD_TOL
+    assert _rel(grad, g_ref) < GRAD_TOL
+
+
+def test_autograd_function_and_iteration_agree():
+    from paper_2501_07979_gb300 import zone_focal
+    spec = GRAD_SPECS["tiny2"]
+    rho = smoothed_rho(spec.n_r_design, spec.n_phi, 5, mode="minmax")
+    z = _zone(spec)
+    r = _dev(rho).requires_grad_(True)
+    S = zone_focal(r, z)
+    I = 2.0 * (S ** 2).sum()
+    I.backward()
+    I_it, g_it = z.iteration(_dev(rho))
+    I_h, g_h = z.iteration(torch.tensor(rho, dtype=torch.float32), host=True)
+    I_ref, g_ref, _, _ = O.gradient(spec, rho)
+    assert abs(I.item() - I_ref) / I_ref < FIELD_TOL
+    assert abs(I_it - I_ref) / I_ref < FIELD_TOL and I_h == I_it
+    assert _rel(r.grad.cpu().numpy(), g_ref) < GRAD_TOL
+    assert torch.equal(g_it.cpu(), r.grad.cpu()) and torch.equal(g_h, g_it.cpu())
+
+
+def test_objective_of_phasors_other_than_intensity():
+    """The backward accepts any dI/dS: here f = |S_0|^2 only."""
+    from paper_2501_07979_gb300 import zone_focal
+    spec = GRAD_SPECS["tiny2"]
+    rho = smoothed_rho(spec.n_r_design, spec.n_phi, 6, mode="minmax")
+    z = _zone(spec)
+    r = _dev(rho).requires_grad_(True)
+    S = zone_focal(r, z)
+    (S[0] ** 2).sum().backward()
+    fwd = O.forward(spec, rho)
+    fwd["rho"] = rho
+    g = np.zeros(fwd["S"].shape, complex)
+    g[0] = 2 * fwd["S"][0]
+    adj = O.adjoint(spec, fwd, g)
+    geom = fwd["geom"]
+    rbar = O.conic_filter(spec, geom, rho)
+    g_ref = O.conic_filter_T(spec, geom, adj["grad_rho_tilde"] * O.project_grad(spec, rbar))
+    assert _rel(r.grad.cpu().numpy(), g_ref) < GRAD_TOL
+
+
+# ------------------------------------------------------------------ full size
+def test_wide_zone_full_grid_short_run_matches_oracle():
+    """The 300x320x160 wide-zone grid (3 wavelengths, filter + projection) in
+    the benchmark's launch configuration, shortened to 120 steps so the
+    oracle finishes: forward DFTs and phasors."""
+    spec = zone_cfg2(n_steps=120)
+    rho = rho_for(spec, 2)
+    z = _zone(spec)
+    S = z.forward(_dev(rho))
+    mon, des, _, S_ref = _oracle_forward_state(spec, rho)
+    assert _rel(z.monitor_dft().cpu().numpy(), mon) < FIELD_TOL
+    assert _rel(np.moveaxis(z.design_dft(0).cpu().numpy(), 4, 2), des) < FIELD_TOL
+    assert _rel(S, S_ref) < FIELD_TOL
+
+
+# ------------------------------------------------------------------ errors
+def test_adjoint_before_forward_is_a_state_error():
+    from paper_2501_07979_gb300 import ZdaError
+    spec = RAGGED["tiny"]
+    z = _zone(spec)
+    with pytest.raises(ZdaError, match="ZDA_ERR_STATE"):
+        z.adjoint(np.ones(z.n_freq, complex))
+
+
+def test_divergent_run_reports_nonfinite():
+    """A near-zero permittivity makes the explicit scheme overflow: the run
+    ends with ZDA_ERR_NONFINITE instead of returning garbage."""
+    from paper_2501_07979_gb300 import ZdaError
+    spec = RAGGED["tiny"].replace(layer_eps=(1e-9, 1e-9, 1e-9), n_steps=400)
+    z = _zone(spec)
+    with pytest.raises(ZdaError, match="ZDA_ERR_NONFINITE"):
+        z.forward(_dev(np.zeros((spec.n_r_design, spec.n_phi))))
