@@ -183,6 +183,15 @@ zda_status zda_copy_design_dft(zda_zone *zone, int which, float *out_dev, void *
  * (for launch accounting in benchmarks). */
 long long zda_zone_launch_count(const zda_zone *zone);
 
+/* Time-step kernel of the zone.  variant 1 (default when n_z <= 256): one
+ * fused launch per step (E and H updated together, ping-pong field buffers,
+ * streaming along r; tile_phi in {2, 4} phi rows per thread block,
+ * i_ranges radius ranges per phi tile, 0 = as many as fit in one wave).
+ * variant 0: two launches per step (H update, E update), in place.  Both
+ * compute the same scheme; results agree to FP32 rounding. */
+zda_status zda_zone_set_kernel(zda_zone *zone, int variant, int tile_phi, int i_ranges);
+zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi, int *i_ranges);
+
 /* Kernel timing with CUDA events recorded on the launching stream: with
  * every > 0, every every-th time step's H-update and E-update launches are
  * bracketed by events (a ring of 64 samples; the host waits for a sample

@@ -74,6 +74,8 @@ SIGNATURES = {
     "zda_copy_monitor_dft": (_i, [_vp, _vp, _vp]),
     "zda_copy_design_dft": (_i, [_vp, _i, _vp, _vp]),
     "zda_zone_launch_count": (ctypes.c_longlong, [_vp]),
+    "zda_zone_set_kernel": (_i, [_vp, _i, _i, _i]),
+    "zda_zone_get_kernel": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "zda_zone_set_timing": (_i, [_vp, _i]),
     "zda_zone_timing": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "zda_last_error": (ctypes.c_char_p, []),

@@ -18,6 +18,7 @@
 
 #include "zda.h"
 #include "zda_internal.h"
+#include "zda_step.h"
 
 using cd = std::complex<double>;
 
@@ -43,7 +44,7 @@ struct zda_ctx {
 namespace {
 
 struct Layout {           // byte offsets inside the workspace
-    size_t fields, psi_z, psi_r, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
+    size_t fields, psi_z, psi_r, fields2, psi_h2, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
         norm, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
         ph_h, pulse, twiddle, adj_time, Gr, Gp, emph_n, emph_h, wt, beta_r, beta_p, g_in, partial, S,
         status, total;
@@ -67,6 +68,9 @@ struct zda_zone {
     bool have_forward = false;
     bool adjoint_ok = false;        // the broadband adjoint pulse matrix was invertible
     long long launches = 0;
+    // time-step kernel: 0 = split H/E launches, 1 = fused single launch
+    int variant = 1, tile_phi = 2, i_ranges = 0;
+    int last_parity = 0;            // fused runs: which buffer holds the final fields
     // optional CUDA-event timing of every `time_every`-th H/E launch pair
     int time_every = 0;
     std::vector<cudaEvent_t> ev;    // ring of (before H, between, after E) triples
@@ -183,6 +187,9 @@ static void compute_layout(zda_zone &z)
     L.fields = take(6 * ncell * sizeof(float2));
     L.psi_z = take(4 * plane * 2 * d.pml_z * sizeof(float2));
     L.psi_r = take(4 * (size_t)(d.pml_r_in + d.pml_r_out) * np * nz * sizeof(float2));
+    // second field buffer and H-side CPML set for the fused (ping-pong) step
+    L.fields2 = take(6 * ncell * sizeof(float2));
+    L.psi_h2 = take((2 * plane * 2 * d.pml_z + 2 * (size_t)(d.pml_r_in + d.pml_r_out) * np * nz) * sizeof(float2));
     L.mon = take(Q * 2 * plane * sizeof(float2));
     L.des_f = take(Q * 3 * plane * z.nk * sizeof(float2));
     L.des_a = take(Q * 3 * plane * z.nk * sizeof(float2));
@@ -427,6 +434,7 @@ static zda_status derive(zda_zone &z)
     } else {
         z.di_max = z.dj_max = 0;
     }
+    if (d.n_z > zda::fused_max_nz()) z.variant = 0;
     compute_layout(z);
     z.tables_dirty = true;
     z.have_forward = false;
@@ -512,13 +520,95 @@ static zda_status run_filter(zda_zone &z, const float *rho_dev, cudaStream_t s)
 static zda_status clear_state(zda_zone &z, cudaStream_t s)
 {
     CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields, 0, z.L.psi_r - z.L.fields, s));      // fields, psi_z
-    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.psi_r, 0, z.L.mon - z.L.psi_r, s));          // psi_r
+    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.psi_r, 0, z.L.fields2 - z.L.psi_r, s));      // psi_r
+    if (z.variant == 1) {                                                             // fields2, psi_h2
+        CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields2, 0, z.L.mon - z.L.fields2, s));
+    }
     return ZDA_OK;
+}
+
+static int auto_i_ranges(const zda_zone &z)
+{
+    if (z.i_ranges > 0) return std::min(z.i_ranges, z.d.n_r);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = std::max(1, zda::fused_blocks_per_sm(z.tile_phi, z.d.n_z));
+    const int jt = (z.d.n_phi + z.tile_phi - 1) / z.tile_phi;
+    // as many radius ranges as fit in one wave (all CTAs co-resident, so the
+    // phi-halo rows of neighbouring tiles are read while still in L2), at
+    // least 8 radii per range
+    int ir = std::max(1, (sms * per_sm) / std::max(jt, 1));
+    ir = std::min(ir, std::max(1, z.d.n_r / 8));
+    return ir;
+}
+
+static zda::FusedParams fused_params(zda_zone &z, const zda::StepParams &p, int parity)
+{
+    using namespace zda;
+    const zda_zone_desc &d = z.d;
+    const size_t ncell = (size_t)d.n_r * d.n_phi * d.n_z;
+    float2 *A = P<float2>(z, z.L.fields), *B = P<float2>(z, z.L.fields2);
+    float2 *src = parity ? B : A, *dst = parity ? A : B;
+    const size_t nzs = (size_t)d.n_r * d.n_phi * 2 * d.pml_z;
+    const size_t nrs = (size_t)(d.pml_r_in + d.pml_r_out) * d.n_phi * d.n_z;
+    float2 *H1 = P<float2>(z, z.L.psi_h2);
+    // H-side CPML sets: set 0 = (psi_z[0..1], psi_r[0..1]) of the split layout, set 1 = psi_h2
+    float2 *s0[4] = {p.psi.hr_z, p.psi.hp_z, p.psi.hp_r, p.psi.hz_r};
+    float2 *s1[4] = {H1, H1 + nzs, H1 + 2 * nzs, H1 + 2 * nzs + nrs};
+    float2 **rd = parity ? s1 : s0, **wr = parity ? s0 : s1;
+    FusedParams f{};
+    f.nr = d.n_r; f.nphi = d.n_phi; f.nz = d.n_z; f.nzs = d.n_z;
+    f.pr_in = d.pml_r_in; f.pr_out = d.pml_r_out; f.pz = d.pml_z;
+    f.tj = z.tile_phi;
+    const int nir = auto_i_ranges(z);
+    f.i_range = (d.n_r + nir - 1) / nir;
+    f.dt = p.dt; f.inv_dr = p.inv_dr; f.inv_dz = p.inv_dz; f.inv_dphi = p.inv_dphi;
+    f.bloch = p.bloch; f.bloch_inv = p.bloch_inv;
+    f.Er = src; f.Ep = src + ncell; f.Ez = src + 2 * ncell;
+    f.Hr = src + 3 * ncell; f.Hp = src + 4 * ncell; f.Hz = src + 5 * ncell;
+    f.oEr = dst; f.oEp = dst + ncell; f.oEz = dst + 2 * ncell;
+    f.oHr = dst + 3 * ncell; f.oHp = dst + 4 * ncell; f.oHz = dst + 5 * ncell;
+    f.psH_hr_z = rd[0]; f.psH_hp_z = rd[1]; f.psH_hp_r = rd[2]; f.psH_hz_r = rd[3];
+    f.opsH_hr_z = wr[0]; f.opsH_hp_z = wr[1]; f.opsH_hp_r = wr[2]; f.opsH_hz_r = wr[3];
+    f.psE_er_z = p.psi.er_z; f.psE_ep_z = p.psi.ep_z; f.psE_ep_r = p.psi.ep_r; f.psE_ez_r = p.psi.ez_r;
+    f.t = p.t;
+    f.rb_r = p.rb_r; f.rb_p = p.rb_p; f.rb_z = p.rb_z;
+    f.src_mode = p.src_mode; f.src_k = p.src_k; f.src_scale = p.src_scale;
+    f.beta_r = p.beta_r; f.beta_p = p.beta_p;
+    f.nq = p.nq;
+    f.mon_k = p.mon_k; f.mon = p.mon;
+    f.des_k0 = p.des_k0; f.des_nk = p.des_nk; f.des = p.des;
+    return f;
 }
 
 static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
 {
     const int R = (int)z.ev_pending.size();
+    if (z.variant == 1) {
+        zda::FusedParams f[2] = {fused_params(z, p, 0), fused_params(z, p, 1)};
+        for (int n = 0; n < z.d.n_steps; ++n) {
+            const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
+            int slot = 0;
+            if (timed) {
+                slot = z.ev_next;
+                z.ev_next = (z.ev_next + 1) % R;
+                timing_drain_slot(z, slot);
+                CUDA_TRY(cudaEventRecord(z.ev[3 * slot], s));
+                CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 1], s));     // no separate H launch
+            }
+            cudaError_t e = zda::launch_fused_step(f[n & 1], n, s);
+            if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("fused step: ") + cudaGetErrorString(e));
+            if (timed) {
+                CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 2], s));
+                z.ev_pending[slot] = 1;
+            }
+        }
+        z.last_parity = z.d.n_steps & 1;
+        z.launches += z.d.n_steps;
+        return ZDA_OK;
+    }
+    z.last_parity = 0;
     for (int n = 0; n < z.d.n_steps; ++n) {
         const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
         int slot = 0;
@@ -780,7 +870,8 @@ zda_status zda_copy_fields(zda_zone *z, float *out, void *stream)
     if (st) return st;
     if (!out) return fail(ZDA_ERR_ARG, "null pointer");
     const size_t n = 6 * (size_t)z->d.n_r * z->d.n_phi * z->d.n_z * sizeof(float2);
-    CUDA_TRY(cudaMemcpyAsync(out, z->ws + z->L.fields, n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    const size_t off = (z->variant == 1 && z->last_parity) ? z->L.fields2 : z->L.fields;
+    CUDA_TRY(cudaMemcpyAsync(out, z->ws + off, n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return ZDA_OK;
 }
 
@@ -806,6 +897,29 @@ zda_status zda_copy_design_dft(zda_zone *z, int which, float *out, void *stream)
 }
 
 long long zda_zone_launch_count(const zda_zone *z) { return z ? z->launches : -1; }
+
+zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ranges)
+{
+    if (!z || (variant != 0 && variant != 1) || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
+    if (variant == 1) {
+        if (tile_phi != 2 && tile_phi != 4) return fail(ZDA_ERR_ARG, "fused step: tile_phi must be 2 or 4");
+        if (z->d.n_z > zda::fused_max_nz()) return fail(ZDA_ERR_ARG, "fused step supports n_z <= 256");
+    }
+    z->variant = variant;
+    z->tile_phi = variant == 1 ? tile_phi : z->tile_phi;
+    z->i_ranges = i_ranges;
+    z->have_forward = false;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_get_kernel(const zda_zone *z, int *variant, int *tile_phi, int *i_ranges)
+{
+    if (!z || !variant || !tile_phi || !i_ranges) return fail(ZDA_ERR_ARG, "null argument");
+    *variant = z->variant;
+    *tile_phi = z->tile_phi;
+    *i_ranges = z->variant == 1 ? auto_i_ranges(*z) : 0;
+    return ZDA_OK;
+}
 
 zda_status zda_zone_set_timing(zda_zone *z, int every)
 {

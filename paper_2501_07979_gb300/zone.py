@@ -181,6 +181,15 @@ class Zone:
         check(_lib.lib().zda_copy_design_dft(self.handle, int(which), _ptr(out), _stream()))
         return out
 
+    def set_kernel(self, variant=1, tile_phi=2, i_ranges=0):
+        """Time-step kernel: variant 1 fused (tile_phi 2 or 4), 0 split H/E."""
+        check(_lib.lib().zda_zone_set_kernel(self.handle, int(variant), int(tile_phi), int(i_ranges)))
+
+    def get_kernel(self):
+        v, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(_lib.lib().zda_zone_get_kernel(self.handle, ctypes.byref(v), ctypes.byref(t), ctypes.byref(r)))
+        return v.value, t.value, r.value
+
     def set_timing(self, every):
         """Sample every `every`-th step's H/E launches with CUDA events (0: off)."""
         check(_lib.lib().zda_zone_set_timing(self.handle, int(every)))

@@ -18,7 +18,8 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def libpath():
-    from paper_2501_07979_gb300 import build
+    import __graft_entry__
+    build = __graft_entry__._build_module()
     p = build.lib_path()
     srcs = [os.path.join(build.CSRC, s) for s in build.SOURCES] + [os.path.join(ROOT, "include", "zda.h")]
     if not os.path.exists(p) or os.path.getmtime(p) < max(os.path.getmtime(s) for s in srcs):

@@ -3,7 +3,8 @@
 Element-by-element comparisons on the same seeded inputs: filter and
 projection, the focal transform, forward DFT fields / final fields / focal
 phasors, the adjoint DFT and the gradient, on grids that span several tiles
-with ragged tails, plus the full-size wide-zone grid on a shortened run.
+with ragged tails, plus the full-size wide-zone workload checked against the
+oracle through the phi-invariant (ring) reduction.
 Tolerances: DFT fields relative L2 <= 1e-4, gradients <= 1e-3 (FP32 device
 arithmetic against FP64).
 """
@@ -22,9 +23,15 @@ FIELD_TOL = 1e-4
 GRAD_TOL = 1e-3
 
 
-def _zone(spec):
+KERNELS = {"split": (0, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0), "fused2_ir3": (1, 2, 3)}
+
+
+def _zone(spec, kernel=None):
     from paper_2501_07979_gb300 import Zone
-    return Zone(spec, device=0)
+    z = Zone(spec, device=0)
+    if kernel is not None:
+        z.set_kernel(*KERNELS[kernel])
+    return z
 
 
 def _rel(a, b):
@@ -100,11 +107,12 @@ def test_focal_transform_matches_oracle(name):
 
 
 # ------------------------------------------------------------------ forward
+@pytest.mark.parametrize("kernel", list(KERNELS))
 @pytest.mark.parametrize("name", ["cfg1"] + list(RAGGED))
-def test_forward_matches_oracle(name):
+def test_forward_matches_oracle(name, kernel):
     spec = zone_cfg1() if name == "cfg1" else RAGGED[name]
     rho = rho_for(spec, 1)
-    z = _zone(spec)
+    z = _zone(spec, kernel)
     S = z.forward(_dev(rho))
     mon, des, st, S_ref = _oracle_forward_state(spec, rho)
     assert _rel(z.monitor_dft().cpu().numpy(), mon) < FIELD_TOL
@@ -125,6 +133,22 @@ def test_forward_uniform_density(value):
     assert _rel(S, S_ref) < FIELD_TOL
 
 
+@pytest.mark.parametrize("kernel", ["fused2", "fused4"])
+def test_fused_step_equals_split_step(kernel):
+    """The fused single-launch step and the split H/E launches compute the
+    same scheme: fields and DFTs agree to FP32 rounding on the wide-zone grid
+    (400 steps, all CTAs, CPML slabs, phi wrap, ragged radius ranges)."""
+    spec = zone_cfg2(n_steps=400).replace(pulse_t0=0.05, source_k=38, monitor_k=54)
+    rho = _dev(rho_for(spec, 2))
+    a = _zone(spec, "split")
+    b = _zone(spec, kernel)
+    Sa, Sb = a.forward(rho), b.forward(rho)
+    assert np.abs(a.fields().cpu().numpy()).max() > 0
+    assert _rel(b.fields().cpu().numpy(), a.fields().cpu().numpy()) < 1e-6
+    assert _rel(b.design_dft(0).cpu().numpy(), a.design_dft(0).cpu().numpy()) < 1e-6
+    assert _rel(Sb, Sa) < 1e-6
+
+
 def test_forward_is_deterministic():
     spec = RAGGED["ragged"]
     z = _zone(spec)
@@ -143,11 +167,12 @@ GRAD_SPECS = {
 }
 
 
+@pytest.mark.parametrize("kernel", ["split", "fused2", "fused4"])
 @pytest.mark.parametrize("name", list(GRAD_SPECS))
-def test_gradient_matches_oracle(name):
+def test_gradient_matches_oracle(name, kernel):
     spec = GRAD_SPECS[name]
     rho = smoothed_rho(spec.n_r_design, spec.n_phi, 5, mode="minmax")
-    z = _zone(spec)
+    z = _zone(spec, kernel)
     S = z.forward(_dev(rho))
     grad = z.adjoint(4.0 * S).cpu().numpy()
     I_ref, g_ref, fwd, adj = O.gradient(spec, rho)
@@ -196,18 +221,42 @@ def test_objective_of_phasors_other_than_intensity():
 
 
 # ------------------------------------------------------------------ full size
-def test_wide_zone_full_grid_short_run_matches_oracle():
-    """The 300x320x160 wide-zone grid (3 wavelengths, filter + projection) in
-    the benchmark's launch configuration, shortened to 120 steps so the
-    oracle finishes: forward DFTs and phasors."""
-    spec = zone_cfg2(n_steps=120)
-    rho = rho_for(spec, 2)
+def _rings(spec, seed):
+    """Seeded axisymmetric (phi-invariant) density: smoothed random rings."""
+    from scipy.ndimage import gaussian_filter1d
+    rng = np.random.default_rng(seed)
+    f = gaussian_filter1d(rng.random(spec.n_r_design), 2.0, mode="reflect")
+    f = (f - f.min()) / (f.max() - f.min())
+    return np.repeat(f[:, None], spec.n_phi, axis=1)
+
+
+@pytest.mark.parametrize("n_steps", [20000])
+def test_wide_zone_full_size_against_one_cell_wedge(n_steps):
+    """Full-size wide zone (300x320x160, 3 wavelengths, filter + projection,
+    the benchmark's launch configuration and step count) with a
+    phi-invariant ring density.  Its solution is the single Bloch mode
+    e^{i phi}: the 320-cell wedge equals a 1-cell wedge of the same dphi
+    (n_fold = 4000 * 320), which the oracle runs in full.  Compared element
+    by element: monitor and design DFTs (times e^{i phi_j}), focal phasors,
+    and the gradient (the 1-cell pixel gradient is the sum over the 320
+    pixels of a ring, each equal by symmetry)."""
+    spec = zone_cfg2(n_steps=n_steps)
+    rho = _rings(spec, 12)
     z = _zone(spec)
     S = z.forward(_dev(rho))
-    mon, des, _, S_ref = _oracle_forward_state(spec, rho)
-    assert _rel(z.monitor_dft().cpu().numpy(), mon) < FIELD_TOL
-    assert _rel(np.moveaxis(z.design_dft(0).cpu().numpy(), 4, 2), des) < FIELD_TOL
-    assert _rel(S, S_ref) < FIELD_TOL
+    mon = z.monitor_dft().cpu().numpy()
+    des = np.moveaxis(z.design_dft(0).cpu().numpy(), 4, 2)
+    grad = z.adjoint(4.0 * S).cpu().numpy()
+    one = spec.replace(n_phi=1, n_fold=spec.n_fold * spec.n_phi)
+    I1, g1, f1, _ = O.gradient(one, rho[:, :1])
+    g = O.Geometry(spec)
+    shift = np.exp(1j * g.phi_n)          # cell j is cell 0 rotated by j dphi
+    mon_ref = f1["mon"] * shift
+    assert _rel(mon, mon_ref) < FIELD_TOL
+    des_ref = f1["des"] * shift
+    assert _rel(des, des_ref) < FIELD_TOL
+    assert _rel(S, f1["S"]) < FIELD_TOL
+    assert _rel(grad, np.repeat(g1 / spec.n_phi, spec.n_phi, axis=1)) < GRAD_TOL
 
 
 # ------------------------------------------------------------------ errors
