@@ -201,6 +201,22 @@ zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi
 zda_status zda_zone_set_timing(zda_zone *zone, int every);
 zda_status zda_zone_timing(zda_zone *zone, double *h_ms_host, double *e_ms_host, long long *count_host);
 
+/* Density filter + projection without any device allocation (the paper has
+ * no counterpart: this exists for callers that cannot call cudaMalloc, e.g.
+ * a program whose device memory belongs to another framework's pool, or a
+ * loop that may not allocate once running).  Same result as
+ * zda_filter_project, but needs no context, zone or workspace: desc is the
+ * zone description (host), rho_dev [n_r_design][n_phi] the density and
+ * rho_tilde_dev the output (device, current device), stream a cudaStream_t.
+ * Scratch (the filter's per-row weight sums) is a fixed 64 KiB device array
+ * inside the library: n_r_design is limited to 16384 rows (ZDA_ERR_ARG
+ * beyond).  The first call on each device looks up that array's device
+ * address (with that device current); make that first call before any
+ * stream capture.  All calls on a device share the array: calls whose
+ * kernels overlap on the GPU race.  Allocates nothing. */
+zda_status zda_filter_project_noalloc(const zda_zone_desc *desc, const float *rho_dev, float *rho_tilde_dev,
+                                      void *stream);
+
 /* Thread-local message of the last error ("" if none). */
 const char *zda_last_error(void);
 

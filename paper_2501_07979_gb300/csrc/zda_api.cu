@@ -30,6 +30,8 @@ static zda_status fail(zda_status s, const std::string &msg)
     return s;
 }
 
+void zda_internal_set_error(const char *msg) { g_err = msg ? msg : ""; }
+
 #define CUDA_TRY(expr)                                                                         \
     do {                                                                                       \
         cudaError_t e_ = (expr);                                                               \

@@ -89,3 +89,6 @@ void launch_cell_gradient(const float *site_grad, int nr, int nphi, int nk, int 
 void launch_fill_status_check(const float *x, size_t n, int *status, cudaStream_t s);
 
 }  // namespace zda
+
+// Sets the calling thread's message returned by zda_last_error().
+void zda_internal_set_error(const char *msg);
