@@ -63,6 +63,10 @@ typedef struct zda_ctx zda_ctx;
 typedef struct zda_zone zda_zone;
 
 /* Zone descriptor (plain data, copied at zda_zone_create).
+ * n_fold = 0 selects continuous axisymmetry (the axis zone, section "Centimeter-
+ * scale metalens": the first zone is continuously axisymmetric): n_phi = 1,
+ * every (1/r) d/dphi is i m / r, r_lo >= 0 (r_lo = 0 puts the axis inside,
+ * then pml_r_in = 0); dt uses (m / max(r_lo, dr/2))^2 for the azimuthal term.
  * The simulated domain is r in [r_lo, r_lo + n_r dr], one wedge
  * phi in [0, 2 pi / n_fold) with n_phi cells (Bloch-periodic with phase
  * e^{i m 2pi/n_fold}), z in [0, n_z dz].  pml_* cells of CPML line the r and
@@ -183,12 +187,12 @@ zda_status zda_copy_design_dft(zda_zone *zone, int which, float *out_dev, void *
  * (for launch accounting in benchmarks). */
 long long zda_zone_launch_count(const zda_zone *zone);
 
-/* Time-step kernel of the zone.  variant 1 (default when n_z <= 256): one
- * fused launch per step (E and H updated together, ping-pong field buffers,
- * streaming along r; tile_phi in {2, 4} phi rows per thread block,
+/* Time-step kernel of the zone.  variant 0 (default): two launches per step
+ * (H update, E update), in place.  variant 1 (annular zones, n_z <= 256):
+ * one fused launch per step (E and H updated together, ping-pong field
+ * buffers, streaming along r; tile_phi in {2, 4} phi rows per thread block,
  * i_ranges radius ranges per phi tile, 0 = as many as fit in one wave).
- * variant 0: two launches per step (H update, E update), in place.  Both
- * compute the same scheme; results agree to FP32 rounding. */
+ * Both compute the same scheme; results agree to FP32 rounding. */
 zda_status zda_zone_set_kernel(zda_zone *zone, int variant, int tile_phi, int i_ranges);
 zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi, int *i_ranges);
 

@@ -61,6 +61,7 @@ class _Problem(ctypes.Structure):
         ("src_k", ctypes.c_int), ("n_src", ctypes.c_int),
         ("src_pat", ctypes.c_void_p), ("src_time", ctypes.c_void_p),
         ("n_freq", ctypes.c_int), ("twiddle", ctypes.c_void_p),
+        ("bor", ctypes.c_int), ("m", ctypes.c_int),
         ("mon_k", ctypes.c_int), ("mon_dft", ctypes.c_void_p),
         ("des_k0", ctypes.c_int), ("des_nk", ctypes.c_int), ("des_dft", ctypes.c_void_p),
         ("state", ctypes.c_void_p), ("nthreads", ctypes.c_int),
@@ -99,24 +100,39 @@ class Geometry:
     def __init__(self, spec):
         self.spec = spec
         s = spec
-        if s.n_fold <= 0 or s.r_lo <= 0:
-            raise ValueError("annular zones only (n_fold > 0, r_lo > 0)")
+        self.bor = s.n_fold == 0
+        if self.bor:
+            # continuous axisymmetry (the axis zone): one phi cell, d/dphi -> i m
+            if s.n_phi != 1 or s.r_lo < 0:
+                raise ValueError("continuous axisymmetry needs n_phi = 1 and r_lo >= 0")
+        elif s.n_fold < 0 or s.r_lo <= 0:
+            raise ValueError("annular wedge zones need n_fold > 0 and r_lo > 0")
         self.nr, self.nphi, self.nz = s.n_r, s.n_phi, s.n_z
         self.dr, self.dz = s.dr, s.dz
-        self.tau = 2.0 * math.pi / s.n_fold
+        self.tau = 2.0 * math.pi / (1 if self.bor else s.n_fold)
         self.dphi = self.tau / s.n_phi
         self.r_n = s.r_lo + s.dr * np.arange(s.n_r + 1)          # r_i
         self.r_h = s.r_lo + s.dr * (np.arange(s.n_r) + 0.5)       # r_{i+1/2}
-        r_min = s.r_lo
-        self.dt = s.courant / math.sqrt(1.0 / s.dr ** 2 + 1.0 / (r_min * self.dphi) ** 2
-                                        + 1.0 / s.dz ** 2)
+        if self.bor:
+            # the im/r terms act at r >= r_lo + dr/2 (no phi-difference): the
+            # smallest radius plays the part of r dphi in the Courant bound
+            r_min = s.r_lo if s.r_lo > 0 else 0.5 * s.dr
+            self.dt = s.courant / math.sqrt(1.0 / s.dr ** 2 + (s.m / r_min) ** 2 + 1.0 / s.dz ** 2)
+        else:
+            r_min = s.r_lo
+            self.dt = s.courant / math.sqrt(1.0 / s.dr ** 2 + 1.0 / (r_min * self.dphi) ** 2
+                                            + 1.0 / s.dz ** 2)
         self.bloch = complex(math.cos(s.m * self.tau), math.sin(s.m * self.tau))
         self.i_d0 = s.pml_r_in
         self.i_d1 = s.n_r - s.pml_r_out
         self.r0 = s.r_lo + self.i_d0 * s.dr          # design / monitor annulus
         self.r1 = s.r_lo + self.i_d1 * s.dr
-        self.phi_n = self.dphi * np.arange(s.n_phi)               # phi_j
-        self.phi_h = self.dphi * (np.arange(s.n_phi) + 0.5)       # phi_{j+1/2}
+        if self.bor:                                              # u-form: no phase
+            self.phi_n = np.zeros(1)
+            self.phi_h = np.zeros(1)
+        else:
+            self.phi_n = self.dphi * np.arange(s.n_phi)           # phi_j
+            self.phi_h = self.dphi * (np.arange(s.n_phi) + 0.5)   # phi_{j+1/2}
         lam = np.asarray(s.wavelengths, dtype=np.float64)
         w = 2.0 * math.pi / lam
         self.omega = np.concatenate([w, -w])        # signed frequency list, +w first
@@ -393,7 +409,7 @@ def run(spec, geom, eps, n_steps=None, pml=None, src_pat=None, src_time=None, sr
         n_freq=nf, twiddle=_ptr(twiddle),
         mon_k=(mon_k if mon is not None else -1), mon_dft=_ptr(mon),
         des_k0=geom.des_k0, des_nk=(geom.des_nk if des is not None else 0), des_dft=_ptr(des),
-        state=_ptr(state), nthreads=int(nthreads))
+        state=_ptr(state), nthreads=int(nthreads), bor=int(geom.bor), m=int(s.m))
     rc = _lib().orc_run(ctypes.byref(P))
     if rc != 0:
         raise RuntimeError("oracle time loop failed: %d" % rc)
@@ -446,7 +462,7 @@ def focal_weights(spec, geom):
         def G(r):
             R = np.sqrt(zf * zf + r * r)
             K = (1 / (2 * math.pi)) * (zf / R) * (1 / R - 1j * kk) * np.exp(1j * kk * R) / R
-            return 0.5 * s.n_fold * K * r * geom.dphi
+            return 0.5 * (1 if geom.bor else s.n_fold) * K * r * geom.dphi
 
         gr = G(geom.r_h) * qr
         gp = G(geom.r_n[:s.n_r]) * qp
@@ -545,8 +561,9 @@ def adjoint(spec, fwd, dI_dS, nthreads=0):
     a_r = np.conj(g)[:, None, None] * wr
     a_p = np.conj(g)[:, None, None] * wp
     b_r = 1j * np.conj(a_r) / (wt[:, None, None] * Vr[None])
-    b_p = 1j * np.conj(a_p) / (wt[:, None, None] * Vp[None])
-    b_p[:, 0, :] = 0.0                                 # E_phi on the PEC wall r_lo
+    with np.errstate(invalid="ignore", divide="ignore"):       # V = 0 on the axis
+        b_p = 1j * np.conj(a_p) / (wt[:, None, None] * Vp[None])
+    b_p[:, 0, :] = 0.0                                 # E_phi on the PEC wall r_lo (or the axis)
     pat = np.stack([b_r, b_p], axis=1)                 # [q][2][nr][nphi]
     src_t = adjoint_pulse_matrix(s, geom, n)
     _, des_a, _ = run(s, geom, fwd["eps"], n_steps=n, src_pat=pat, src_time=src_t, src_k=k,

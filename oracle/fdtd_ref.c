@@ -27,6 +27,13 @@
  *  - The source current J enters the E update as E += dt/eps (curl H - J)
  *    on the E_r and E_phi sites of one z-plane at t_{n+1/2}.
  *  - DFT: X(w) += E^{n+1} e^{i w t_{n+1}} dt after each E update.
+ *  - Continuous axisymmetry (bor != 0, the axis zone): one phi cell, the
+ *    fields are the m-th azimuthal harmonic u and every (1/r) d/dphi is
+ *    exactly i m / r (Eq. 5 with the phi-dependence removed).  With r_lo = 0
+ *    the axis r = 0 carries E_phi, E_z and H_r sites; for |m| = 1 E_z = 0 there
+ *    and E_phi, H_r on the axis enter every other update multiplied by r = 0,
+ *    so they are left at zero (they affect no other field, no DFT weight and
+ *    no gradient: all carry the factor r).
  *
  * Array layout: every field is complex double [nr][nphi][nz] (z fastest).
  */
@@ -52,6 +59,8 @@ typedef struct {
     const double *src_time;   /* complex [n_steps][n_src], value at t_{n+1/2} */
     int n_freq;
     const double *twiddle;    /* complex [n_steps][n_freq] = e^{i w t_{n+1}} dt */
+    int bor;                  /* 1: continuous axisymmetry, d/dphi -> i m */
+    int m;                    /* azimuthal order for bor */
     int mon_k;                /* < 0: no monitor DFT */
     double *mon_dft;          /* complex [n_freq][2][nr][nphi] (E_r, E_phi) */
     int des_k0, des_nk;       /* des_nk == 0: no design-volume DFT */
@@ -113,9 +122,10 @@ int orc_run(const orc_problem *p)
                     const cplx ez_ip = (i + 1 < nr) ? AT(Ez, i + 1, j, k) : 0.0;
                     const cplx ep_ip = (i + 1 < nr) ? AT(Ep, i + 1, j, k) : 0.0;
 
-                    /* H_r at (r_i, phi_{j+1/2}, z_{k+1/2}) */
-                    {
-                        cplx d_phi = (ez_jp - AT(Ez, i, j, k)) / (r_n[i] * dphi);
+                    /* H_r at (r_i, phi_{j+1/2}, z_{k+1/2}); on the axis it stays 0 */
+                    if (r_n[i] > 0.0) {
+                        cplx d_phi = p->bor ? I * p->m * AT(Ez, i, j, k) / r_n[i]
+                                            : (ez_jp - AT(Ez, i, j, k)) / (r_n[i] * dphi);
                         cplx d_z = (ep_kp - AT(Ep, i, j, k)) / dz;
                         cplx *ps = &AT(f + PS_HR_Z * ncell, i, j, k);
                         *ps = p->bz_h[k] * *ps + p->cz_h[k] * d_z;
@@ -134,7 +144,8 @@ int orc_run(const orc_problem *p)
                     /* H_z at (r_{i+1/2}, phi_{j+1/2}, z_k) */
                     {
                         cplx d_r = (r_n[i + 1] * ep_ip - r_n[i] * AT(Ep, i, j, k)) / (r_h[i] * dr);
-                        cplx d_phi = (er_jp - AT(Er, i, j, k)) / (r_h[i] * dphi);
+                        cplx d_phi = p->bor ? I * p->m * AT(Er, i, j, k) / r_h[i]
+                                            : (er_jp - AT(Er, i, j, k)) / (r_h[i] * dphi);
                         cplx *ps = &AT(f + PS_HZ_R * ncell, i, j, k);
                         *ps = p->br_h[i] * *ps + p->cr_h[i] * d_r;
                         AT(Hz, i, j, k) -= dt * ((d_r + *ps) - d_phi);
@@ -160,7 +171,8 @@ int orc_run(const orc_problem *p)
 
                     /* E_r at (r_{i+1/2}, phi_j, z_k); PEC at k = 0 */
                     if (k > 0) {
-                        cplx d_phi = (AT(Hz, i, j, k) - hz_jm) / (r_h[i] * dphi);
+                        cplx d_phi = p->bor ? I * p->m * AT(Hz, i, j, k) / r_h[i]
+                                            : (AT(Hz, i, j, k) - hz_jm) / (r_h[i] * dphi);
                         cplx d_z = (AT(Hp, i, j, k) - AT(Hp, i, j, k - 1)) / dz;
                         cplx *ps = &AT(f + PS_ER_Z * ncell, i, j, k);
                         *ps = p->bz_n[k] * *ps + p->cz_n[k] * d_z;
@@ -179,7 +191,8 @@ int orc_run(const orc_problem *p)
                     /* E_z at (r_i, phi_j, z_{k+1/2}); PEC at i = 0 */
                     if (i > 0) {
                         cplx d_r = (r_h[i] * AT(Hp, i, j, k) - r_h[i - 1] * AT(Hp, i - 1, j, k)) / (r_n[i] * dr);
-                        cplx d_phi = (AT(Hr, i, j, k) - hr_jm) / (r_n[i] * dphi);
+                        cplx d_phi = p->bor ? I * p->m * AT(Hr, i, j, k) / r_n[i]
+                                            : (AT(Hr, i, j, k) - hr_jm) / (r_n[i] * dphi);
                         cplx *ps = &AT(f + PS_EZ_R * ncell, i, j, k);
                         *ps = p->br_n[i] * *ps + p->cr_n[i] * d_r;
                         AT(Ez, i, j, k) += dt / AT(p->eps_z, i, j, k) * ((d_r + *ps) - d_phi);

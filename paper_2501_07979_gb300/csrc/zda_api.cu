@@ -70,8 +70,8 @@ struct zda_zone {
     bool have_forward = false;
     bool adjoint_ok = false;        // the broadband adjoint pulse matrix was invertible
     long long launches = 0;
-    // time-step kernel: 0 = split H/E launches, 1 = fused single launch
-    int variant = 1, tile_phi = 2, i_ranges = 0;
+    // time-step kernel: 0 = split H/E launches (default), 1 = fused single launch
+    int variant = 0, tile_phi = 2, i_ranges = 0;
     int last_parity = 0;            // fused runs: which buffer holds the final fields
     // optional CUDA-event timing of every `time_every`-th H/E launch pair
     int time_every = 0;
@@ -248,7 +248,10 @@ static zda_status upload(zda_zone &z)
     };
     // radii
     std::vector<float> irn(nr + 1), irh(nr);
-    for (int i = 0; i <= nr; ++i) irn[i] = (float)(1.0 / (d.r_lo + i * d.dr));
+    for (int i = 0; i <= nr; ++i) {
+        const double r = d.r_lo + i * d.dr;
+        irn[i] = r > 0 ? (float)(1.0 / r) : 0.f;        // axis: the 1/r terms vanish there
+    }
     for (int i = 0; i < nr; ++i) irh[i] = (float)(1.0 / (d.r_lo + (i + 0.5) * d.dr));
     CUDA_TRY(put(z.L.inv_r_n, irn.data(), irn.size() * 4));
     CUDA_TRY(put(z.L.inv_r_h, irh.data(), irh.size() * 4));
@@ -297,12 +300,14 @@ static zda_status upload(zda_zone &z)
     {
         std::vector<float2> pn(np), ph(np);
         std::vector<double2> en(np), eh(np);
+        const bool bor = d.n_fold == 0;       // u-form: no azimuthal phase
         for (int j = 0; j < np; ++j) {
-            const double a = d.m * j * z.dphi, b = d.m * (j + 0.5) * z.dphi;
+            const double a = bor ? 0.0 : d.m * j * z.dphi, b = bor ? 0.0 : d.m * (j + 0.5) * z.dphi;
             pn[j] = make_float2((float)std::cos(a), (float)std::sin(a));
             ph[j] = make_float2((float)std::cos(b), (float)std::sin(b));
-            en[j] = make_double2(std::cos(j * z.dphi), -std::sin(j * z.dphi));
-            eh[j] = make_double2(std::cos((j + 0.5) * z.dphi), -std::sin((j + 0.5) * z.dphi));
+            const double pn_ = bor ? 0.0 : j * z.dphi, ph_ = bor ? 0.0 : (j + 0.5) * z.dphi;
+            en[j] = make_double2(std::cos(pn_), -std::sin(pn_));
+            eh[j] = make_double2(std::cos(ph_), -std::sin(ph_));
         }
         CUDA_TRY(put(z.L.ph_n, pn.data(), np * 8));
         CUDA_TRY(put(z.L.ph_h, ph.data(), np * 8));
@@ -379,7 +384,7 @@ static zda_status upload(zda_zone &z)
             auto G = [&](double r) {
                 const double R = std::sqrt(zf * zf + r * r);
                 const cd K = (1.0 / (2 * M_PI)) * (zf / R) * (1.0 / R - cd(0, kk)) * std::exp(cd(0, kk * R)) / R;
-                return 0.5 * d.n_fold * K * r * z.dphi;
+                return 0.5 * (d.n_fold == 0 ? 1 : d.n_fold) * K * r * z.dphi;
             };
             const bool neg = q >= (int)z.lambda.size();
             for (int i = 0; i < nr; ++i) {
@@ -407,8 +412,13 @@ static zda_status upload(zda_zone &z)
 static zda_status derive(zda_zone &z)
 {
     const zda_zone_desc &d = z.d;
-    if (d.n_r < 2 || d.n_phi < 1 || d.n_z < 2 || d.n_fold < 1 || d.dr <= 0 || d.dz <= 0 || d.r_lo <= 0)
-        return fail(ZDA_ERR_ARG, "annular zone needs n_r>=2, n_phi>=1, n_z>=2, n_fold>=1, dr,dz>0, r_lo>0");
+    const bool bor = d.n_fold == 0;
+    if (d.n_r < 2 || d.n_phi < 1 || d.n_z < 2 || d.n_fold < 0 || d.dr <= 0 || d.dz <= 0)
+        return fail(ZDA_ERR_ARG, "zone needs n_r>=2, n_phi>=1, n_z>=2, n_fold>=0, dr,dz>0");
+    if (bor && (d.n_phi != 1 || d.r_lo < 0))
+        return fail(ZDA_ERR_ARG, "continuous axisymmetry (n_fold = 0) needs n_phi = 1 and r_lo >= 0");
+    if (!bor && d.r_lo <= 0) return fail(ZDA_ERR_ARG, "a wedge zone (n_fold > 0) needs r_lo > 0");
+    if (d.r_lo == 0 && d.pml_r_in != 0) return fail(ZDA_ERR_ARG, "the axis zone has no inner r-PML");
     if (d.pml_r_in < 0 || d.pml_r_out < 0 || d.pml_z < 0 || d.pml_r_in + d.pml_r_out >= d.n_r ||
         2 * d.pml_z >= d.n_z)
         return fail(ZDA_ERR_ARG, "PML widths do not fit the grid");
@@ -421,9 +431,15 @@ static zda_status derive(zda_zone &z)
     if (d.eps_lo <= 0 || d.eps_hi <= 0) return fail(ZDA_ERR_ARG, "permittivities must be positive");
     for (int l = 0; l < d.n_layers; ++l)
         if (d.layer_eps[l] <= 0) return fail(ZDA_ERR_ARG, "layer permittivities must be positive");
-    z.tau = 2 * M_PI / d.n_fold;
+    z.tau = 2 * M_PI / (bor ? 1 : d.n_fold);
     z.dphi = z.tau / d.n_phi;
-    z.dt = d.courant / std::sqrt(1.0 / (d.dr * d.dr) + 1.0 / std::pow(d.r_lo * z.dphi, 2) + 1.0 / (d.dz * d.dz));
+    if (bor) {
+        // the i m / r terms act from r_lo (or dr/2 on the axis) outwards
+        const double rmin = d.r_lo > 0 ? d.r_lo : 0.5 * d.dr;
+        z.dt = d.courant / std::sqrt(1.0 / (d.dr * d.dr) + std::pow(d.m / rmin, 2) + 1.0 / (d.dz * d.dz));
+    } else {
+        z.dt = d.courant / std::sqrt(1.0 / (d.dr * d.dr) + 1.0 / std::pow(d.r_lo * z.dphi, 2) + 1.0 / (d.dz * d.dz));
+    }
     z.nq = 2 * (int)z.lambda.size();
     z.i_d0 = d.pml_r_in;
     z.i_d1 = d.n_r - d.pml_r_out;
@@ -436,7 +452,7 @@ static zda_status derive(zda_zone &z)
     } else {
         z.di_max = z.dj_max = 0;
     }
-    if (d.n_z > zda::fused_max_nz()) z.variant = 0;
+    if (d.n_z > zda::fused_max_nz() || bor) z.variant = 0;
     compute_layout(z);
     z.tables_dirty = true;
     z.have_forward = false;
@@ -461,6 +477,8 @@ static zda::StepParams step_params(zda_zone &z)
     StepParams p{};
     p.nr = d.n_r; p.nphi = d.n_phi; p.nz = d.n_z;
     p.pr_in = d.pml_r_in; p.pr_out = d.pml_r_out; p.pz = d.pml_z;
+    p.bor = d.n_fold == 0 ? 1 : 0;
+    p.m = (float)d.m;
     p.dt = (float)z.dt;
     p.inv_dr = (float)(1.0 / d.dr); p.inv_dz = (float)(1.0 / d.dz); p.inv_dphi = (float)(1.0 / z.dphi);
     const double ph = d.m * z.tau;
@@ -904,6 +922,7 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
 {
     if (!z || (variant != 0 && variant != 1) || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
     if (variant == 1) {
+        if (z->d.n_fold == 0) return fail(ZDA_ERR_ARG, "the axis zone (continuous axisymmetry) uses the split step");
         if (tile_phi != 2 && tile_phi != 4) return fail(ZDA_ERR_ARG, "fused step: tile_phi must be 2 or 4");
         if (z->d.n_z > zda::fused_max_nz()) return fail(ZDA_ERR_ARG, "fused step supports n_z <= 256");
     }

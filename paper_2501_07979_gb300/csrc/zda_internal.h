@@ -22,6 +22,36 @@ __host__ __device__ __forceinline__ float2 c_fma(float2 a, float2 b, float2 acc)
 }
 __host__ __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
 
+#ifdef __CUDACC__
+// Running-DFT update X_q += E_c w_q for nc components at stride `comp`,
+// frequencies at stride `qstride`: each chunk of frequencies loads all its
+// accumulators before any store, so the read-modify-writes overlap instead
+// of serialising on possible aliasing.
+template <int NC, int CH = 4>
+__device__ __forceinline__ void dft_update(float2 *d, size_t qstride, size_t comp, const float2 *tw, int nq,
+                                           const float2 (&e)[NC])
+{
+    for (int q0 = 0; q0 < nq; q0 += CH) {
+        float2 v[CH][NC], w[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            if (q0 + u < nq) {
+                w[u] = tw[q0 + u];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) v[u][c] = d[(size_t)(q0 + u) * qstride + c * comp];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            if (q0 + u < nq) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) d[(size_t)(q0 + u) * qstride + c * comp] = c_fma(e[c], w[u], v[u][c]);
+            }
+        }
+    }
+}
+#endif
+
 // Per-position coefficient tables (device pointers into the workspace).
 struct Tables {
     const float *inv_r_n, *inv_r_h;            // 1/r_i (n_r+1), 1/r_{i+1/2} (n_r)
@@ -42,6 +72,8 @@ enum { SRC_NONE = 0, SRC_PLANE_WAVE = 1, SRC_ADJOINT = 2 };
 struct StepParams {
     int nr, nphi, nz;
     int pr_in, pr_out, pz;
+    int bor;                                   // continuous axisymmetry: (1/r) d/dphi -> i m / r
+    float m;
     float dt, inv_dr, inv_dz, inv_dphi;
     float2 bloch, bloch_inv;                   // e^{+-i m tau}
     Fields f;

@@ -10,6 +10,12 @@
 // L1 and the i neighbours from L2.  CPML auxiliaries live only in the PML
 // slabs; the plane-wave / adjoint sources and the running DFTs are fused
 // into the E update.
+//
+// Continuous axisymmetry (the axis zone, one phi cell): every (1/r) d/dphi
+// is i m / r times the local value.  On the axis (r_lo = 0) the table entry
+// 1/r_0 is 0, so H_r(0) keeps its value 0; E_z(0) and E_phi(0) are not
+// updated (E_z vanishes on the axis for |m| = 1 and E_phi(0), H_r(0) enter the
+// other updates multiplied by r = 0).
 #include "zda_internal.h"
 
 namespace zda {
@@ -63,7 +69,8 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_h(const StepParams p
 
     // H_r(i, j+1/2, k+1/2): (1/r) dE_z/dphi - dE_phi/dz
     {
-        const float2 dph = c_scale(c_sub(ez_jp, ez), irn * p.inv_dphi);
+        const float2 dph = p.bor ? c_scale(make_float2(-ez.y, ez.x), p.m * irn)
+                                 : c_scale(c_sub(ez_jp, ez), irn * p.inv_dphi);
         float2 dz = c_scale(c_sub(ep_kp, ep), p.inv_dz);
         if (kz >= 0) {
             const size_t ix = ((size_t)i * nphi + j) * (2 * p.pz) + kz;
@@ -97,7 +104,8 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_h(const StepParams p
     //   (r_{i+1} E(i+1) - r_i E(i)) / (r_{i+1/2} dr) = (E(i+1)-E(i))/dr + (E(i+1)+E(i)) / (2 r_{i+1/2})
     {
         float2 drr = c_add(c_scale(c_sub(ep_ip, ep), p.inv_dr), c_scale(c_add(ep_ip, ep), 0.5f * irh));
-        const float2 dph = c_scale(c_sub(er_jp, er), irh * p.inv_dphi);
+        const float2 dph = p.bor ? c_scale(make_float2(-er.y, er.x), p.m * irh)
+                                 : c_scale(c_sub(er_jp, er), irh * p.inv_dphi);
         if (ir >= 0) {
             const size_t ix = ((size_t)ir * nphi + j) * nz + k;
             float2 ps = c_add(c_scale(p.psi.hz_r[ix], __ldg(p.t.br_h + i)), c_scale(drr, __ldg(p.t.cr_h + i)));
@@ -167,7 +175,8 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_e(const StepParams p
     float2 er = p.f.Er[c], ep = p.f.Ep[c], ez = p.f.Ez[c];
     // E_r(i+1/2, j, k): (1/r) dH_z/dphi - dH_phi/dz ; PEC at k = 0
     if (k > 0) {
-        const float2 dph = c_scale(c_sub(hz, hz_jm), irh * p.inv_dphi);
+        const float2 dph = p.bor ? c_scale(make_float2(-hz.y, hz.x), p.m * irh)
+                                 : c_scale(c_sub(hz, hz_jm), irh * p.inv_dphi);
         float2 dz = c_scale(c_sub(hp, hp_km), p.inv_dz);
         if (kz >= 0) {
             const size_t ix = ij * (2 * p.pz) + kz;
@@ -203,7 +212,8 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_e(const StepParams p
     //   (r_{i+1/2} H(i+1/2) - r_{i-1/2} H(i-1/2)) / (r_i dr) = (H - H_im)/dr + (H + H_im) / (2 r_i)
     if (i > 0) {
         float2 drr = c_add(c_scale(c_sub(hp, hp_im), p.inv_dr), c_scale(c_add(hp, hp_im), 0.5f * irn));
-        const float2 dph = c_scale(c_sub(hr, hr_jm), irn * p.inv_dphi);
+        const float2 dph = p.bor ? c_scale(make_float2(-hr.y, hr.x), p.m * irn)
+                                 : c_scale(c_sub(hr, hr_jm), irn * p.inv_dphi);
         if (ir >= 0) {
             const size_t ix = ((size_t)ir * nphi + j) * nz + k;
             float2 ps = c_add(c_scale(p.psi.ez_r[ix], __ldg(p.t.br_n + i)), c_scale(drr, __ldg(p.t.cr_n + i)));
@@ -217,29 +227,16 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_e(const StepParams p
 
     // running DFTs of E^{n+1}
     if (p.mon && k == p.mon_k) {
-        const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
         const size_t plane = (size_t)nr * nphi;
-        for (int q = 0; q < p.nq; ++q) {
-            const float2 w = tw[q];
-            float2 *m0 = p.mon + ((size_t)q * 2) * plane + ij;
-            float2 *m1 = m0 + plane;
-            *m0 = c_fma(er, w, *m0);
-            *m1 = c_fma(ep, w, *m1);
-        }
+        const float2 e2[2] = {er, ep};
+        dft_update<2>(p.mon + ij, 2 * plane, plane, p.t.twiddle + (size_t)n * p.nq, p.nq, e2);
     }
     if (p.des) {
         const int kk = k - p.des_k0;
         if (kk >= 0 && kk < p.des_nk) {
-            const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
             const size_t comp = (size_t)nr * nphi * p.des_nk;
-            float2 *d = p.des + ij * p.des_nk + kk;
-            for (int q = 0; q < p.nq; ++q) {
-                const float2 w = tw[q];
-                float2 *d0 = d + (size_t)q * 3 * comp;
-                d0[0] = c_fma(er, w, d0[0]);
-                d0[comp] = c_fma(ep, w, d0[comp]);
-                d0[2 * comp] = c_fma(ez, w, d0[2 * comp]);
-            }
+            const float2 e3[3] = {er, ep, ez};
+            dft_update<3>(p.des + ij * p.des_nk + kk, 3 * comp, comp, p.t.twiddle + (size_t)n * p.nq, p.nq, e3);
         }
     }
 }

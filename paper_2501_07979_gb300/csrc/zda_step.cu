@@ -294,25 +294,14 @@ __global__ void __launch_bounds__(32 * NKW, (NKW <= 2) ? 4 : 2) k_fused_step(con
                 p.oEz[c] = ez;
 
                 if (in_mon) {
-                    const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
-                    for (int q = 0; q < p.nq; ++q) {
-                        const float2 wq = tw[q];
-                        float2 *m0 = p.mon + ((size_t)q * 2) * plane + ij;
-                        *m0 = c_fma(er, wq, *m0);
-                        m0[plane] = c_fma(ep, wq, m0[plane]);
-                    }
+                    const float2 e2[2] = {er, ep};
+                    dft_update<2, 2>(p.mon + ij, 2 * plane, plane, p.t.twiddle + (size_t)n * p.nq, p.nq, e2);
                 }
                 if (in_des) {
-                    const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
                     const size_t comp = plane * p.des_nk;
-                    float2 *d = p.des + ij * p.des_nk + dkk;
-                    for (int q = 0; q < p.nq; ++q) {
-                        const float2 wq = tw[q];
-                        float2 *d0 = d + (size_t)q * 3 * comp;
-                        d0[0] = c_fma(er, wq, d0[0]);
-                        d0[comp] = c_fma(ep, wq, d0[comp]);
-                        d0[2 * comp] = c_fma(ez, wq, d0[2 * comp]);
-                    }
+                    const float2 e3[3] = {er, ep, ez};
+                    dft_update<3, 2>(p.des + ij * p.des_nk + dkk, 3 * comp, comp, p.t.twiddle + (size_t)n * p.nq,
+                                  p.nq, e3);
                 }
             }
         }

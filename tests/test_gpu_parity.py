@@ -259,6 +259,29 @@ def test_wide_zone_full_size_against_one_cell_wedge(n_steps):
     assert _rel(grad, np.repeat(g1 / spec.n_phi, spec.n_phi, axis=1)) < GRAD_TOL
 
 
+# ------------------------------------------------------------------ axis zone
+AXIS = zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0, n_steps=700, filter_radius=0.25, beta=4.0,
+                 wavelengths=(0.9, 1.1), pulse_sigma=0.4, pulse_t0=1.6)
+
+
+def test_axis_zone_forward_and_gradient_match_oracle():
+    """Continuous axisymmetry with the axis inside (the innermost zone of a
+    lens): forward DFTs, fields, phasors and the adjoint gradient."""
+    spec = AXIS
+    rho = smoothed_rho(spec.n_r_design, 1, 8, mode="minmax")
+    z = _zone(spec)
+    assert z.get_kernel()[0] == 0                      # split step
+    S = z.forward(_dev(rho))
+    mon, des, st, S_ref = _oracle_forward_state(spec, rho)
+    assert _rel(z.monitor_dft().cpu().numpy(), mon) < FIELD_TOL
+    assert _rel(np.moveaxis(z.design_dft(0).cpu().numpy(), 4, 2), des) < FIELD_TOL
+    assert _rel(z.fields().cpu().numpy(), st[:6]) < FIELD_TOL
+    assert _rel(S, S_ref) < FIELD_TOL
+    grad = z.adjoint(4.0 * S).cpu().numpy()
+    _, g_ref, _, _ = O.gradient(spec, rho)
+    assert _rel(grad, g_ref) < GRAD_TOL
+
+
 # ------------------------------------------------------------------ errors
 def test_adjoint_before_forward_is_a_state_error():
     from paper_2501_07979_gb300 import ZdaError

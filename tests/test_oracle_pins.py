@@ -388,3 +388,77 @@ def test_cfg1_geometry():
     assert abs(s.r_lo * g.dphi - 2 * math.pi / 96 / 48 * 10) < 1e-15
     assert abs(g.dt - 0.5 / math.sqrt(2 / 0.05 ** 2 + 1 / (10 * g.dphi) ** 2)) < 1e-15
     assert abs(g.dt - 6.361e-3) < 1e-6
+
+
+# ---------------------------------------------------------------- axis zone (continuous axisymmetry)
+def _cylinder_error(dr, mode, a=1.0, d=1.0, n_steps=2500):
+    """Full PEC cylinder r in [0, a] in the continuous-axisymmetry (axis
+    zone) mode, m = 1: lowest TM_{1,1,0} (J_1 zero) / TE_{1,1,1} (J_1' zero)."""
+    nr = int(round(a / dr))
+    nz = 2 if mode == "TM" else int(round(d / dr))
+    s = _pec_spec(r_lo=0.0, n_r=nr, n_phi=1, n_z=nz, n_fold=0, dr=dr, dz=(dr if mode == "TM" else d / nz))
+    g = O.Geometry(s)
+    st = np.zeros((O.N_STATE, nr, 1, nz), complex)
+    if mode == "TM":
+        k = sp.jn_zeros(1, 1)[0] / a
+        prof = sp.jv(1, k * g.r_n[:nr])
+        prof[0] = 0
+        st[2] = prof[:, None, None] * np.ones((1, 1, nz))
+        w2, comp, site = k * k, 2, (nr // 3, 0, 0)
+    else:
+        k = sp.jnp_zeros(1, 1)[0] / a
+        kz = 2 / s.dz * math.sin(math.pi * s.dz / (2 * d))
+        sz = np.sin(math.pi * s.dz * np.arange(nz) / d)[None, None, :]
+        Rh = sp.jv(1, k * g.r_h)
+        dR = np.zeros(nr)
+        dR[1:] = (Rh[1:] - Rh[:-1]) / dr
+        st[0] = (1j / g.r_h * Rh)[:, None, None] * sz
+        st[1] = (-dR)[:, None, None] * sz
+        w2, comp, site = k * k + kz * kz, 1, (nr // 3, 0, nz // 2)
+    eps = [np.ones((nr, 1, nz))] * 3
+    sig = np.empty(n_steps, complex)
+    for n in range(n_steps):
+        _, _, st = O.run(s, g, eps, n_steps=1, pml=O.no_pml(s), state=st)
+        sig[n] = st[comp][site]
+    A = np.stack([sig[1:-1], np.ones(n_steps - 2)], axis=1)
+    c = np.linalg.lstsq(A, sig[2:] + sig[:-2], rcond=None)[0][0].real
+    return ((2 - c) / g.dt ** 2 - w2) / w2
+
+
+def test_axis_zone_cylinder_resonances():
+    e1, e2 = _cylinder_error(0.05, "TM"), _cylinder_error(0.025, "TM")
+    assert abs(e1) < 3e-3 and 3.5 < e1 / e2 < 4.5, (e1, e2)
+    assert abs(_cylinder_error(0.05, "TE")) < 1e-4
+
+
+def test_axis_zone_energy_conserved():
+    """Axis zone with PEC walls: leap-frog energy with the r-weighted volumes
+    (the on-axis sites weigh zero) is conserved."""
+    s = _pec_spec(r_lo=0.0, n_r=12, n_phi=1, n_z=10, n_fold=0, dr=0.1, dz=0.1)
+    g = O.Geometry(s)
+    rng = np.random.default_rng(1)
+    sh = (6, s.n_r, 1, s.n_z)
+    st = np.zeros((O.N_STATE, s.n_r, 1, s.n_z), complex)
+    st[:6] = rng.standard_normal(sh) + 1j * rng.standard_normal(sh)
+    st = _enforce_pec(st)
+    eps = tuple(1.0 + rng.random((s.n_r, 1, s.n_z)) for _ in range(3))
+    VE, VH = _volumes(s, g)
+    W = []
+    for n in range(300):
+        E, Hm = st[:3].copy(), st[3:6].copy()
+        _, _, st = O.run(s, g, eps, n_steps=1, pml=O.no_pml(s), state=st)
+        W.append(sum((eps[c] * VE[c] * abs(E[c]) ** 2).sum() for c in range(3))
+                 + sum((VH[c] * np.real(np.conj(Hm[c]) * st[3 + c])).sum() for c in range(3)))
+    W = np.array(W)
+    assert np.abs(W / W[0] - 1).max() < 1e-12
+
+
+def test_axis_zone_adjoint_matches_central_differences():
+    """The hybrid adjoint in the axis zone (continuous axisymmetry, r_lo = 0):
+    directional derivative along the gradient and a few pixels."""
+    spec = zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0, n_steps=2400, courant=0.9,
+                     filter_radius=0.25, beta=4.0, wavelengths=(0.9, 1.1), pulse_sigma=0.4,
+                     pulse_t0=1.6, eps_hi=2.1)
+    assert _directional_error(spec) < 1e-3
+    errs = _fd_errors(spec, [(0, 0), (3, 0), (9, 0), (15, 0)])
+    assert errs.max() < 2e-3, errs
