@@ -147,7 +147,8 @@ zda_status zda_forward(zda_zone *zone, const float *rho_dev, double *focal_out_h
 /* Adjoint run (second FDTD run) and gradient: dI_dfocal_host holds n_freq
  * complex doubles (dI/dRe S_q, dI/dIm S_q) for any real objective I(S);
  * grad_rho_dev [n_r_design][n_phi] floats receives dI/drho.  Requires a
- * preceding zda_forward with the same rho (ZDA_ERR_STATE otherwise). */
+ * preceding zda_forward with the same rho (ZDA_ERR_STATE otherwise).  With
+ * the fused step it synchronises the stream to report wait timeouts. */
 zda_status zda_adjoint(zda_zone *zone, const double *dI_dfocal_host, float *grad_rho_dev, void *stream);
 
 /* One TopOpt iteration of the summed focal intensity I = 2 sum |S_q|^2:
@@ -196,9 +197,18 @@ long long zda_zone_launch_count(const zda_zone *zone);
 zda_status zda_zone_set_kernel(zda_zone *zone, int variant, int tile_phi, int i_ranges);
 zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi, int *i_ranges);
 
+/* The fused step (variant 1) waits on shared-memory barriers for its staged
+ * copies; every wait gives up after `polls` polls (default 4194304), sets an
+ * error word and lets the kernel finish, and the call then returns
+ * ZDA_ERR_TIMEOUT (zda_forward, zda_adjoint and zda_iteration synchronise
+ * their stream to read it).  inject_timeout != 0 is for tests of that path:
+ * each radius also waits on a barrier that nothing completes. */
+zda_status zda_zone_set_wait_limit(zda_zone *zone, int polls, int inject_timeout);
+
 /* Kernel timing with CUDA events recorded on the launching stream: with
- * every > 0, every every-th time step's H-update and E-update launches are
- * bracketed by events (a ring of 64 samples; the host waits for a sample
+ * every > 0, every every-th time step's two main launches are bracketed by
+ * events (split step: the H update and the E update; fused step: the
+ * streaming E/H kernel and the DFT kernel) (a ring of 64 samples; the host waits for a sample
  * 64 samples old before reusing its slot).  every = 0 turns it off.
  * zda_zone_timing waits for pending samples and returns the summed
  * durations (ms) and the number of sampled launch pairs, then resets. */

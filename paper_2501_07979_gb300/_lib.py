@@ -76,6 +76,7 @@ SIGNATURES = {
     "zda_zone_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_zone_set_kernel": (_i, [_vp, _i, _i, _i]),
     "zda_zone_get_kernel": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "zda_zone_set_wait_limit": (_i, [_vp, _i, _i]),
     "zda_zone_set_timing": (_i, [_vp, _i]),
     "zda_zone_timing": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "zda_filter_project_noalloc": (_i, [ctypes.POINTER(ZoneDesc), _vp, _vp, _vp]),

@@ -47,7 +47,7 @@ namespace {
 
 struct Layout {           // byte offsets inside the workspace
     size_t fields, psi_z, psi_r, fields2, psi_h2, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
-        norm, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
+        norm, src_rad, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
         ph_h, pulse, twiddle, adj_time, Gr, Gp, emph_n, emph_h, wt, beta_r, beta_p, g_in, partial, S,
         status, total;
 };
@@ -72,6 +72,7 @@ struct zda_zone {
     long long launches = 0;
     // time-step kernel: 0 = split H/E launches (default), 1 = fused single launch
     int variant = 0, tile_phi = 2, i_ranges = 0;
+    int wait_limit = 1 << 22, inject_timeout = 0;   // bounded mbarrier waits of the fused step
     int last_parity = 0;            // fused runs: which buffer holds the final fields
     // optional CUDA-event timing of every `time_every`-th H/E launch pair
     int time_every = 0;
@@ -203,6 +204,7 @@ static void compute_layout(zda_zone &z)
     L.g_t = take((size_t)z.nrd * np * sizeof(float));
     L.g_rho = take((size_t)z.nrd * np * sizeof(float));
     L.norm = take((size_t)z.nrd * sizeof(float));
+    L.src_rad = take(2 * nr * sizeof(float2));
     L.inv_r_n = take((nr + 1) * sizeof(float));
     L.inv_r_h = take(nr * sizeof(float));
     L.br_n = take((nr + 1) * sizeof(float));
@@ -539,6 +541,7 @@ static zda_status run_filter(zda_zone &z, const float *rho_dev, cudaStream_t s)
 
 static zda_status clear_state(zda_zone &z, cudaStream_t s)
 {
+    CUDA_TRY(cudaMemsetAsync(P<int>(z, z.L.status) + 1, 0, sizeof(int), s));         // wait-timeout word
     CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields, 0, z.L.psi_r - z.L.fields, s));      // fields, psi_z
     CUDA_TRY(cudaMemsetAsync(z.ws + z.L.psi_r, 0, z.L.fields2 - z.L.psi_r, s));      // psi_r
     if (z.variant == 1) {                                                             // fields2, psi_h2
@@ -553,7 +556,7 @@ static int auto_i_ranges(const zda_zone &z)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = std::max(1, zda::fused_blocks_per_sm(z.tile_phi, z.d.n_z));
+    const int per_sm = std::max(1, zda::fused_blocks_per_sm(z.tile_phi, z.d.n_z, z.d.pml_z));
     const int jt = (z.d.n_phi + z.tile_phi - 1) / z.tile_phi;
     // as many radius ranges as fit in one wave (all CTAs co-resident, so the
     // phi-halo rows of neighbouring tiles are read while still in L2), at
@@ -599,6 +602,10 @@ static zda::FusedParams fused_params(zda_zone &z, const zda::StepParams &p, int 
     f.nq = p.nq;
     f.mon_k = p.mon_k; f.mon = p.mon;
     f.des_k0 = p.des_k0; f.des_nk = p.des_nk; f.des = p.des;
+    f.src_rad = P<float2>(z, z.L.src_rad);
+    f.err = P<int>(z, z.L.status) + 1;
+    f.wait_limit = z.wait_limit;
+    f.inject_timeout = z.inject_timeout;
     return f;
 }
 
@@ -607,25 +614,31 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
     const int R = (int)z.ev_pending.size();
     if (z.variant == 1) {
         zda::FusedParams f[2] = {fused_params(z, p, 0), fused_params(z, p, 1)};
+        // timed samples: [stream kernel] between events 0 and 1, [DFT kernel] between 1 and 2
         for (int n = 0; n < z.d.n_steps; ++n) {
             const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
             int slot = 0;
+            const zda::FusedParams &fp = f[n & 1];
+            cudaError_t e = zda::launch_fused_pre(fp, n, s);
+            if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("adjoint source step: ") + cudaGetErrorString(e));
             if (timed) {
                 slot = z.ev_next;
                 z.ev_next = (z.ev_next + 1) % R;
                 timing_drain_slot(z, slot);
                 CUDA_TRY(cudaEventRecord(z.ev[3 * slot], s));
-                CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 1], s));     // no separate H launch
             }
-            cudaError_t e = zda::launch_fused_step(f[n & 1], n, s);
+            e = zda::launch_fused_stream(fp, n, s);
             if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("fused step: ") + cudaGetErrorString(e));
+            if (timed) CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 1], s));
+            e = zda::launch_fused_post(fp, n, s);
+            if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("DFT step: ") + cudaGetErrorString(e));
             if (timed) {
                 CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 2], s));
                 z.ev_pending[slot] = 1;
             }
         }
         z.last_parity = z.d.n_steps & 1;
-        z.launches += z.d.n_steps;
+        z.launches += (long long)z.d.n_steps * zda::fused_launches_per_step(f[0]);
         return ZDA_OK;
     }
     z.last_parity = 0;
@@ -648,6 +661,15 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
     }
     z.launches += 2LL * z.d.n_steps;
     CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
+static zda_status check_wait_status(zda_zone &z, cudaStream_t s)
+{
+    int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, P<int>(z, z.L.status) + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (e) return fail(ZDA_ERR_TIMEOUT, "a bounded device-side wait of the fused step gave up");
     return ZDA_OK;
 }
 
@@ -798,6 +820,8 @@ zda_status zda_forward(zda_zone *z, const float *rho, double *focal_out, void *s
     p.des = P<float2>(*z, z->L.des_f);
     st = time_loop(*z, p, s);
     if (st) return st;
+    st = check_wait_status(*z, s);
+    if (st) return st;
     st = focal(*z, P<float2>(*z, z->L.mon), focal_out, s);
     if (st) return st;
     z->have_forward = true;
@@ -841,6 +865,7 @@ zda_status zda_adjoint(zda_zone *z, const double *dI, float *grad_rho, void *str
                                         P<float>(*z, z->L.g_t), grad_rho, s);
     z->launches += 3;
     CUDA_TRY(cudaGetLastError());
+    if (z->variant == 1) return check_wait_status(*z, s);
     return ZDA_OK;
 }
 
@@ -925,11 +950,20 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
         if (z->d.n_fold == 0) return fail(ZDA_ERR_ARG, "the axis zone (continuous axisymmetry) uses the split step");
         if (tile_phi != 2 && tile_phi != 4) return fail(ZDA_ERR_ARG, "fused step: tile_phi must be 2 or 4");
         if (z->d.n_z > zda::fused_max_nz()) return fail(ZDA_ERR_ARG, "fused step supports n_z <= 256");
+        if (z->d.n_z % 2) return fail(ZDA_ERR_ARG, "fused step needs an even n_z (16-byte bulk copies)");
     }
     z->variant = variant;
     z->tile_phi = variant == 1 ? tile_phi : z->tile_phi;
     z->i_ranges = i_ranges;
     z->have_forward = false;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_set_wait_limit(zda_zone *z, int polls, int inject_timeout)
+{
+    if (!z || polls < 1) return fail(ZDA_ERR_ARG, "bad wait limit");
+    z->wait_limit = polls;
+    z->inject_timeout = inject_timeout ? 1 : 0;
     return ZDA_OK;
 }
 

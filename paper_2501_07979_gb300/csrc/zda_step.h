@@ -25,10 +25,20 @@ struct FusedParams {
     float2 *mon;
     int des_k0, des_nk;
     float2 *des;
+    float2 *src_rad;                           // adjoint runs: per-step radial source [2][n_r] (r, phi)
+    int *err;                                  // device error word (bounded waits that gave up)
+    int wait_limit;                            // polls of an mbarrier before giving up
+    int inject_timeout;                        // test only: also wait on a barrier nobody arrives on
 };
 
-cudaError_t launch_fused_step(const FusedParams &p, int n, cudaStream_t s);
-int fused_blocks_per_sm(int tj, int nz);
+// One time step = launch_fused_pre (adjoint runs: per-step radial source),
+// launch_fused_stream (the streaming E/H kernel; needs an even n_z for its
+// 16-byte bulk copies), launch_fused_post (the running DFTs, if requested).
+cudaError_t launch_fused_pre(const FusedParams &p, int n, cudaStream_t s);
+cudaError_t launch_fused_stream(const FusedParams &p, int n, cudaStream_t s);
+cudaError_t launch_fused_post(const FusedParams &p, int n, cudaStream_t s);
+int fused_launches_per_step(const FusedParams &p);
+int fused_blocks_per_sm(int tj, int nz, int pz);
 int fused_max_nz();
 
 }  // namespace zda

@@ -185,6 +185,9 @@ class Zone:
         """Time-step kernel: variant 1 fused (tile_phi 2 or 4), 0 split H/E."""
         check(_lib.lib().zda_zone_set_kernel(self.handle, int(variant), int(tile_phi), int(i_ranges)))
 
+    def set_wait_limit(self, polls, inject_timeout=False):
+        check(_lib.lib().zda_zone_set_wait_limit(self.handle, int(polls), int(bool(inject_timeout))))
+
     def get_kernel(self):
         v, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(_lib.lib().zda_zone_get_kernel(self.handle, ctypes.byref(v), ctypes.byref(t), ctypes.byref(r)))
