@@ -61,6 +61,7 @@ typedef enum {
 
 typedef struct zda_ctx zda_ctx;
 typedef struct zda_zone zda_zone;
+typedef struct zda_lens zda_lens;
 
 /* Zone descriptor (plain data, copied at zda_zone_create).
  * n_fold = 0 selects continuous axisymmetry (the axis zone, section "Centimeter-
@@ -197,6 +198,12 @@ long long zda_zone_launch_count(const zda_zone *zone);
 zda_status zda_zone_set_kernel(zda_zone *zone, int variant, int tile_phi, int i_ranges);
 zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi, int *i_ranges);
 
+/* Time `steps` time steps of the zone's current step kernel (no source, no
+ * DFT) on its current field state, with CUDA events on `stream`; ms_out
+ * receives the elapsed milliseconds.  Overwrites the fields (a following
+ * zda_adjoint needs a new zda_forward).  Used by the tile-shape tuner. */
+zda_status zda_zone_time_steps(zda_zone *zone, int steps, double *ms_out_host, void *stream);
+
 /* The fused step (variant 1) waits on shared-memory barriers for its staged
  * copies; every wait gives up after `polls` polls (default 4194304), sets an
  * error word and lets the kernel finish, and the call then returns
@@ -230,6 +237,31 @@ zda_status zda_zone_timing(zda_zone *zone, double *h_ms_host, double *e_ms_host,
  * kernels overlap on the GPU race.  Allocates nothing. */
 zda_status zda_filter_project_noalloc(const zda_zone_desc *desc, const float *rho_dev, float *rho_tilde_dev,
                                       void *stream);
+
+/* ---- lens: all zones of a lens (section "Zoned discrete axisymmetry (ZDA)":
+ * concentric zones, each simulated on its own, whose fields add up at the
+ * focus).  The caller creates the zones (same wavelengths and focal
+ * distance; an axis zone may be first) and binds their workspaces, then the
+ * lens and its small workspace.  zda_lens_forward runs every zone's forward
+ * solve -- as parallel branches of one CUDA graph replayed per call (captured
+ * on first use, and again after a zone's kernel or workspace changes), each
+ * zone with its own dt and step count -- and sums the zones' focal phasors on
+ * the device: focal_out_host = sum_z S_z (n_freq complex doubles).
+ * zda_lens_adjoint gives every zone the same dI/dS (the lens phasor is the
+ * plain sum) and writes each zone's dI/drho.  Device buffers: rho_dev[z] and
+ * grad_rho_dev[z] are arrays (host) of n_zones device pointers.  Both calls
+ * synchronise `stream`.  The lens keeps its own streams and graphs; it owns
+ * no device memory beyond what the graph runtime needs. */
+zda_status zda_lens_create(zda_ctx *ctx, zda_zone *const *zones, int n_zones, zda_lens **out);
+void zda_lens_destroy(zda_lens *lens);
+zda_status zda_lens_workspace_bytes(const zda_lens *lens, size_t *bytes);
+zda_status zda_lens_bind_workspace(zda_lens *lens, void *workspace_dev, size_t bytes);
+zda_status zda_lens_set_graph(zda_lens *lens, int use_graph);     /* 0: enqueue directly, no graph */
+zda_status zda_lens_forward(zda_lens *lens, const float *const *rho_dev, double *focal_out_host, void *stream);
+zda_status zda_lens_adjoint(zda_lens *lens, const double *dI_dfocal_host, float *const *grad_rho_dev, void *stream);
+/* zone z's own phasors S_z from the last zda_lens_forward (host copy). */
+zda_status zda_lens_zone_focal(const zda_lens *lens, int zone, double *focal_out_host);
+long long zda_lens_launch_count(const zda_lens *lens);   /* graph launches (or direct runs) issued */
 
 /* Thread-local message of the last error ("" if none). */
 const char *zda_last_error(void);

@@ -77,9 +77,19 @@ SIGNATURES = {
     "zda_zone_set_kernel": (_i, [_vp, _i, _i, _i]),
     "zda_zone_get_kernel": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "zda_zone_set_wait_limit": (_i, [_vp, _i, _i]),
+    "zda_zone_time_steps": (_i, [_vp, _i, _dp, _vp]),
     "zda_zone_set_timing": (_i, [_vp, _i]),
     "zda_zone_timing": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "zda_filter_project_noalloc": (_i, [ctypes.POINTER(ZoneDesc), _vp, _vp, _vp]),
+    "zda_lens_create": (_i, [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "zda_lens_destroy": (None, [_vp]),
+    "zda_lens_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "zda_lens_bind_workspace": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "zda_lens_set_graph": (_i, [_vp, _i]),
+    "zda_lens_forward": (_i, [_vp, ctypes.POINTER(_vp), _dp, _vp]),
+    "zda_lens_adjoint": (_i, [_vp, _dp, ctypes.POINTER(_vp), _vp]),
+    "zda_lens_zone_focal": (_i, [_vp, _i, _dp]),
+    "zda_lens_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_last_error": (ctypes.c_char_p, []),
 }
 

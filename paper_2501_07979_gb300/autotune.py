@@ -1,0 +1,62 @@
+"""Tile-shape tuner for the time-step kernel of a zone.
+
+For each candidate (variant, phi rows per block, radius ranges) the zone's
+step kernel is timed on the GPU for a few steps (`Zone.time_steps`); the
+fastest is applied to the zone and remembered in a JSON cache keyed by the
+zone's shape (n_r, n_phi, n_z, PML widths), so zones of the same shape in a
+lens (and later runs) reuse it without timing again.
+"""
+import json
+import os
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "zda_tiles.json")
+
+
+def shape_key(spec):
+    return "%dx%dx%d_p%d-%d-%d_%s" % (spec.n_r, spec.n_phi, spec.n_z, spec.pml_r_in, spec.pml_r_out,
+                                      spec.pml_z, "axis" if spec.n_fold == 0 else "wedge")
+
+
+def candidates(spec):
+    cands = [(0, 2, 0)]
+    if spec.n_fold > 0 and spec.n_z % 2 == 0 and spec.n_z <= 256:
+        for tj in (2, 4):
+            for ir in (0, 2, 4):
+                cands.append((1, tj, ir))
+    return cands
+
+
+def tune_zone(zone, steps=40, cache_path=None, use_cache=True):
+    """Pick and apply the fastest step kernel for `zone`; returns
+    (choice, {choice: ms}) with choice = (variant, tile_phi, i_ranges)."""
+    from ._lib import ZdaError
+    path = cache_path or DEFAULT_CACHE
+    key = shape_key(zone.spec)
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        choice = tuple(cache[key]["choice"])
+        zone.set_kernel(*choice)
+        return choice, {}
+    times = {}
+    for c in candidates(zone.spec):
+        try:
+            zone.set_kernel(*c)
+            zone.time_steps(4)                      # warm-up (module load, first touch)
+            times[c] = zone.time_steps(steps)
+        except ZdaError:
+            continue
+    choice = min(times, key=times.get)
+    zone.set_kernel(*choice)
+    if use_cache:
+        cache[key] = {"choice": list(choice), "ms_per_step": times[choice] / steps,
+                      "times": {"%d,%d,%d" % c: t / steps for c, t in times.items()}}
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".%d.tmp" % os.getpid()
+        json.dump(cache, open(tmp, "w"), indent=1)
+        os.replace(tmp, path)
+    return choice, times

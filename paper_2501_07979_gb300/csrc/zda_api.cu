@@ -673,7 +673,8 @@ static zda_status check_wait_status(zda_zone &z, cudaStream_t s)
     return ZDA_OK;
 }
 
-static zda_status focal(zda_zone &z, const float2 *mon, double *out_host, cudaStream_t s)
+// focal kernels: S (workspace) and the non-finite flag (status[0])
+static zda_status focal_enqueue(zda_zone &z, const float2 *mon, cudaStream_t s)
 {
     int *status = P<int>(z, z.L.status);
     CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
@@ -682,11 +683,81 @@ static zda_status focal(zda_zone &z, const float2 *mon, double *out_host, cudaSt
     zda::launch_focal_sum(P<double2>(z, z.L.partial), z.nq, z.d.n_r, P<double2>(z, z.L.S), status, s);
     z.launches += 2;
     CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
+static zda_status focal_finish(zda_zone &z, double *out_host, cudaStream_t s)
+{
     int st = 0;
-    CUDA_TRY(cudaMemcpyAsync(out_host, z.ws + z.L.S, z.nq * sizeof(double2), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (out_host)
+        CUDA_TRY(cudaMemcpyAsync(out_host, z.ws + z.L.S, z.nq * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&st, P<int>(z, z.L.status), sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (st) return fail(ZDA_ERR_NONFINITE, "non-finite focal phasor (the time loop diverged)");
+    return ZDA_OK;
+}
+
+static zda_status focal(zda_zone &z, const float2 *mon, double *out_host, cudaStream_t s)
+{
+    zda_status st = focal_enqueue(z, mon, s);
+    if (st) return st;
+    return focal_finish(z, out_host, s);
+}
+
+// Everything of a forward run that is enqueued on the stream (no host sync):
+// filter + projection, cleared state, the time loop with DFTs, focal kernels.
+static zda_status forward_enqueue(zda_zone &z, const float *rho, cudaStream_t s)
+{
+    z.have_forward = false;
+    zda_status st = run_filter(z, rho, s);
+    if (st) return st;
+    st = clear_state(z, s);
+    if (st) return st;
+    const size_t plane = (size_t)z.d.n_r * z.d.n_phi;
+    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.mon, 0, z.nq * 2 * plane * sizeof(float2), s));
+    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.des_f, 0, z.nq * 3 * plane * z.nk * sizeof(float2), s));
+    zda::StepParams p = step_params(z);
+    p.src_mode = zda::SRC_PLANE_WAVE;
+    p.src_k = z.d.source_k;
+    p.mon_k = z.d.monitor_k;
+    p.mon = P<float2>(z, z.L.mon);
+    p.des = P<float2>(z, z.L.des_f);
+    st = time_loop(z, p, s);
+    if (st) return st;
+    return focal_enqueue(z, P<float2>(z, z.L.mon), s);
+}
+
+// Everything of an adjoint run that is enqueued (dI/dS already in g_in):
+// adjoint profiles, the adjoint time loop, overlap, transposed chain.
+static zda_status adjoint_enqueue(zda_zone &z, float *grad_rho, cudaStream_t s)
+{
+    const zda_zone_desc &d = z.d;
+    const size_t plane = (size_t)d.n_r * d.n_phi;
+    const double vol = d.dr * z.dphi * d.dz;
+    zda::launch_adjoint_profiles(P<double2>(z, z.L.g_in), P<double2>(z, z.L.Gr), P<double2>(z, z.L.Gp),
+                                 P<float>(z, z.L.wt), z.nq, d.n_r, d.r_lo, d.dr, vol, P<float2>(z, z.L.beta_r),
+                                 P<float2>(z, z.L.beta_p), s);
+    z.launches++;
+    zda_status st = clear_state(z, s);
+    if (st) return st;
+    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.des_a, 0, z.nq * 3 * plane * z.nk * sizeof(float2), s));
+    zda::StepParams p = step_params(z);
+    p.src_mode = zda::SRC_ADJOINT;
+    p.src_k = d.monitor_k;
+    p.mon_k = -1;
+    p.mon = nullptr;
+    p.des = P<float2>(z, z.L.des_a);
+    st = time_loop(z, p, s);
+    if (st) return st;
+    zda::launch_site_gradient(P<float2>(z, z.L.des_f), P<float2>(z, z.L.des_a), P<float>(z, z.L.wt), z.nq,
+                              d.n_r, d.n_phi, z.nk, d.r_lo, d.dr, vol, P<float>(z, z.L.site_grad), s);
+    zda::launch_cell_gradient(P<float>(z, z.L.site_grad), d.n_r, d.n_phi, z.nk, z.i_d0, z.nrd,
+                              (float)(d.eps_hi - d.eps_lo), P<float>(z, z.L.g_t), s);
+    const zda::FilterParams fp = filter_params(z);
+    zda::launch_filter_project_backward(fp, P<float>(z, z.L.rho_bar), P<float>(z, z.L.norm),
+                                        P<float>(z, z.L.g_t), grad_rho, s);
+    z.launches += 3;
+    CUDA_TRY(cudaGetLastError());
     return ZDA_OK;
 }
 
@@ -804,25 +875,11 @@ zda_status zda_forward(zda_zone *z, const float *rho, double *focal_out, void *s
     if (st) return st;
     if (!rho || !focal_out) return fail(ZDA_ERR_ARG, "null pointer");
     cudaStream_t s = (cudaStream_t)stream;
-    z->have_forward = false;
-    st = run_filter(*z, rho, s);
-    if (st) return st;
-    st = clear_state(*z, s);
-    if (st) return st;
-    const size_t plane = (size_t)z->d.n_r * z->d.n_phi;
-    CUDA_TRY(cudaMemsetAsync(z->ws + z->L.mon, 0, z->nq * 2 * plane * sizeof(float2), s));
-    CUDA_TRY(cudaMemsetAsync(z->ws + z->L.des_f, 0, z->nq * 3 * plane * z->nk * sizeof(float2), s));
-    zda::StepParams p = step_params(*z);
-    p.src_mode = zda::SRC_PLANE_WAVE;
-    p.src_k = z->d.source_k;
-    p.mon_k = z->d.monitor_k;
-    p.mon = P<float2>(*z, z->L.mon);
-    p.des = P<float2>(*z, z->L.des_f);
-    st = time_loop(*z, p, s);
+    st = forward_enqueue(*z, rho, s);
     if (st) return st;
     st = check_wait_status(*z, s);
     if (st) return st;
-    st = focal(*z, P<float2>(*z, z->L.mon), focal_out, s);
+    st = focal_finish(*z, focal_out, s);
     if (st) return st;
     z->have_forward = true;
     return ZDA_OK;
@@ -837,34 +894,9 @@ zda_status zda_adjoint(zda_zone *z, const double *dI, float *grad_rho, void *str
     if (!z->adjoint_ok)
         return fail(ZDA_ERR_ARG, "n_steps too short: the broadband adjoint pulses do not fit the run");
     cudaStream_t s = (cudaStream_t)stream;
-    const zda_zone_desc &d = z->d;
-    const size_t plane = (size_t)d.n_r * d.n_phi;
     CUDA_TRY(cudaMemcpyAsync(z->ws + z->L.g_in, dI, z->nq * sizeof(double2), cudaMemcpyHostToDevice, s));
-    const double vol = d.dr * z->dphi * d.dz;
-    zda::launch_adjoint_profiles(P<double2>(*z, z->L.g_in), P<double2>(*z, z->L.Gr), P<double2>(*z, z->L.Gp),
-                                 P<float>(*z, z->L.wt), z->nq, d.n_r, d.r_lo, d.dr, vol, P<float2>(*z, z->L.beta_r),
-                                 P<float2>(*z, z->L.beta_p), s);
-    z->launches++;
-    st = clear_state(*z, s);
+    st = adjoint_enqueue(*z, grad_rho, s);
     if (st) return st;
-    CUDA_TRY(cudaMemsetAsync(z->ws + z->L.des_a, 0, z->nq * 3 * plane * z->nk * sizeof(float2), s));
-    zda::StepParams p = step_params(*z);
-    p.src_mode = zda::SRC_ADJOINT;
-    p.src_k = d.monitor_k;
-    p.mon_k = -1;
-    p.mon = nullptr;
-    p.des = P<float2>(*z, z->L.des_a);
-    st = time_loop(*z, p, s);
-    if (st) return st;
-    zda::launch_site_gradient(P<float2>(*z, z->L.des_f), P<float2>(*z, z->L.des_a), P<float>(*z, z->L.wt), z->nq,
-                              d.n_r, d.n_phi, z->nk, d.r_lo, d.dr, vol, P<float>(*z, z->L.site_grad), s);
-    zda::launch_cell_gradient(P<float>(*z, z->L.site_grad), d.n_r, d.n_phi, z->nk, z->i_d0, z->nrd,
-                              (float)(d.eps_hi - d.eps_lo), P<float>(*z, z->L.g_t), s);
-    const zda::FilterParams fp = filter_params(*z);
-    zda::launch_filter_project_backward(fp, P<float>(*z, z->L.rho_bar), P<float>(*z, z->L.norm),
-                                        P<float>(*z, z->L.g_t), grad_rho, s);
-    z->launches += 3;
-    CUDA_TRY(cudaGetLastError());
     if (z->variant == 1) return check_wait_status(*z, s);
     return ZDA_OK;
 }
@@ -959,6 +991,41 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
     return ZDA_OK;
 }
 
+zda_status zda_zone_time_steps(zda_zone *z, int steps, double *ms_out, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (steps < 1 || !ms_out) return fail(ZDA_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    z->have_forward = false;                 // the fields are overwritten
+    zda::StepParams p = step_params(*z);
+    p.src_mode = zda::SRC_NONE;
+    p.mon = nullptr;
+    p.des = nullptr;
+    p.mon_k = -1;
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    const int saved_steps = z->d.n_steps;
+    const int saved_every = z->time_every;
+    z->d.n_steps = steps;
+    z->time_every = 0;
+    cudaError_t e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) st = time_loop(*z, p, s);
+    if (e == cudaSuccess && st == ZDA_OK) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess && st == ZDA_OK) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess && st == ZDA_OK) e = cudaEventElapsedTime(&ms, a, b);
+    z->d.n_steps = saved_steps;
+    z->time_every = saved_every;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) return st;
+    if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("timing: ") + cudaGetErrorString(e));
+    *ms_out = ms;
+    return check_wait_status(*z, s);
+}
+
 zda_status zda_zone_set_wait_limit(zda_zone *z, int polls, int inject_timeout)
 {
     if (!z || polls < 1) return fail(ZDA_ERR_ARG, "bad wait limit");
@@ -1005,5 +1072,269 @@ zda_status zda_zone_timing(zda_zone *z, double *h_ms, double *e_ms, long long *c
     z->t_count = 0;
     return ZDA_OK;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ lens
+// A lens: concentric zones solved independently (section "Zoned discrete
+// axisymmetry") whose focal phasors add up.  Each zone's whole forward (or
+// adjoint) run is captured as one branch of a CUDA graph (the branches fork
+// from one capture stream, so the zones run concurrently, each with its own
+// dt and number of steps), joined by a device-side sum of the phasors.  One
+// graph launch per run; the graph is captured on first use and again when a
+// zone's configuration changes.
+struct zda_lens {
+    zda_ctx *ctx = nullptr;
+    std::vector<zda_zone *> zones;
+    int nq = 0;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool use_graph = true;
+    cudaGraphExec_t g_fwd = nullptr, g_adj = nullptr;
+    std::vector<std::vector<long long>> stamp_fwd, stamp_adj;
+    std::vector<cudaStream_t> streams;     // [0] capture / join stream, [1 + z] zone branches
+    std::vector<cudaEvent_t> events;       // [0] fork, [1 + z] joins
+    bool have_forward = false;
+    long long launches = 0;
+    std::vector<const void *> bound_S;     // zones' phasor addresses when the workspace was bound
+    ~zda_lens();
+};
+
+zda_lens::~zda_lens()
+{
+    if (g_fwd) cudaGraphExecDestroy(g_fwd);
+    if (g_adj) cudaGraphExecDestroy(g_adj);
+    for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+}
+
+static size_t lens_ws_ptrs(const zda_lens &L) { return 0; }
+static size_t lens_ws_S(const zda_lens &L) { return align_up(L.zones.size() * sizeof(void *)); }
+static size_t lens_ws_status(const zda_lens &L) { return lens_ws_S(L) + align_up(L.nq * sizeof(double2)); }
+static size_t lens_ws_total(const zda_lens &L) { return lens_ws_status(L) + 256; }
+
+static std::vector<long long> zone_stamp(const zda_zone &z)
+{
+    return {(long long)(uintptr_t)z.ws, z.variant, z.tile_phi, z.i_ranges, z.d.n_steps, z.nq,
+            z.wait_limit, z.inject_timeout, (long long)z.lambda.size()};
+}
+
+static bool stamps_match(const zda_lens &L, const std::vector<std::vector<long long>> &st)
+{
+    if (st.size() != L.zones.size()) return false;
+    for (size_t i = 0; i < L.zones.size(); ++i)
+        if (st[i] != zone_stamp(*L.zones[i])) return false;
+    return true;
+}
+
+// enqueue every zone's run on its branch stream and join on streams[0]
+template <class F>
+static zda_status lens_branches(zda_lens &L, F &&per_zone)
+{
+    cudaStream_t s0 = L.streams[0];
+    CUDA_TRY(cudaEventRecord(L.events[0], s0));
+    for (size_t z = 0; z < L.zones.size(); ++z) {
+        cudaStream_t sz = L.streams[1 + z];
+        CUDA_TRY(cudaStreamWaitEvent(sz, L.events[0], 0));
+        zda_status st = per_zone(*L.zones[z], z, sz);
+        if (st) return st;
+        CUDA_TRY(cudaEventRecord(L.events[1 + z], sz));
+        CUDA_TRY(cudaStreamWaitEvent(s0, L.events[1 + z], 0));
+    }
+    return ZDA_OK;
+}
+
+template <class F>
+static zda_status lens_run(zda_lens &L, cudaGraphExec_t &exec, std::vector<std::vector<long long>> &stamp,
+                           cudaStream_t user, F &&body)
+{
+    cudaStream_t s0 = L.streams[0];
+    if (!L.use_graph) {
+        CUDA_TRY(cudaEventRecord(L.events[0], user));
+        CUDA_TRY(cudaStreamWaitEvent(s0, L.events[0], 0));
+        zda_status st = body();
+        if (st) return st;
+        CUDA_TRY(cudaEventRecord(L.events[0], s0));
+        CUDA_TRY(cudaStreamWaitEvent(user, L.events[0], 0));
+        return ZDA_OK;
+    }
+    if (!exec || !stamps_match(L, stamp)) {
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        std::vector<int> saved(L.zones.size());
+        for (size_t z = 0; z < L.zones.size(); ++z) {       // no host waits inside a capture
+            saved[z] = L.zones[z]->time_every;
+            L.zones[z]->time_every = 0;
+        }
+        CUDA_TRY(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        zda_status st = body();
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s0, &g);
+        for (size_t z = 0; z < L.zones.size(); ++z) L.zones[z]->time_every = saved[z];
+        if (st) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { exec = nullptr; return fail(ZDA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+        stamp.clear();
+        for (zda_zone *z : L.zones) stamp.push_back(zone_stamp(*z));
+    }
+    CUDA_TRY(cudaGraphLaunch(exec, user));
+    L.launches++;
+    return ZDA_OK;
+}
+
+extern "C" {
+
+zda_status zda_lens_create(zda_ctx *ctx, zda_zone *const *zones, int n_zones, zda_lens **out)
+{
+    if (!ctx || !zones || n_zones < 1 || !out) return fail(ZDA_ERR_ARG, "bad argument");
+    for (int z = 0; z < n_zones; ++z) {
+        if (!zones[z] || zones[z]->ctx != ctx) return fail(ZDA_ERR_ARG, "zone missing or from another context");
+        if (zones[z]->nq != zones[0]->nq) return fail(ZDA_ERR_ARG, "all zones of a lens need the same wavelengths");
+        for (int y = 0; y < z; ++y)
+            if (zones[y] == zones[z]) return fail(ZDA_ERR_ARG, "a zone appears twice");
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    zda_lens *L = new zda_lens();
+    L->ctx = ctx;
+    L->zones.assign(zones, zones + n_zones);
+    L->nq = zones[0]->nq;
+    L->streams.resize(n_zones + 1);
+    L->events.resize(n_zones + 1);
+    for (auto &s : L->streams)
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { delete L; return fail(ZDA_ERR_CUDA, "stream"); }
+    for (auto &e : L->events)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { delete L; return fail(ZDA_ERR_CUDA, "event"); }
+    *out = L;
+    return ZDA_OK;
+}
+
+void zda_lens_destroy(zda_lens *lens) { delete lens; }
+
+zda_status zda_lens_workspace_bytes(const zda_lens *L, size_t *bytes)
+{
+    if (!L || !bytes) return fail(ZDA_ERR_ARG, "null argument");
+    *bytes = lens_ws_total(*L);
+    return ZDA_OK;
+}
+
+zda_status zda_lens_bind_workspace(zda_lens *L, void *ws, size_t bytes)
+{
+    if (!L || !ws) return fail(ZDA_ERR_ARG, "null argument");
+    if (((uintptr_t)ws) & 255) return fail(ZDA_ERR_ARG, "workspace must be 256-byte aligned");
+    if (bytes < lens_ws_total(*L)) return fail(ZDA_ERR_OOM, "workspace smaller than zda_lens_workspace_bytes");
+    CUDA_TRY(cudaSetDevice(L->ctx->device));
+    L->ws = (char *)ws;
+    L->ws_bytes = bytes;
+    std::vector<const double2 *> ptrs;
+    for (zda_zone *z : L->zones) {
+        if (!z->ws) return fail(ZDA_ERR_STATE, "bind every zone's workspace before the lens workspace");
+        ptrs.push_back((const double2 *)(z->ws + z->L.S));
+    }
+    L->bound_S.assign(ptrs.begin(), ptrs.end());
+    CUDA_TRY(cudaMemcpy(L->ws + lens_ws_ptrs(*L), ptrs.data(), ptrs.size() * sizeof(void *), cudaMemcpyHostToDevice));
+    if (L->g_fwd) { cudaGraphExecDestroy(L->g_fwd); L->g_fwd = nullptr; }
+    if (L->g_adj) { cudaGraphExecDestroy(L->g_adj); L->g_adj = nullptr; }
+    L->have_forward = false;
+    return ZDA_OK;
+}
+
+zda_status zda_lens_set_graph(zda_lens *L, int use_graph)
+{
+    if (!L) return fail(ZDA_ERR_ARG, "null lens");
+    L->use_graph = use_graph != 0;
+    return ZDA_OK;
+}
+
+zda_status zda_lens_forward(zda_lens *L, const float *const *rho, double *focal_out, void *stream)
+{
+    if (!L || !rho || !focal_out) return fail(ZDA_ERR_ARG, "null argument");
+    if (!L->ws) return fail(ZDA_ERR_STATE, "no lens workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t z = 0; z < L->zones.size(); ++z) {
+        zda_zone *Z = L->zones[z];
+        if (!rho[z]) return fail(ZDA_ERR_ARG, "null density pointer");
+        const void *now = Z->ws ? (const void *)(Z->ws + Z->L.S) : nullptr;
+        if (now != L->bound_S[z]) return fail(ZDA_ERR_STATE, "a zone's workspace changed: re-bind the lens workspace");
+        zda_status st = ready(Z);            // tables (host copies) before any capture
+        if (st) return st;
+        CUDA_TRY(cudaMemcpyAsync(Z->ws + Z->L.rho_in, rho[z], (size_t)Z->nrd * Z->d.n_phi * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    L->have_forward = false;
+    for (zda_zone *Z : L->zones) Z->have_forward = false;
+    int *status = (int *)(L->ws + lens_ws_status(*L));
+    auto body = [&]() -> zda_status {
+        zda_status st = lens_branches(*L, [&](zda_zone &Z, size_t, cudaStream_t sz) {
+            return forward_enqueue(Z, P<float>(Z, Z.L.rho_in), sz);
+        });
+        if (st) return st;
+        CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), L->streams[0]));
+        zda::launch_lens_sum((const double2 *const *)(L->ws + lens_ws_ptrs(*L)), (int)L->zones.size(), L->nq,
+                             (double2 *)(L->ws + lens_ws_S(*L)), status, L->streams[0]);
+        CUDA_TRY(cudaGetLastError());
+        return ZDA_OK;
+    };
+    zda_status st = lens_run(*L, L->g_fwd, L->stamp_fwd, s, body);
+    if (st) return st;
+    int flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(focal_out, L->ws + lens_ws_S(*L), L->nq * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (zda_zone *Z : L->zones) {
+        if (Z->variant == 1) {
+            st = check_wait_status(*Z, s);
+            if (st) return st;
+        }
+    }
+    if (flag) return fail(ZDA_ERR_NONFINITE, "non-finite lens focal phasor");
+    for (zda_zone *Z : L->zones) Z->have_forward = true;
+    L->have_forward = true;
+    return ZDA_OK;
+}
+
+zda_status zda_lens_zone_focal(const zda_lens *L, int zone, double *focal_out)
+{
+    if (!L || zone < 0 || zone >= (int)L->zones.size() || !focal_out) return fail(ZDA_ERR_ARG, "bad argument");
+    if (!L->have_forward) return fail(ZDA_ERR_STATE, "no lens forward yet");
+    const zda_zone *Z = L->zones[zone];
+    CUDA_TRY(cudaMemcpy(focal_out, Z->ws + Z->L.S, L->nq * sizeof(double2), cudaMemcpyDeviceToHost));
+    return ZDA_OK;
+}
+
+zda_status zda_lens_adjoint(zda_lens *L, const double *dI, float *const *grad_rho, void *stream)
+{
+    if (!L || !dI || !grad_rho) return fail(ZDA_ERR_ARG, "null argument");
+    if (!L->have_forward) return fail(ZDA_ERR_STATE, "zda_lens_adjoint needs a preceding zda_lens_forward");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (zda_zone *Z : L->zones) {
+        if (!Z->adjoint_ok)
+            return fail(ZDA_ERR_ARG, "n_steps too short: the broadband adjoint pulses do not fit a zone's run");
+        // every zone's phasors enter the lens sum with weight 1: same dI/dS
+        CUDA_TRY(cudaMemcpyAsync(Z->ws + Z->L.g_in, dI, L->nq * sizeof(double2), cudaMemcpyHostToDevice, s));
+    }
+    auto body = [&]() -> zda_status {
+        return lens_branches(*L, [&](zda_zone &Z, size_t, cudaStream_t sz) {
+            return adjoint_enqueue(Z, P<float>(Z, Z.L.g_rho), sz);
+        });
+    };
+    zda_status st = lens_run(*L, L->g_adj, L->stamp_adj, s, body);
+    if (st) return st;
+    for (size_t z = 0; z < L->zones.size(); ++z) {
+        zda_zone *Z = L->zones[z];
+        if (!grad_rho[z]) return fail(ZDA_ERR_ARG, "null gradient pointer");
+        CUDA_TRY(cudaMemcpyAsync(grad_rho[z], Z->ws + Z->L.g_rho, (size_t)Z->nrd * Z->d.n_phi * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (zda_zone *Z : L->zones)
+        if (Z->variant == 1) {
+            st = check_wait_status(*Z, s);
+            if (st) return st;
+        }
+    return ZDA_OK;
+}
+
+long long zda_lens_launch_count(const zda_lens *L) { return L ? L->launches : -1; }
 
 }  // extern "C"

@@ -119,6 +119,7 @@ void launch_site_gradient(const float2 *des_f, const float2 *des_a, const float 
 void launch_cell_gradient(const float *site_grad, int nr, int nphi, int nk, int i_d0, int nrd, float deps,
                           float *g_t, cudaStream_t s);
 void launch_fill_status_check(const float *x, size_t n, int *status, cudaStream_t s);
+void launch_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, int *status, cudaStream_t s);
 
 }  // namespace zda
 

@@ -578,6 +578,27 @@ void launch_cell_gradient(const float *site_grad, int nr, int nphi, int nk, int 
     k_cell_gradient<<<g, 128, 0, s>>>(site_grad, nr, nphi, nk, i_d0, nrd, deps, g_t);
 }
 
+// Lens focal phasors: the sum over zones of each zone's S (the only
+// cross-zone coupling of a lens), with a non-finite flag.
+__global__ void k_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, int *status)
+{
+    const int q = threadIdx.x;
+    if (q >= nq) return;
+    double2 v = make_double2(0.0, 0.0);
+    for (int z = 0; z < nzones; ++z) {
+        const double2 a = S[z][q];
+        v.x += a.x;
+        v.y += a.y;
+    }
+    out[q] = v;
+    if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(status, 1);
+}
+
+void launch_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, int *status, cudaStream_t s)
+{
+    k_lens_sum<<<1, 32, 0, s>>>(S, nzones, nq, out, status);
+}
+
 __global__ void k_status_check(const float *x, size_t n, int *status)
 {
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -10,6 +10,8 @@ phasor sum is one all-reduce of a few hundred bytes.
 The zone solver is pluggable (any object with forward(rho) -> S and
 adjoint(dI_dS) -> grad): `Zone` on a GPU, or any stand-in.
 """
+import ctypes
+
 import numpy as np
 
 
@@ -66,3 +68,76 @@ class ShardedLens:
 
     def adjoint(self, dI_dS):
         return {z: solver.adjoint(dI_dS) for z, solver in sorted(self.solvers.items())}
+
+
+class Lens:
+    """All zones of a lens on one GPU through the C ABI (zda_lens_*): one
+    CUDA graph launch runs every zone's forward (or adjoint) run, the zones'
+    focal phasors are summed on the device."""
+
+    def __init__(self, zones, use_graph=True):
+        import torch
+        from . import _lib
+        from ._lib import check
+        self.zones = list(zones)
+        L = _lib.lib()
+        arr = (ctypes.c_void_p * len(self.zones))(*[z.handle.value for z in self.zones])
+        h = ctypes.c_void_p()
+        check(L.zda_lens_create(self.zones[0].ctx.handle, arr, len(self.zones), ctypes.byref(h)))
+        self.handle = h
+        nb = ctypes.c_size_t()
+        check(L.zda_lens_workspace_bytes(h, ctypes.byref(nb)))
+        self.workspace = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.zones[0].device)
+        check(L.zda_lens_bind_workspace(h, ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel()))
+        check(L.zda_lens_set_graph(h, int(bool(use_graph))))
+        self.n_freq = self.zones[0].n_freq
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            from . import _lib
+            _lib.lib().zda_lens_destroy(h)
+            self.handle = None
+
+    def _stream(self):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def forward(self, rhos):
+        """rhos: list of CUDA float32 tensors (one per zone) -> lens phasors S."""
+        from . import _lib
+        from ._lib import check
+        rs = [z._rho(r) for z, r in zip(self.zones, rhos)]
+        self._rhos = rs
+        arr = (ctypes.c_void_p * len(rs))(*[r.data_ptr() for r in rs])
+        out = (ctypes.c_double * (2 * self.n_freq))()
+        check(_lib.lib().zda_lens_forward(self.handle, arr, out, self._stream()))
+        a = np.frombuffer(out, dtype=np.float64).copy()
+        return a[0::2] + 1j * a[1::2]
+
+    def zone_focal(self, z):
+        from . import _lib
+        from ._lib import check
+        out = (ctypes.c_double * (2 * self.n_freq))()
+        check(_lib.lib().zda_lens_zone_focal(self.handle, int(z), out))
+        a = np.frombuffer(out, dtype=np.float64).copy()
+        return a[0::2] + 1j * a[1::2]
+
+    def adjoint(self, dI_dS):
+        """dI_dS: n_freq complex (dI/dRe S + i dI/dIm S of the lens phasors)
+        -> list of dI/drho tensors, one per zone."""
+        import torch
+        from . import _lib
+        from ._lib import check
+        g = np.asarray(dI_dS, dtype=np.complex128)
+        buf = (ctypes.c_double * (2 * self.n_freq))(*np.stack([g.real, g.imag], 1).ravel().tolist())
+        grads = [torch.empty((z.n_r_design, z.spec.n_phi), dtype=torch.float32, device=z.device)
+                 for z in self.zones]
+        arr = (ctypes.c_void_p * len(grads))(*[t.data_ptr() for t in grads])
+        check(_lib.lib().zda_lens_adjoint(self.handle, buf, arr, self._stream()))
+        return grads
+
+    @property
+    def launches(self):
+        from . import _lib
+        return int(_lib.lib().zda_lens_launch_count(self.handle))

@@ -185,6 +185,13 @@ class Zone:
         """Time-step kernel: variant 1 fused (tile_phi 2 or 4), 0 split H/E."""
         check(_lib.lib().zda_zone_set_kernel(self.handle, int(variant), int(tile_phi), int(i_ranges)))
 
+    def time_steps(self, steps):
+        """Milliseconds for `steps` steps of the current step kernel (no
+        source, no DFT); overwrites the fields."""
+        ms = ctypes.c_double()
+        check(_lib.lib().zda_zone_time_steps(self.handle, int(steps), ctypes.byref(ms), _stream()))
+        return ms.value
+
     def set_wait_limit(self, polls, inject_timeout=False):
         check(_lib.lib().zda_zone_set_wait_limit(self.handle, int(polls), int(bool(inject_timeout))))
 

@@ -322,3 +322,59 @@ def test_divergent_run_reports_nonfinite():
     z = _zone(spec)
     with pytest.raises(ZdaError, match="ZDA_ERR_NONFINITE"):
         z.forward(_dev(np.zeros((spec.n_r_design, spec.n_phi))))
+
+
+def test_autotuner_times_candidates_and_applies_the_fastest(tmp_path):
+    from paper_2501_07979_gb300.autotune import tune_zone, candidates
+    spec = zone_cfg2(n_steps=100)
+    z = _zone(spec)
+    cache = str(tmp_path / "tiles.json")
+    choice, times = tune_zone(z, steps=8, cache_path=cache)
+    assert len(times) == len(candidates(spec)) and times[choice] == min(times.values())
+    v, tj, _ = z.get_kernel()
+    assert (v, tj) == choice[:2]
+    z2 = _zone(spec)
+    again, t2 = tune_zone(z2, cache_path=cache)           # cached: no timing
+    assert again == choice and t2 == {}
+
+
+# ------------------------------------------------------------------ lens (all zones, one graph)
+def _lens_specs():
+    base = dict(n_steps=500, filter_radius=0.2, beta=3.0, wavelengths=(0.9, 1.1), pulse_sigma=0.4,
+                pulse_t0=1.6, focal=12.0)
+    return [zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0, n_r=20, **base),
+            zone_tiny(r_lo=1.2, n_fold=12, n_phi=6, n_r=24, **base),
+            zone_tiny(r_lo=3.2, n_fold=24, n_phi=8, n_r=28, **base)]
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("kernel", ["split", "fused2"])
+def test_lens_equals_sum_of_zones_and_oracle(use_graph, kernel):
+    from paper_2501_07979_gb300.lens import Lens
+    specs = _lens_specs()
+    rhos = [smoothed_rho(s.n_r_design, s.n_phi, 30 + z, mode="minmax") for z, s in enumerate(specs)]
+    zones = [_zone(s) for s in specs]
+    if kernel == "fused2":
+        for z in zones[1:]:
+            z.set_kernel(*KERNELS["fused2"])
+    lens = Lens(zones, use_graph=use_graph)
+    S = lens.forward([_dev(r) for r in rhos])
+    per_zone = [lens.zone_focal(z) for z in range(len(zones))]
+    assert _rel(S, sum(per_zone)) < 1e-12
+    refs = [O.gradient(s, r) for s, r in zip(specs, rhos)]           # (I, g, fwd, adj) per zone
+    S_ref = sum(f[2]["S"] for f in refs)
+    assert _rel(S, S_ref) < FIELD_TOL
+    g = 4.0 * S
+    grads = lens.adjoint(g)
+    for z, (s, r) in enumerate(zip(specs, rhos)):
+        f = dict(refs[z][2])
+        f["rho"] = r
+        adj = O.adjoint(s, f, g)
+        gm = f["geom"]
+        g_ref = O.conic_filter_T(s, gm, adj["grad_rho_tilde"] * O.project_grad(s, O.conic_filter(s, gm, r)))
+        assert _rel(grads[z].cpu().numpy(), g_ref) < GRAD_TOL
+    # a second iteration replays the same graph with new densities
+    n0 = lens.launches
+    S2 = lens.forward([_dev(1.0 - r) for r in rhos])
+    assert lens.launches == n0 + 1 and _rel(S2, S) > 1e-3
+    assert _rel(S2, sum(lens.zone_focal(z) for z in range(len(zones)))) < 1e-12
