@@ -127,6 +127,11 @@ zda_status zda_set_wavelengths(zda_zone *zone, const double *lambda_host, int n_
 /* Source pulse g(t) = cos(2 pi f0 (t - t0)) exp(-(t - t0)^2 / (2 sigma_t^2)). */
 zda_status zda_set_pulse(zda_zone *zone, double f0, double sigma_t, double t0);
 
+/* Binarisation strength of the tanh projection for the next runs (the
+ * continuation of beta during a topology optimisation, "Results and
+ * Discussion"): beta <= 0 turns it off, 0 < eta < 1. */
+zda_status zda_zone_set_projection(zda_zone *zone, double beta, double eta);
+
 /* Sizes / layouts (workspace_bytes depends on wavelengths and n_steps). */
 zda_status zda_zone_query(const zda_zone *zone, zda_zone_info *info);
 zda_status zda_zone_workspace_bytes(const zda_zone *zone, size_t *bytes);
@@ -262,6 +267,19 @@ zda_status zda_lens_adjoint(zda_lens *lens, const double *dI_dfocal_host, float 
 /* zone z's own phasors S_z from the last zda_lens_forward (host copy). */
 zda_status zda_lens_zone_focal(const zda_lens *lens, int zone, double *focal_out_host);
 long long zda_lens_launch_count(const zda_lens *lens);   /* graph launches (or direct runs) issued */
+
+/* Focal-plane evaluation after zda_lens_forward (section "Centimeter-scale
+ * metalens": focusing efficiency within 3 FWHM, Eq. 9's Strehl ratio with the
+ * power transmitted through the whole lens).  pts_dev: n_pts (x, y) doubles
+ * in the focal plane (origin on the axis).  field_dev (caller-allocated,
+ * 2 * n_lambda * n_pts complex doubles) receives E_x for every wavelength
+ * and point, then E_y: Rayleigh-Sommerfeld (first kind) of each zone's
+ * azimuthal orders +-1 (its phi-averaged near field), integrated with
+ * n_phi_samples (>= 8) azimuthal samples, summed over zones.  p_trans_host
+ * (n_lambda doubles, may be NULL): (n/2) |E_t|^2 over all monitor annuli
+ * (all azimuthal orders), the transmitted power.  Synchronises `stream`. */
+zda_status zda_lens_focal_plane(zda_lens *lens, const double *pts_dev, int n_pts, int n_phi_samples,
+                                double *field_dev, double *p_trans_host, void *stream);
 
 /* Thread-local message of the last error ("" if none). */
 const char *zda_last_error(void);

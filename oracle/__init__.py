@@ -598,3 +598,92 @@ def gradient(spec, rho, nthreads=0, n_steps=None):
     g_rbar = adj["grad_rho_tilde"] * project_grad(spec, rbar)
     g_rho = conic_filter_T(spec, geom, g_rbar)
     return fwd["I"], g_rho, fwd, adj
+
+
+# --------------------------------------------------------------------------
+# a14: focal-plane field (off axis) and transmitted power
+# --------------------------------------------------------------------------
+def focal_plane_bruteforce(spec, geom, mon, pts):
+    """Physical focal-plane field (E_x, E_y) [n_lambda][n_pts] of one zone by
+    brute force: every wedge copy c of the monitor plane is rebuilt with its
+    Bloch phase e^{i m c tau} (all azimuthal orders kept), the physical phasor
+    at +w is Psi(+w) + conj(Psi(-w)) (m = +1 run plus its conjugate), and the
+    Rayleigh-Sommerfeld (first kind) kernel is summed over every site of the
+    full circle (midpoint radial weights at E_r, trapezoid at E_phi, the grid's
+    dphi).  For continuous axisymmetry the circle is sampled with n_phi_bor
+    points."""
+    s = spec
+    nl = geom.n_lambda
+    layer = np.searchsorted(np.asarray(s.layer_k0), s.monitor_k, side="right") - 1
+    n_top = math.sqrt(s.layer_eps[layer])
+    zf = s.focal - (s.monitor_k * s.dz - s.design_k1 * s.dz)
+    qr = np.zeros(s.n_r)
+    qr[geom.i_d0:geom.i_d1] = s.dr
+    qp = np.zeros(s.n_r + 1)
+    qp[geom.i_d0:geom.i_d1 + 1] = s.dr
+    qp[geom.i_d0] *= 0.5
+    qp[geom.i_d1] *= 0.5
+    qp = qp[:s.n_r]
+    pts = np.asarray(pts, dtype=np.float64).reshape(-1, 2)
+    if geom.bor:
+        ncopy, dphi, nphi = 1, 2 * math.pi / 256, 256
+    else:
+        ncopy, dphi, nphi = s.n_fold, geom.dphi, s.n_phi
+    ex = np.zeros((nl, len(pts)), complex)
+    ey = np.zeros((nl, len(pts)), complex)
+    for l in range(nl):
+        kk = 2 * math.pi * n_top / s.wavelengths[l]
+        Er = mon[l, 0] + np.conj(mon[l + nl, 0])           # [nr][nphi] physical phasors
+        Ep = mon[l, 1] + np.conj(mon[l + nl, 1])
+        for comp in (0, 1):
+            r = geom.r_h if comp == 0 else geom.r_n[:s.n_r]
+            w = qr if comp == 0 else qp
+            if geom.bor:
+                # the axis zone stores u: the physical field is u e^{i phi} + conj(u(-w)) e^{-i phi}
+                phis = dphi * np.arange(nphi)
+                up = mon[l, comp][:, 0][:, None] * np.exp(1j * phis)[None, :]
+                um = np.conj(mon[l + nl, comp][:, 0])[:, None] * np.exp(-1j * phis)[None, :]
+                F = up + um
+                ph = np.broadcast_to(phis, F.shape)
+            else:
+                base = geom.phi_n if comp == 0 else geom.phi_h
+                F = []
+                ph = []
+                for c in range(ncopy):
+                    # psi of copy c = e^{i m c tau} psi; its conjugate part gets the opposite phase
+                    Pp = mon[l, comp] * np.exp(1j * s.m * c * geom.tau)
+                    Pm = np.conj(mon[l + nl, comp] * np.exp(1j * s.m * c * geom.tau))
+                    F.append(Pp + Pm)
+                    ph.append(np.broadcast_to(base + c * geom.tau, Pp.shape))
+                F = np.concatenate(F, axis=1)
+                ph = np.concatenate(ph, axis=1)
+            cs, sn = np.cos(ph), np.sin(ph)
+            fx = F * cs if comp == 0 else -F * sn
+            fy = F * sn if comp == 0 else F * cs
+            X = r[:, None] * cs
+            Y = r[:, None] * sn
+            wt = (w * r)[:, None] * dphi
+            for p, (x, y) in enumerate(pts):
+                R = np.sqrt(zf * zf + (x - X) ** 2 + (y - Y) ** 2)
+                K = (1 / (2 * math.pi)) * (zf / R) * (1 / R - 1j * kk) * np.exp(1j * kk * R) / R
+                ex[l, p] += np.sum(K * fx * wt)
+                ey[l, p] += np.sum(K * fy * wt)
+    return ex, ey
+
+
+def transmitted_power(spec, geom, mon):
+    """(n/2) |E_t|^2 over the monitor annulus of the whole circle per
+    wavelength (plane-wave estimate of the transmitted flux)."""
+    s = spec
+    nl = geom.n_lambda
+    layer = np.searchsorted(np.asarray(s.layer_k0), s.monitor_k, side="right") - 1
+    n_top = math.sqrt(s.layer_eps[layer])
+    copies = 1.0 if geom.bor else float(s.n_fold)
+    out = np.zeros(nl)
+    for l in range(nl):
+        Er = mon[l, 0] + np.conj(mon[l + nl, 0])
+        Ep = mon[l, 1] + np.conj(mon[l + nl, 1])
+        pw = (np.abs(Er) ** 2 + np.abs(Ep) ** 2).sum(axis=1)
+        i0, i1 = geom.i_d0, geom.i_d1
+        out[l] = 0.5 * n_top * np.sum(pw[i0:i1] * geom.r_h[i0:i1] * s.dr * geom.dphi) * copies
+    return out

@@ -62,6 +62,7 @@ SIGNATURES = {
     "zda_set_wavelengths": (_i, [_vp, _dp, _i]),
     "zda_set_pulse": (_i, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "zda_zone_query": (_i, [_vp, ctypes.POINTER(ZoneInfo)]),
+    "zda_zone_set_projection": (_i, [_vp, ctypes.c_double, ctypes.c_double]),
     "zda_zone_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "zda_zone_bind_workspace": (_i, [_vp, _vp, ctypes.c_size_t]),
     "zda_forward": (_i, [_vp, _vp, _dp, _vp]),
@@ -90,6 +91,7 @@ SIGNATURES = {
     "zda_lens_adjoint": (_i, [_vp, _dp, ctypes.POINTER(_vp), _vp]),
     "zda_lens_zone_focal": (_i, [_vp, _i, _dp]),
     "zda_lens_launch_count": (ctypes.c_longlong, [_vp]),
+    "zda_lens_focal_plane": (_i, [_vp, _vp, _i, _i, _vp, _dp, _vp]),
     "zda_last_error": (ctypes.c_char_p, []),
 }
 

@@ -49,7 +49,7 @@ struct Layout {           // byte offsets inside the workspace
     size_t fields, psi_z, psi_r, fields2, psi_h2, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
         norm, src_rad, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
         ph_h, pulse, twiddle, adj_time, Gr, Gp, emph_n, emph_h, wt, beta_r, beta_p, g_in, partial, S,
-        status, total;
+        umean, pt_row, qr, qw, qp, qwp, kk, status, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -234,6 +234,13 @@ static void compute_layout(zda_zone &z)
     L.g_in = take(Q * sizeof(double2));
     L.partial = take(Q * nr * sizeof(double2));
     L.S = take(Q * sizeof(double2));
+    L.umean = take(Q * 2 * nr * sizeof(double2));
+    L.pt_row = take(Q * nr * sizeof(double));
+    L.qr = take(nr * sizeof(double));
+    L.qw = take(nr * sizeof(double));
+    L.qp = take(nr * sizeof(double));
+    L.qwp = take(nr * sizeof(double));
+    L.kk = take(Q * sizeof(double));
     L.status = take(sizeof(int) * 4);
     L.total = off;
 }
@@ -406,6 +413,21 @@ static zda_status upload(zda_zone &z)
         CUDA_TRY(put(z.L.Gr, gr.data(), gr.size() * 16));
         CUDA_TRY(put(z.L.Gp, gp.data(), gp.size() * 16));
         CUDA_TRY(put(z.L.wt, wt.data(), Q * 4));
+        // radial quadrature (r dr) of the focal-plane evaluation: midpoint at
+        // the E_r radii, trapezoid at the E_phi radii, over the design annulus
+        std::vector<double> qr(nr), qw(nr), qp(nr), qwp(nr), kk(Q);
+        for (int i = 0; i < nr; ++i) {
+            qr[i] = d.r_lo + (i + 0.5) * d.dr;
+            qw[i] = (i >= z.i_d0 && i < z.i_d1) ? qr[i] * d.dr : 0.0;
+            qp[i] = d.r_lo + i * d.dr;
+            qwp[i] = (i >= z.i_d0 && i <= z.i_d1) ? qp[i] * ((i == z.i_d0 || i == z.i_d1) ? 0.5 * d.dr : d.dr) : 0.0;
+        }
+        for (int q = 0; q < Q; ++q) kk[q] = 2 * M_PI * ntop / z.lambda[q % z.lambda.size()];
+        CUDA_TRY(put(z.L.qr, qr.data(), nr * 8));
+        CUDA_TRY(put(z.L.qw, qw.data(), nr * 8));
+        CUDA_TRY(put(z.L.qp, qp.data(), nr * 8));
+        CUDA_TRY(put(z.L.qwp, qwp.data(), nr * 8));
+        CUDA_TRY(put(z.L.kk, kk.data(), Q * 8));
     }
     z.tables_dirty = false;
     return ZDA_OK;
@@ -807,6 +829,15 @@ zda_status zda_set_pulse(zda_zone *z, double f0, double sigma_t, double t0)
     if (!z || !(f0 > 0) || !(sigma_t > 0)) return fail(ZDA_ERR_ARG, "bad pulse");
     z->f0 = f0; z->sigma = sigma_t; z->t0 = t0;
     z->tables_dirty = true;
+    z->have_forward = false;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_set_projection(zda_zone *z, double beta, double eta)
+{
+    if (!z || !(eta > 0 && eta < 1)) return fail(ZDA_ERR_ARG, "bad projection");
+    z->d.beta = beta;
+    z->d.eta = eta;
     z->have_forward = false;
     return ZDA_OK;
 }
@@ -1336,5 +1367,42 @@ zda_status zda_lens_adjoint(zda_lens *L, const double *dI, float *const *grad_rh
 }
 
 long long zda_lens_launch_count(const zda_lens *L) { return L ? L->launches : -1; }
+
+zda_status zda_lens_focal_plane(zda_lens *L, const double *pts_dev, int n_pts, int n_phi_samples, double *field_dev,
+                                double *p_trans_host, void *stream)
+{
+    if (!L || !pts_dev || n_pts < 1 || n_phi_samples < 8 || !field_dev) return fail(ZDA_ERR_ARG, "bad argument");
+    if (!L->have_forward) return fail(ZDA_ERR_STATE, "zda_lens_focal_plane needs a preceding zda_lens_forward");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nl = L->nq / 2;
+    double2 *ex = (double2 *)field_dev, *ey = ex + (size_t)nl * n_pts;
+    CUDA_TRY(cudaMemsetAsync(field_dev, 0, (size_t)2 * nl * n_pts * sizeof(double2), s));
+    std::vector<double> ptrans(nl, 0.0);
+    for (zda_zone *Z : L->zones) {
+        const zda_zone_desc &d = Z->d;
+        zda::launch_phi_means(P<float2>(*Z, Z->L.mon), P<double2>(*Z, Z->L.emph_n), P<double2>(*Z, Z->L.emph_h),
+                              Z->nq, d.n_r, d.n_phi, P<double2>(*Z, Z->L.umean), P<double>(*Z, Z->L.pt_row), s);
+        const double zf = d.focal - (d.monitor_k * d.dz - d.design_k1 * d.dz);
+        zda::launch_focal_plane(P<double2>(*Z, Z->L.umean), P<double>(*Z, Z->L.qr), P<double>(*Z, Z->L.qw),
+                                P<double>(*Z, Z->L.qp), P<double>(*Z, Z->L.qwp), d.n_r, nl, pts_dev, n_pts, zf,
+                                P<double>(*Z, Z->L.kk), n_phi_samples, ex, ey, s);
+        CUDA_TRY(cudaGetLastError());
+        Z->launches += 2;
+        // transmitted power: (n_top/2) |E_t|^2 over the annulus, whole circle
+        std::vector<double> row((size_t)nl * d.n_r);
+        CUDA_TRY(cudaMemcpyAsync(row.data(), Z->ws + Z->L.pt_row, row.size() * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        const double ntop = std::sqrt(layer_eps_at(d, d.monitor_k));
+        const double copies = d.n_fold == 0 ? 1.0 : (double)d.n_fold;
+        for (int l = 0; l < nl; ++l)
+            for (int i = Z->i_d0; i < Z->i_d1; ++i)
+                ptrans[l] += 0.5 * ntop * row[(size_t)l * d.n_r + i] * (d.r_lo + (i + 0.5) * d.dr) * d.dr * Z->dphi *
+                             copies;
+    }
+    if (p_trans_host)
+        for (int l = 0; l < nl; ++l) p_trans_host[l] = ptrans[l];
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return ZDA_OK;
+}
 
 }  // extern "C"

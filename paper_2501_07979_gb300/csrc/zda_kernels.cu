@@ -599,6 +599,130 @@ void launch_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, 
     k_lens_sum<<<1, 32, 0, s>>>(S, nzones, nq, out, status);
 }
 
+// ------------------------------------------------ focal-plane evaluation
+// Per zone: phi-means of the m = +1 run's monitor DFT, u_c(q, i) =
+// (1/n_phi) sum_j Psi_c(q, i, j) e^{-i phi} (E_r at phi_j, E_phi at
+// phi_{j+1/2}; no phase in the axis zone), and the transmitted-power density
+// sum over the row of |E_r|^2 + |E_phi|^2 of the physical phasor at +w_l,
+// Psi(+w) + conj(Psi(-w)).
+__global__ void k_phi_means(const float2 *__restrict__ mon, const double2 *__restrict__ emph_n,
+                            const double2 *__restrict__ emph_h, int nq, int nr, int nphi, double2 *umean,
+                            double *pt_row)
+{
+    const int i = blockIdx.x, q = blockIdx.y;
+    const size_t plane = (size_t)nr * nphi;
+    const int nl = nq / 2;
+    const float2 *er = mon + (size_t)q * 2 * plane + (size_t)i * nphi;
+    const float2 *ep = er + plane;
+    double2 sr = make_double2(0, 0), sp = make_double2(0, 0);
+    double pw = 0.0;
+    for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
+        const float2 a = er[j], b = ep[j];
+        const double2 pa = d_cmul(emph_n[j], make_double2(a.x, a.y));
+        const double2 pb = d_cmul(emph_h[j], make_double2(b.x, b.y));
+        sr.x += pa.x; sr.y += pa.y;
+        sp.x += pb.x; sp.y += pb.y;
+        if (q < nl) {                                   // physical phasor at +w_q
+            const float2 *er2 = mon + (size_t)(q + nl) * 2 * plane + (size_t)i * nphi;
+            const float2 *ep2 = er2 + plane;
+            const double xr = (double)a.x + er2[j].x, yr = (double)a.y - er2[j].y;
+            const double xp = (double)b.x + ep2[j].x, yp = (double)b.y - ep2[j].y;
+            pw += xr * xr + yr * yr + xp * xp + yp * yp;
+        }
+    }
+    const double2 tr = block_sum2(sr);
+    __syncthreads();
+    const double2 tp = block_sum2(sp);
+    __syncthreads();
+    const double2 tw = block_sum2(make_double2(pw, 0.0));
+    if (threadIdx.x == 0) {
+        umean[((size_t)q * 2 + 0) * nr + i] = make_double2(tr.x / nphi, tr.y / nphi);
+        umean[((size_t)q * 2 + 1) * nr + i] = make_double2(tp.x / nphi, tp.y / nphi);
+        if (q < nl) pt_row[(size_t)q * nr + i] = tw.x;
+    }
+}
+
+void launch_phi_means(const float2 *mon, const double2 *emph_n, const double2 *emph_h, int nq, int nr, int nphi,
+                      double2 *umean, double *pt_row, cudaStream_t s)
+{
+    dim3 g(nr, nq);
+    k_phi_means<<<g, 256, 0, s>>>(mon, emph_n, emph_h, nq, nr, nphi, umean, pt_row);
+}
+
+// Focal-plane field of one zone at points P = (x, y, z_f) above the monitor
+// plane: Rayleigh-Sommerfeld (first kind) over the zone's annulus with the
+// azimuthal orders +-1 of its near field,
+//   E_x(Q) = e^{i phi}(u+_r cos - u+_phi sin) + e^{-i phi}(u-_r cos - u-_phi sin)
+//   E_y(Q) = e^{i phi}(u+_r sin + u+_phi cos) + e^{-i phi}(u-_r sin + u-_phi cos)
+// with u+ = u(+w), u- = conj(u(-w)); each component integrated on its own
+// radial grid (weights wr, wp include r dr) and n_s phi samples.
+// Accumulates (E_x, E_y) into ex, ey [n_lambda][n_pts].
+__global__ void k_focal_plane(const double2 *__restrict__ umean, const double *__restrict__ rr,
+                              const double *__restrict__ wr, const double *__restrict__ rp,
+                              const double *__restrict__ wp, int nr, int nl, const double *__restrict__ pts,
+                              int npts, double zf, const double *__restrict__ kk, int ns, double2 *ex, double2 *ey)
+{
+    const int pidx = blockIdx.x, l = blockIdx.y;
+    const double px = pts[2 * pidx], py = pts[2 * pidx + 1];
+    const double k = kk[l];
+    const double2 *upr = umean + ((size_t)l * 2 + 0) * nr, *upp = umean + ((size_t)l * 2 + 1) * nr;
+    const double2 *umr = umean + ((size_t)(l + nl) * 2 + 0) * nr, *ump = umean + ((size_t)(l + nl) * 2 + 1) * nr;
+    double2 ax = make_double2(0, 0), ay = make_double2(0, 0);
+    const double dphi = 2.0 * M_PI / ns;
+    const size_t total = (size_t)2 * nr * ns;
+    for (size_t t = threadIdx.x; t < total; t += blockDim.x) {
+        const int comp = (int)(t / ((size_t)nr * ns));
+        const size_t rem = t - (size_t)comp * nr * ns;
+        const int i = (int)(rem / ns), s = (int)(rem % ns);
+        const double w = comp == 0 ? wr[i] : wp[i];
+        if (w == 0.0) continue;
+        const double r = comp == 0 ? rr[i] : rp[i];
+        double sn, cs;
+        sincos(s * dphi, &sn, &cs);
+        const double dx = px - r * cs, dy = py - r * sn;
+        const double R = sqrt(zf * zf + dx * dx + dy * dy);
+        double sk, ck;
+        sincos(k * R, &sk, &ck);
+        // K = (1/2pi)(z/R)(1/R - ik) e^{ikR}/R, times the quadrature weight
+        const double f = w * dphi * zf / (2.0 * M_PI * R * R);
+        const double2 K = d_cmul(make_double2(f / R, -f * k), make_double2(ck, sk));
+        const double2 ep = make_double2(cs, sn), em = make_double2(cs, -sn);     // e^{+-i phi}
+        double2 ux, uy;
+        if (comp == 0) {        // u_r terms: cos / sin
+            const double2 a = d_cmul(ep, upr[i]);
+            const double2 umc = make_double2(umr[i].x, -umr[i].y);
+            const double2 b = d_cmul(em, umc);
+            ux = make_double2((a.x + b.x) * cs, (a.y + b.y) * cs);
+            uy = make_double2((a.x + b.x) * sn, (a.y + b.y) * sn);
+        } else {                // u_phi terms: -sin / cos
+            const double2 a = d_cmul(ep, upp[i]);
+            const double2 umc = make_double2(ump[i].x, -ump[i].y);
+            const double2 b = d_cmul(em, umc);
+            ux = make_double2(-(a.x + b.x) * sn, -(a.y + b.y) * sn);
+            uy = make_double2((a.x + b.x) * cs, (a.y + b.y) * cs);
+        }
+        const double2 cx = d_cmul(K, ux), cy = d_cmul(K, uy);
+        ax.x += cx.x; ax.y += cx.y;
+        ay.x += cy.x; ay.y += cy.y;
+    }
+    const double2 sx = block_sum2(ax);
+    __syncthreads();
+    const double2 sy = block_sum2(ay);
+    if (threadIdx.x == 0) {
+        double2 *ox = ex + (size_t)l * npts + pidx, *oy = ey + (size_t)l * npts + pidx;
+        ox->x += sx.x; ox->y += sx.y;
+        oy->x += sy.x; oy->y += sy.y;
+    }
+}
+
+void launch_focal_plane(const double2 *umean, const double *rr, const double *wr, const double *rp, const double *wp,
+                        int nr, int nl, const double *pts, int npts, double zf, const double *kk, int ns, double2 *ex,
+                        double2 *ey, cudaStream_t s)
+{
+    dim3 g(npts, nl);
+    k_focal_plane<<<g, 256, 0, s>>>(umean, rr, wr, rp, wp, nr, nl, pts, npts, zf, kk, ns, ex, ey);
+}
+
 __global__ void k_status_check(const float *x, size_t n, int *status)
 {
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -141,3 +141,20 @@ class Lens:
     def launches(self):
         from . import _lib
         return int(_lib.lib().zda_lens_launch_count(self.handle))
+
+    def focal_plane(self, pts_xy, n_phi_samples=128):
+        """Focal-plane field of the last forward at points (x, y) (n x 2):
+        returns (E_x, E_y) as complex arrays [n_lambda][n_pts] and the
+        transmitted power per wavelength."""
+        import torch
+        from . import _lib
+        from ._lib import check
+        pts = torch.tensor(np.asarray(pts_xy, dtype=np.float64).reshape(-1, 2), device=self.zones[0].device)
+        n = pts.shape[0]
+        nl = self.n_freq // 2
+        out = torch.empty((2, nl, n, 2), dtype=torch.float64, device=pts.device)
+        pt = (ctypes.c_double * nl)()
+        check(_lib.lib().zda_lens_focal_plane(self.handle, ctypes.c_void_p(pts.data_ptr()), int(n), int(n_phi_samples),
+                                              ctypes.c_void_p(out.data_ptr()), pt, self._stream()))
+        o = out.cpu().numpy()
+        return o[0, ..., 0] + 1j * o[0, ..., 1], o[1, ..., 0] + 1j * o[1, ..., 1], np.array(pt[:])

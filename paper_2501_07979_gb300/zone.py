@@ -192,6 +192,9 @@ class Zone:
         check(_lib.lib().zda_zone_time_steps(self.handle, int(steps), ctypes.byref(ms), _stream()))
         return ms.value
 
+    def set_projection(self, beta, eta=0.5):
+        check(_lib.lib().zda_zone_set_projection(self.handle, float(beta), float(eta)))
+
     def set_wait_limit(self, polls, inject_timeout=False):
         check(_lib.lib().zda_zone_set_wait_limit(self.handle, int(polls), int(bool(inject_timeout))))
 

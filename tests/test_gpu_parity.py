@@ -378,3 +378,59 @@ def test_lens_equals_sum_of_zones_and_oracle(use_graph, kernel):
     S2 = lens.forward([_dev(1.0 - r) for r in rhos])
     assert lens.launches == n0 + 1 and _rel(S2, S) > 1e-3
     assert _rel(S2, sum(lens.zone_focal(z) for z in range(len(zones)))) < 1e-12
+
+
+def test_lens_focal_plane_matches_bruteforce_oracle():
+    """Off-axis focal-plane field of a lens (axis zone + two wedge zones):
+    the GPU's azimuthal-order +-1 quadrature against the oracle's brute-force
+    sum over every site of the full circle; transmitted power likewise."""
+    from paper_2501_07979_gb300.lens import Lens
+    specs = _lens_specs()
+    rhos = [smoothed_rho(s.n_r_design, s.n_phi, 40 + z, mode="minmax") for z, s in enumerate(specs)]
+    zones = [_zone(s) for s in specs]
+    lens = Lens(zones)
+    lens.forward([_dev(r) for r in rhos])
+    pts = [(0.0, 0.0), (0.4, 0.0), (0.0, 0.7), (1.1, -0.5), (2.0, 1.0)]
+    ex, ey, pt = lens.focal_plane(pts, n_phi_samples=256)
+    rx = ry = 0
+    p_ref = 0
+    for s, r in zip(specs, rhos):
+        f = O.forward(s, r)
+        a, b = O.focal_plane_bruteforce(s, f["geom"], f["mon"], pts)
+        rx, ry = rx + a, ry + b
+        p_ref = p_ref + O.transmitted_power(s, f["geom"], f["mon"])
+    assert _rel(ex, rx) < 1e-4 and _rel(ey, ry) < 1e-4
+    assert _rel(pt, p_ref) < 1e-4
+
+
+def test_topopt_on_a_zone_increases_focal_intensity():
+    from paper_2501_07979_gb300.topopt import TopOpt
+    spec = GRAD_SPECS["tiny2"]
+    z = _zone(spec)
+    rho0 = smoothed_rho(spec.n_r_design, spec.n_phi, 5, mode="minmax")
+
+    def vg(rhos):
+        I, g = z.iteration(_dev(rhos[0]))
+        return I, [g.cpu().numpy()]
+
+    opt = TopOpt(vg, [rho0], lr=0.05, set_beta=z.set_projection, schedule=lambda it: 4.0)
+    hist = opt.run(6)
+    assert hist[-1]["objective"] > 1.2 * hist[0]["objective"]
+
+
+def test_lens_evaluation_quantities_are_consistent():
+    """FE, relative FE, transmittance and Strehl from the focal-plane field:
+    FE = transmittance x relative FE, all positive; FWHM finite."""
+    from paper_2501_07979_gb300.evaluate import evaluate_lens, incident_intensity
+    from paper_2501_07979_gb300.lens import Lens
+    specs = _lens_specs()
+    rhos = [smoothed_rho(s.n_r_design, s.n_phi, 50 + z, mode="minmax") for z, s in enumerate(specs)]
+    lens = Lens([_zone(s) for s in specs])
+    lens.forward([_dev(r) for r in rhos])
+    inc = incident_intensity(specs[1])
+    R = specs[-1].r_lo + (specs[-1].n_r - specs[-1].pml_r_out) * specs[-1].dr
+    res, xs, I = evaluate_lens(lens, R, specs[0].focal, inc, n_rad=16, n_ang=4)
+    for r in res:
+        assert math.isfinite(r["fwhm"]) and r["fwhm"] > 0
+        assert 0 < r["focusing_efficiency"] and 0 < r["relative_efficiency"] and 0 < r["strehl"]
+        assert abs(r["focusing_efficiency"] - r["transmittance"] * r["relative_efficiency"]) < 1e-12

@@ -462,3 +462,17 @@ def test_axis_zone_adjoint_matches_central_differences():
     assert _directional_error(spec) < 1e-3
     errs = _fd_errors(spec, [(0, 0), (3, 0), (9, 0), (15, 0)])
     assert errs.max() < 2e-3, errs
+
+
+def test_focal_plane_on_axis_equals_on_axis_transform():
+    """The brute-force focal-plane field at the axis equals the on-axis
+    transform: (E_x, E_y) = c+ (1, i) + c- (1, -i), c+ = S(+w), c- = conj(S(-w))."""
+    spec = zone_tiny(n_steps=500, wavelengths=(0.9, 1.1), pulse_sigma=0.4, pulse_t0=1.6, focal=8.0)
+    rho = smoothed_rho(spec.n_r_design, spec.n_phi, 3, mode="binary")
+    f = O.forward(spec, rho)
+    g = f["geom"]
+    ex, ey = O.focal_plane_bruteforce(spec, g, f["mon"], [(0.0, 0.0)])
+    nl = g.n_lambda
+    cp, cm = f["S"][:nl], np.conj(f["S"][nl:])
+    assert np.allclose(ex[:, 0], cp + cm, rtol=1e-10, atol=1e-14)
+    assert np.allclose(ey[:, 0], 1j * (cp - cm), rtol=1e-10, atol=1e-14)
