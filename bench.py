@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
-    ap.add_argument("--kernel", default="default", choices=["default", "split", "fused2", "fused4"],
+    ap.add_argument("--kernel", default="default", choices=["default", "split", "split1", "fused2", "fused4"],
                     help="time-step kernel (default: the library's choice for the zone)")
     return ap.parse_args()
 
@@ -211,7 +211,7 @@ def run_ours(a):
 
     spec = workload(a.time_steps)
     zone = Zone(spec, device=local)
-    kern = {"split": (0, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0)}.get(a.kernel)
+    kern = {"split": (0, 2, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0)}.get(a.kernel)
     if kern is not None:
         zone.set_kernel(*kern)
     variant, tile_phi, i_ranges = zone.get_kernel()
@@ -289,7 +289,8 @@ def run_ours(a):
         b_main, b_other = algorithmic_bytes_stream(spec), algorithmic_bytes_dft(spec, nq)
         main_ms, other_ms = a_avg_ms, b_avg_ms
     else:
-        main_name, other_name = "k_update_e", "k_update_h"
+        pair = variant == 0 and spec.n_z % 2 == 0 and spec.pml_z % 2 == 0
+        main_name, other_name = ("k_update_e_pair", "k_update_h_pair") if pair else ("k_update_e", "k_update_h")
         b_main, b_other = algorithmic_bytes_e(spec, nq), algorithmic_bytes_h(spec)
         main_ms, other_ms = b_avg_ms, a_avg_ms
     ach_main = b_main / (main_ms * 1e-3) / 1e9
@@ -311,7 +312,8 @@ def run_ours(a):
                          "sampled_launches": n_timed,
                          "other_kernel": {"kernel": other_name, "achieved": ach_other, "frac": ach_other / peak,
                                           "avg_launch_ms": other_ms, "algorithmic_bytes_per_launch": b_other}},
-            "step_kernel": {"variant": "fused" if variant == 1 else "split", "tile_phi": tile_phi,
+            "step_kernel": {"variant": {0: "split, two z-cells per thread", 1: "fused",
+                                        2: "split, one z-cell per thread"}[variant], "tile_phi": tile_phi,
                             "i_ranges": i_ranges},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "focal_intensity": I}

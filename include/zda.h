@@ -195,7 +195,10 @@ zda_status zda_copy_design_dft(zda_zone *zone, int which, float *out_dev, void *
 long long zda_zone_launch_count(const zda_zone *zone);
 
 /* Time-step kernel of the zone.  variant 0 (default): two launches per step
- * (H update, E update), in place.  variant 1 (annular zones, n_z <= 256):
+ * (H update, E update), in place, two z-cells per thread with 16-byte loads
+ * when n_z and pml_z are even (wedge zones), else one z-cell per thread;
+ * variant 2: the same with one z-cell per thread always.  variant 1 (annular
+ * zones, n_z <= 256):
  * one fused launch per step (E and H updated together, ping-pong field
  * buffers, streaming along r; tile_phi in {2, 4} phi rows per thread block,
  * i_ranges radius ranges per phi tile, 0 = as many as fit in one wave).

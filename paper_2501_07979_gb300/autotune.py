@@ -18,7 +18,7 @@ def shape_key(spec):
 
 
 def candidates(spec):
-    cands = [(0, 2, 0)]
+    cands = [(0, 2, 0), (2, 2, 0)]
     if spec.n_fold > 0 and spec.n_z % 2 == 0 and spec.n_z <= 256:
         for tj in (2, 4):
             for ir in (0, 2, 4):

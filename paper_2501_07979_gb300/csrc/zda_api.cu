@@ -73,6 +73,7 @@ struct zda_zone {
     // time-step kernel: 0 = split H/E launches (default), 1 = fused single launch
     int variant = 0, tile_phi = 2, i_ranges = 0;
     int wait_limit = 1 << 22, inject_timeout = 0;   // bounded mbarrier waits of the fused step
+    bool pair_kernels = true;       // split step: two z-cells per thread where the grid allows
     int last_parity = 0;            // fused runs: which buffer holds the final fields
     // optional CUDA-event timing of every `time_every`-th H/E launch pair
     int time_every = 0;
@@ -664,6 +665,7 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
         return ZDA_OK;
     }
     z.last_parity = 0;
+    const bool pair = z.pair_kernels && zda::pair_kernels_apply(p);
     for (int n = 0; n < z.d.n_steps; ++n) {
         const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
         int slot = 0;
@@ -673,9 +675,11 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
             timing_drain_slot(z, slot);
             CUDA_TRY(cudaEventRecord(z.ev[3 * slot], s));
         }
-        zda::launch_update_h(p, s);
+        if (pair) zda::launch_update_h_pair(p, s);
+        else zda::launch_update_h(p, s);
         if (timed) CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 1], s));
-        zda::launch_update_e(p, n, s);
+        if (pair) zda::launch_update_e_pair(p, n, s);
+        else zda::launch_update_e(p, n, s);
         if (timed) {
             CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 2], s));
             z.ev_pending[slot] = 1;
@@ -1008,7 +1012,16 @@ long long zda_zone_launch_count(const zda_zone *z) { return z ? z->launches : -1
 
 zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ranges)
 {
-    if (!z || (variant != 0 && variant != 1) || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
+    if (!z || variant < 0 || variant > 2 || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
+    if (variant == 2) {                      // split step, one z-cell per thread
+        z->variant = 0;
+        z->pair_kernels = false;
+        z->tile_phi = tile_phi;
+        z->i_ranges = i_ranges;
+        z->have_forward = false;
+        return ZDA_OK;
+    }
+    z->pair_kernels = true;
     if (variant == 1) {
         if (z->d.n_fold == 0) return fail(ZDA_ERR_ARG, "the axis zone (continuous axisymmetry) uses the split step");
         if (tile_phi != 2 && tile_phi != 4) return fail(ZDA_ERR_ARG, "fused step: tile_phi must be 2 or 4");
@@ -1016,7 +1029,7 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
         if (z->d.n_z % 2) return fail(ZDA_ERR_ARG, "fused step needs an even n_z (16-byte bulk copies)");
     }
     z->variant = variant;
-    z->tile_phi = variant == 1 ? tile_phi : z->tile_phi;
+    z->tile_phi = tile_phi;
     z->i_ranges = i_ranges;
     z->have_forward = false;
     return ZDA_OK;
@@ -1068,7 +1081,7 @@ zda_status zda_zone_set_wait_limit(zda_zone *z, int polls, int inject_timeout)
 zda_status zda_zone_get_kernel(const zda_zone *z, int *variant, int *tile_phi, int *i_ranges)
 {
     if (!z || !variant || !tile_phi || !i_ranges) return fail(ZDA_ERR_ARG, "null argument");
-    *variant = z->variant;
+    *variant = (z->variant == 0 && !z->pair_kernels) ? 2 : z->variant;
     *tile_phi = z->tile_phi;
     *i_ranges = z->variant == 1 ? auto_i_ranges(*z) : 0;
     return ZDA_OK;
@@ -1146,7 +1159,7 @@ static size_t lens_ws_total(const zda_lens &L) { return lens_ws_status(L) + 256;
 
 static std::vector<long long> zone_stamp(const zda_zone &z)
 {
-    return {(long long)(uintptr_t)z.ws, z.variant, z.tile_phi, z.i_ranges, z.d.n_steps, z.nq,
+    return {(long long)(uintptr_t)z.ws, z.variant, z.pair_kernels, z.tile_phi, z.i_ranges, z.d.n_steps, z.nq,
             z.wait_limit, z.inject_timeout, (long long)z.lambda.size()};
 }
 
@@ -1187,6 +1200,7 @@ static zda_status lens_run(zda_lens &L, cudaGraphExec_t &exec, std::vector<std::
         if (st) return st;
         CUDA_TRY(cudaEventRecord(L.events[0], s0));
         CUDA_TRY(cudaStreamWaitEvent(user, L.events[0], 0));
+        L.launches++;
         return ZDA_OK;
     }
     if (!exec || !stamps_match(L, stamp)) {

@@ -93,6 +93,10 @@ struct StepParams {
 // kernels (zda_kernels.cu)
 void launch_update_h(const StepParams &p, cudaStream_t s);
 void launch_update_e(const StepParams &p, int n, cudaStream_t s);
+// two z-cells per thread (zda_pair.cu): even n_z, even pml_z, wedge zones
+bool pair_kernels_apply(const StepParams &p);
+void launch_update_h_pair(const StepParams &p, cudaStream_t s);
+void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s);
 
 struct FilterParams {
     int nrd, nphi, di_max, dj_max;

@@ -1,0 +1,277 @@
+// Split step kernels, two z-cells per thread (sm_103a).
+//
+// Same scheme and arithmetic as k_update_h / k_update_e (one thread per Yee
+// cell), but each thread owns the z-cells (2 kp, 2 kp + 1) and moves every
+// field component as one aligned 16-byte float4: half the load/store
+// instructions and twice the bytes in flight per instruction, which is what
+// the one-cell kernels lack (they are latency-bound at 48-59 % of DRAM
+// bandwidth with traffic equal to the algorithmic bytes).  The z-neighbour
+// outside the pair comes from one extra 8-byte load (an L1 hit).  Needs an
+// even n_z and an even z-PML width, so that a pair never straddles a CPML
+// slab boundary; otherwise the one-cell kernels run.
+#include "zda_internal.h"
+
+namespace zda {
+
+#define PX 16
+#define PY 16
+
+struct C2 { float2 a, b; };                      // the pair (k, k+1)
+
+__device__ __forceinline__ C2 ld4(const float2 *p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return C2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ C2 ld4rw(const float2 *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return C2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st4(float2 *p, C2 c)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(c.a.x, c.a.y, c.b.x, c.b.y);
+}
+__device__ __forceinline__ C2 cmul2(float2 s, C2 c) { return C2{c_mul(s, c.a), c_mul(s, c.b)}; }
+
+__global__ void __launch_bounds__(PX * PY, 4) k_update_h_pair(const StepParams p)
+{
+    const int kp = blockIdx.x * PX + threadIdx.x;
+    const int j = blockIdx.y * PY + threadIdx.y;
+    const int i = blockIdx.z;
+    const int nz = p.nz, nphi = p.nphi;
+    const int k = 2 * kp;
+    if (k >= nz || j >= nphi) return;
+    const size_t sj = (size_t)nz, si = (size_t)nphi * nz;
+    const size_t c = (size_t)i * si + (size_t)j * sj + k;
+    const float2 zero = make_float2(0.f, 0.f);
+
+    const C2 er = ld4(p.f.Er + c), ep = ld4(p.f.Ep + c), ez = ld4(p.f.Ez + c);
+    C2 ez_jp, er_jp;
+    if (j + 1 < nphi) {
+        ez_jp = ld4(p.f.Ez + c + sj);
+        er_jp = ld4(p.f.Er + c + sj);
+    } else {
+        const size_t c0 = c - (size_t)(nphi - 1) * sj;
+        ez_jp = cmul2(p.bloch, ld4(p.f.Ez + c0));
+        er_jp = cmul2(p.bloch, ld4(p.f.Er + c0));
+    }
+    const bool kin2 = k + 2 < nz, iin = i + 1 < p.nr;
+    const float2 ep_k2 = kin2 ? __ldg(p.f.Ep + c + 2) : zero;     // z-neighbour of the second cell
+    const float2 er_k2 = kin2 ? __ldg(p.f.Er + c + 2) : zero;
+    const C2 ez_ip = iin ? ld4(p.f.Ez + c + si) : C2{zero, zero};
+    const C2 ep_ip = iin ? ld4(p.f.Ep + c + si) : C2{zero, zero};
+    const float irn = __ldg(p.t.inv_r_n + i), irh = __ldg(p.t.inv_r_h + i);
+    const int kz = (k < p.pz) ? k : ((k >= nz - p.pz) ? k - (nz - 2 * p.pz) : -1);
+    const int ir = (i < p.pr_in) ? i : ((i >= p.nr - p.pr_out) ? i - (p.nr - p.pr_in - p.pr_out) : -1);
+    const float dt = p.dt;
+    const size_t zx = ((size_t)i * nphi + j) * (2 * p.pz) + (kz >= 0 ? kz : 0);
+    const size_t rx = ((size_t)(ir >= 0 ? ir : 0) * nphi + j) * nz + k;
+    float bzh[2] = {0.f, 0.f}, czh[2] = {0.f, 0.f};
+    if (kz >= 0) {
+        bzh[0] = __ldg(p.t.bz_h + k); bzh[1] = __ldg(p.t.bz_h + k + 1);
+        czh[0] = __ldg(p.t.cz_h + k); czh[1] = __ldg(p.t.cz_h + k + 1);
+    }
+    const float brh = ir >= 0 ? __ldg(p.t.br_h + i) : 0.f, crh = ir >= 0 ? __ldg(p.t.cr_h + i) : 0.f;
+
+    const float2 EP[3] = {ep.a, ep.b, ep_k2}, ER[3] = {er.a, er.b, er_k2};
+    const float2 EZ[2] = {ez.a, ez.b}, EZJ[2] = {ez_jp.a, ez_jp.b}, ERJ[2] = {er_jp.a, er_jp.b};
+    const float2 EZI[2] = {ez_ip.a, ez_ip.b}, EPI[2] = {ep_ip.a, ep_ip.b};
+    C2 hr = ld4rw(p.f.Hr + c), hp = ld4rw(p.f.Hp + c), hz = ld4rw(p.f.Hz + c);
+    float2 *HR[2] = {&hr.a, &hr.b}, *HP[2] = {&hp.a, &hp.b}, *HZ[2] = {&hz.a, &hz.b};
+    C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
+    if (kz >= 0) { ps_r = ld4rw(p.psi.hr_z + zx); ps_p = ld4rw(p.psi.hp_z + zx); }
+    if (ir >= 0) { ps_pr = ld4rw(p.psi.hp_r + rx); ps_zr = ld4rw(p.psi.hz_r + rx); }
+    float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
+    float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        // H_r
+        {
+            const float2 dph = c_scale(c_sub(EZJ[u], EZ[u]), irn * p.inv_dphi);
+            float2 dz = c_scale(c_sub(EP[u + 1], EP[u]), p.inv_dz);
+            if (kz >= 0) {
+                *PR[u] = c_add(c_scale(*PR[u], bzh[u]), c_scale(dz, czh[u]));
+                dz = c_add(dz, *PR[u]);
+            }
+            *HR[u] = c_sub(*HR[u], c_scale(c_sub(dph, dz), dt));
+        }
+        // H_phi
+        {
+            float2 dz = c_scale(c_sub(ER[u + 1], ER[u]), p.inv_dz);
+            float2 drr = c_scale(c_sub(EZI[u], EZ[u]), p.inv_dr);
+            if (kz >= 0) {
+                *PP[u] = c_add(c_scale(*PP[u], bzh[u]), c_scale(dz, czh[u]));
+                dz = c_add(dz, *PP[u]);
+            }
+            if (ir >= 0) {
+                *PPR[u] = c_add(c_scale(*PPR[u], brh), c_scale(drr, crh));
+                drr = c_add(drr, *PPR[u]);
+            }
+            *HP[u] = c_sub(*HP[u], c_scale(c_sub(dz, drr), dt));
+        }
+        // H_z
+        {
+            float2 drr = c_add(c_scale(c_sub(EPI[u], EP[u]), p.inv_dr), c_scale(c_add(EPI[u], EP[u]), 0.5f * irh));
+            const float2 dph = c_scale(c_sub(ERJ[u], ER[u]), irh * p.inv_dphi);
+            if (ir >= 0) {
+                *PZR[u] = c_add(c_scale(*PZR[u], brh), c_scale(drr, crh));
+                drr = c_add(drr, *PZR[u]);
+            }
+            *HZ[u] = c_sub(*HZ[u], c_scale(c_sub(drr, dph), dt));
+        }
+    }
+    st4(p.f.Hr + c, hr);
+    st4(p.f.Hp + c, hp);
+    st4(p.f.Hz + c, hz);
+    if (kz >= 0) { st4(p.psi.hr_z + zx, ps_r); st4(p.psi.hp_z + zx, ps_p); }
+    if (ir >= 0) { st4(p.psi.hp_r + rx, ps_pr); st4(p.psi.hz_r + rx, ps_zr); }
+}
+
+__global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p, const int n)
+{
+    const int kp = blockIdx.x * PX + threadIdx.x;
+    const int j = blockIdx.y * PY + threadIdx.y;
+    const int i = blockIdx.z;
+    const int nz = p.nz, nphi = p.nphi, nr = p.nr;
+    const int k = 2 * kp;
+    if (k >= nz || j >= nphi) return;
+    const size_t sj = (size_t)nz, si = (size_t)nphi * nz;
+    const size_t c = (size_t)i * si + (size_t)j * sj + k;
+    const float2 zero = make_float2(0.f, 0.f);
+
+    const C2 hr = ld4(p.f.Hr + c), hp = ld4(p.f.Hp + c), hz = ld4(p.f.Hz + c);
+    C2 hz_jm, hr_jm;
+    if (j > 0) {
+        hz_jm = ld4(p.f.Hz + c - sj);
+        hr_jm = ld4(p.f.Hr + c - sj);
+    } else {
+        const size_t c1 = c + (size_t)(nphi - 1) * sj;
+        hz_jm = cmul2(p.bloch_inv, ld4(p.f.Hz + c1));
+        hr_jm = cmul2(p.bloch_inv, ld4(p.f.Hr + c1));
+    }
+    const float2 hp_km = (k > 0) ? __ldg(p.f.Hp + c - 1) : zero;     // z-neighbour of the first cell
+    const float2 hr_km = (k > 0) ? __ldg(p.f.Hr + c - 1) : zero;
+    const C2 hz_im = (i > 0) ? ld4(p.f.Hz + c - si) : C2{zero, zero};
+    const C2 hp_im = (i > 0) ? ld4(p.f.Hp + c - si) : C2{zero, zero};
+    const float irn = __ldg(p.t.inv_r_n + i), irh = __ldg(p.t.inv_r_h + i);
+    const int kz = (k < p.pz) ? k : ((k >= nz - p.pz) ? k - (nz - 2 * p.pz) : -1);
+    const int ir = (i < p.pr_in) ? i : ((i >= nr - p.pr_out) ? i - (nr - p.pr_in - p.pr_out) : -1);
+    const float dt = p.dt;
+    const size_t ij = (size_t)i * nphi + j;
+    const size_t zx = ij * (2 * p.pz) + (kz >= 0 ? kz : 0);
+    const size_t rx = ((size_t)(ir >= 0 ? ir : 0) * nphi + j) * nz + k;
+
+    const float2 HP[3] = {hp_km, hp.a, hp.b}, HRk[3] = {hr_km, hr.a, hr.b};   // index u+1 = cell u
+    const float2 HZ[2] = {hz.a, hz.b}, HZJ[2] = {hz_jm.a, hz_jm.b}, HRJ[2] = {hr_jm.a, hr_jm.b};
+    const float2 HZI[2] = {hz_im.a, hz_im.b}, HPI[2] = {hp_im.a, hp_im.b};
+    C2 er = ld4rw(p.f.Er + c), ep = ld4rw(p.f.Ep + c), ez = ld4rw(p.f.Ez + c);
+    float2 *ER[2] = {&er.a, &er.b}, *EP[2] = {&ep.a, &ep.b}, *EZ[2] = {&ez.a, &ez.b};
+    C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
+    if (kz >= 0) { ps_r = ld4rw(p.psi.er_z + zx); ps_p = ld4rw(p.psi.ep_z + zx); }
+    if (ir >= 0) { ps_pr = ld4rw(p.psi.ep_r + rx); ps_zr = ld4rw(p.psi.ez_r + rx); }
+    float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
+    float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
+    const float rbr = __ldg(p.rb_r + ij), rbp = __ldg(p.rb_p + ij), rbz = __ldg(p.rb_z + ij);
+    const float brn = ir >= 0 ? __ldg(p.t.br_n + i) : 0.f, crn = ir >= 0 ? __ldg(p.t.cr_n + i) : 0.f;
+
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int kk = k + u;
+        float2 jr = zero, jp = zero;
+        if (kk == p.src_k) {
+            if (p.src_mode == SRC_PLANE_WAVE) {
+                const float a = __ldg(p.t.pulse + n) * p.src_scale;
+                const float2 pn = p.t.ph_n[j], ph = p.t.ph_h[j];
+                jr = c_scale(pn, a);
+                jp = make_float2(-ph.y * a, ph.x * a);
+            } else if (p.src_mode == SRC_ADJOINT) {
+                float2 sr = zero, sp = zero;
+                const float2 *kt = p.t.adj_time + (size_t)n * p.nq;
+                for (int q = 0; q < p.nq; ++q) {
+                    const float2 kq = kt[q];
+                    sr = c_fma(p.beta_r[(size_t)q * nr + i], kq, sr);
+                    sp = c_fma(p.beta_p[(size_t)q * nr + i], kq, sp);
+                }
+                jr = c_mul(p.t.ph_n[j], sr);
+                jp = c_mul(p.t.ph_h[j], sp);
+            }
+        }
+        const float bzn = kz >= 0 ? __ldg(p.t.bz_n + kk) : 0.f, czn = kz >= 0 ? __ldg(p.t.cz_n + kk) : 0.f;
+        if (kk > 0) {                                       // E_r
+            const float2 dph = c_scale(c_sub(HZ[u], HZJ[u]), irh * p.inv_dphi);
+            float2 dz = c_scale(c_sub(HP[u + 1], HP[u]), p.inv_dz);
+            if (kz >= 0) {
+                *PR[u] = c_add(c_scale(*PR[u], bzn), c_scale(dz, czn));
+                dz = c_add(dz, *PR[u]);
+            }
+            const float ie = 1.0f / (__ldg(p.t.a_n + kk) + __ldg(p.t.d_n + kk) * rbr);
+            *ER[u] = c_add(*ER[u], c_scale(c_sub(c_sub(dph, dz), jr), dt * ie));
+        }
+        if (i > 0 && kk > 0) {                              // E_phi
+            float2 dz = c_scale(c_sub(HRk[u + 1], HRk[u]), p.inv_dz);
+            float2 drr = c_scale(c_sub(HZ[u], HZI[u]), p.inv_dr);
+            if (kz >= 0) {
+                *PP[u] = c_add(c_scale(*PP[u], bzn), c_scale(dz, czn));
+                dz = c_add(dz, *PP[u]);
+            }
+            if (ir >= 0) {
+                *PPR[u] = c_add(c_scale(*PPR[u], brn), c_scale(drr, crn));
+                drr = c_add(drr, *PPR[u]);
+            }
+            const float ie = 1.0f / (__ldg(p.t.a_n + kk) + __ldg(p.t.d_n + kk) * rbp);
+            *EP[u] = c_add(*EP[u], c_scale(c_sub(c_sub(dz, drr), jp), dt * ie));
+        }
+        if (i > 0) {                                        // E_z
+            float2 drr = c_add(c_scale(c_sub(HP[u + 1], HPI[u]), p.inv_dr),
+                               c_scale(c_add(HP[u + 1], HPI[u]), 0.5f * irn));
+            const float2 dph = c_scale(c_sub(HRk[u + 1], HRJ[u]), irn * p.inv_dphi);
+            if (ir >= 0) {
+                *PZR[u] = c_add(c_scale(*PZR[u], brn), c_scale(drr, crn));
+                drr = c_add(drr, *PZR[u]);
+            }
+            const float ie = 1.0f / (__ldg(p.t.a_c + kk) + __ldg(p.t.d_c + kk) * rbz);
+            *EZ[u] = c_add(*EZ[u], c_scale(c_sub(drr, dph), dt * ie));
+        }
+    }
+    st4(p.f.Er + c, er);
+    st4(p.f.Ep + c, ep);
+    st4(p.f.Ez + c, ez);
+    if (kz >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
+    if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
+
+    // running DFTs of E^{n+1}
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int kk = k + u;
+        if (p.mon && kk == p.mon_k) {
+            const size_t plane = (size_t)nr * nphi;
+            const float2 e2[2] = {*ER[u], *EP[u]};
+            dft_update<2>(p.mon + ij, 2 * plane, plane, p.t.twiddle + (size_t)n * p.nq, p.nq, e2);
+        }
+        if (p.des) {
+            const int dk = kk - p.des_k0;
+            if (dk >= 0 && dk < p.des_nk) {
+                const size_t comp = (size_t)nr * nphi * p.des_nk;
+                const float2 e3[3] = {*ER[u], *EP[u], *EZ[u]};
+                dft_update<3>(p.des + ij * p.des_nk + dk, 3 * comp, comp, p.t.twiddle + (size_t)n * p.nq, p.nq, e3);
+            }
+        }
+    }
+}
+
+bool pair_kernels_apply(const StepParams &p) { return p.nz % 2 == 0 && p.pz % 2 == 0 && !p.bor; }
+
+void launch_update_h_pair(const StepParams &p, cudaStream_t s)
+{
+    dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
+    k_update_h_pair<<<g, b, 0, s>>>(p);
+}
+
+void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s)
+{
+    dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
+    k_update_e_pair<<<g, b, 0, s>>>(p, n);
+}
+
+}  // namespace zda

@@ -95,8 +95,11 @@ class Lens:
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:
-            from . import _lib
-            _lib.lib().zda_lens_destroy(h)
+            try:
+                from . import _lib
+                _lib.lib().zda_lens_destroy(h)
+            except ImportError:          # interpreter shutting down
+                pass
             self.handle = None
 
     def _stream(self):
