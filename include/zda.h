@@ -221,14 +221,17 @@ zda_status zda_zone_time_steps(zda_zone *zone, int steps, double *ms_out_host, v
 zda_status zda_zone_set_wait_limit(zda_zone *zone, int polls, int inject_timeout);
 
 /* Kernel timing with CUDA events recorded on the launching stream: with
- * every > 0, every every-th time step's two main launches are bracketed by
- * events (split step: the H update and the E update; fused step: the
- * streaming E/H kernel and the DFT kernel) (a ring of 64 samples; the host waits for a sample
- * 64 samples old before reusing its slot).  every = 0 turns it off.
- * zda_zone_timing waits for pending samples and returns the summed
- * durations (ms) and the number of sampled launch pairs, then resets. */
+ * every > 0, every every-th time step's main launches are bracketed by
+ * events (a ring of 64 samples; the host waits for a sample 64 samples old
+ * before reusing its slot).  every = 0 turns it off.
+ * zda_zone_timing waits for pending samples and writes ms3_host[0..2], the
+ * summed durations (ms) of the step's launches 1, 2, 3 over the sampled
+ * steps, and the number of sampled steps, then resets.  Launches 1, 2, 3 are:
+ * split step with two z-cells per thread: H update, E update, DFT update;
+ * split step with one z-cell per thread: H update, E update (with the DFTs), -;
+ * fused step: streaming E/H kernel, -, DFT kernel ("-" reads 0). */
 zda_status zda_zone_set_timing(zda_zone *zone, int every);
-zda_status zda_zone_timing(zda_zone *zone, double *h_ms_host, double *e_ms_host, long long *count_host);
+zda_status zda_zone_timing(zda_zone *zone, double *ms3_host, long long *count_host);
 
 /* Density filter + projection without any device allocation (the paper has
  * no counterpart: this exists for callers that cannot call cudaMalloc, e.g.

@@ -80,7 +80,7 @@ SIGNATURES = {
     "zda_zone_set_wait_limit": (_i, [_vp, _i, _i]),
     "zda_zone_time_steps": (_i, [_vp, _i, _dp, _vp]),
     "zda_zone_set_timing": (_i, [_vp, _i]),
-    "zda_zone_timing": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "zda_zone_timing": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "zda_filter_project_noalloc": (_i, [ctypes.POINTER(ZoneDesc), _vp, _vp, _vp]),
     "zda_lens_create": (_i, [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "zda_lens_destroy": (None, [_vp]),

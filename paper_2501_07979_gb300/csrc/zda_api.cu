@@ -77,10 +77,10 @@ struct zda_zone {
     int last_parity = 0;            // fused runs: which buffer holds the final fields
     // optional CUDA-event timing of every `time_every`-th H/E launch pair
     int time_every = 0;
-    std::vector<cudaEvent_t> ev;    // ring of (before H, between, after E) triples
+    std::vector<cudaEvent_t> ev;    // ring of 4 events per sample: launches 1 | 2 | 3 of a step
     std::vector<char> ev_pending;
     int ev_next = 0;
-    double t_h_ms = 0, t_e_ms = 0;
+    double t_h_ms = 0, t_e_ms = 0, t_x_ms = 0;
     long long t_count = 0;
     ~zda_zone();
 };
@@ -88,12 +88,14 @@ struct zda_zone {
 static void timing_drain_slot(zda_zone &z, int slot)
 {
     if (!z.ev_pending[slot]) return;
-    cudaEventSynchronize(z.ev[3 * slot + 2]);
-    float a = 0, b = 0;
-    cudaEventElapsedTime(&a, z.ev[3 * slot], z.ev[3 * slot + 1]);
-    cudaEventElapsedTime(&b, z.ev[3 * slot + 1], z.ev[3 * slot + 2]);
+    cudaEventSynchronize(z.ev[4 * slot + 3]);
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, z.ev[4 * slot], z.ev[4 * slot + 1]);
+    cudaEventElapsedTime(&b, z.ev[4 * slot + 1], z.ev[4 * slot + 2]);
+    cudaEventElapsedTime(&c, z.ev[4 * slot + 2], z.ev[4 * slot + 3]);
     z.t_h_ms += a;
     z.t_e_ms += b;
+    z.t_x_ms += c;
     z.t_count++;
     z.ev_pending[slot] = 0;
 }
@@ -527,6 +529,7 @@ static zda::StepParams step_params(zda_zone &z)
     p.rb_r = rb; p.rb_p = rb + plane; p.rb_z = rb + 2 * plane;
     p.beta_r = P<float2>(z, z.L.beta_r);
     p.beta_p = P<float2>(z, z.L.beta_p);
+    p.src_rad = P<float2>(z, z.L.src_rad);
     p.nq = z.nq;
     p.src_scale = (float)(0.5 / d.dz);
     p.des_k0 = d.design_k0;
@@ -648,15 +651,18 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
                 slot = z.ev_next;
                 z.ev_next = (z.ev_next + 1) % R;
                 timing_drain_slot(z, slot);
-                CUDA_TRY(cudaEventRecord(z.ev[3 * slot], s));
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot], s));
             }
             e = zda::launch_fused_stream(fp, n, s);
             if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("fused step: ") + cudaGetErrorString(e));
-            if (timed) CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 1], s));
+            if (timed) {
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 1], s));
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 2], s));
+            }
             e = zda::launch_fused_post(fp, n, s);
             if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("DFT step: ") + cudaGetErrorString(e));
             if (timed) {
-                CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 2], s));
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 3], s));
                 z.ev_pending[slot] = 1;
             }
         }
@@ -666,25 +672,30 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
     }
     z.last_parity = 0;
     const bool pair = z.pair_kernels && zda::pair_kernels_apply(p);
+    const bool dft = pair && (p.des || p.mon);
     for (int n = 0; n < z.d.n_steps; ++n) {
         const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
         int slot = 0;
+        if (pair && p.src_mode == zda::SRC_ADJOINT) zda::launch_adjoint_source_rad(p, n, s);
         if (timed) {
             slot = z.ev_next;
             z.ev_next = (z.ev_next + 1) % R;
             timing_drain_slot(z, slot);
-            CUDA_TRY(cudaEventRecord(z.ev[3 * slot], s));
+            CUDA_TRY(cudaEventRecord(z.ev[4 * slot], s));
         }
         if (pair) zda::launch_update_h_pair(p, s);
         else zda::launch_update_h(p, s);
-        if (timed) CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 1], s));
+        if (timed) CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 1], s));
         if (pair) zda::launch_update_e_pair(p, n, s);
         else zda::launch_update_e(p, n, s);
+        if (timed) CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 2], s));
+        if (dft) zda::launch_dft_sites(p, n, s);
         if (timed) {
-            CUDA_TRY(cudaEventRecord(z.ev[3 * slot + 2], s));
+            CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 3], s));
             z.ev_pending[slot] = 1;
         }
     }
+    if (pair) z.launches += (long long)z.d.n_steps * ((dft ? 1 : 0) + (p.src_mode == zda::SRC_ADJOINT ? 1 : 0));
     z.launches += 2LL * z.d.n_steps;
     CUDA_TRY(cudaGetLastError());
     return ZDA_OK;
@@ -1092,11 +1103,11 @@ zda_status zda_zone_set_timing(zda_zone *z, int every)
     if (!z || every < 0) return fail(ZDA_ERR_ARG, "bad argument");
     CUDA_TRY(cudaSetDevice(z->ctx->device));
     timing_release(*z);
-    z->t_h_ms = z->t_e_ms = 0;
+    z->t_h_ms = z->t_e_ms = z->t_x_ms = 0;
     z->t_count = 0;
     if (every == 0) return ZDA_OK;
     const int R = 64;
-    z->ev.resize(3 * R);
+    z->ev.resize(4 * R);
     for (auto &e : z->ev) CUDA_TRY(cudaEventCreate(&e));
     z->ev_pending.assign(R, 0);
     z->ev_next = 0;
@@ -1104,18 +1115,20 @@ zda_status zda_zone_set_timing(zda_zone *z, int every)
     return ZDA_OK;
 }
 
-zda_status zda_zone_timing(zda_zone *z, double *h_ms, double *e_ms, long long *count)
+zda_status zda_zone_timing(zda_zone *z, double *ms3, long long *count)
 {
-    if (!z || !h_ms || !e_ms || !count) return fail(ZDA_ERR_ARG, "null argument");
+    if (!z || !ms3 || !count) return fail(ZDA_ERR_ARG, "null argument");
     CUDA_TRY(cudaSetDevice(z->ctx->device));
     for (size_t s = 0; s < z->ev_pending.size(); ++s) timing_drain_slot(*z, (int)s);
-    *h_ms = z->t_h_ms;
-    *e_ms = z->t_e_ms;
+    ms3[0] = z->t_h_ms;
+    ms3[1] = z->t_e_ms;
+    ms3[2] = z->t_x_ms;
     *count = z->t_count;
-    z->t_h_ms = z->t_e_ms = 0;
+    z->t_h_ms = z->t_e_ms = z->t_x_ms = 0;
     z->t_count = 0;
     return ZDA_OK;
 }
+
 
 }  // extern "C"
 

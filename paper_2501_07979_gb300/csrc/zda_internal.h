@@ -83,6 +83,7 @@ struct StepParams {
     int src_mode, src_k;
     float src_scale;                           // 1/(2 dz) for the plane wave
     const float2 *beta_r, *beta_p;             // adjoint radial profiles [Q][n_r]
+    float2 *src_rad;                           // adjoint source of the current step [2][n_r]
     int nq;
     int mon_k;                                 // < 0: no monitor DFT
     float2 *mon;
@@ -96,7 +97,9 @@ void launch_update_e(const StepParams &p, int n, cudaStream_t s);
 // two z-cells per thread (zda_pair.cu): even n_z, even pml_z, wedge zones
 bool pair_kernels_apply(const StepParams &p);
 void launch_update_h_pair(const StepParams &p, cudaStream_t s);
-void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s);
+void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s);   // no DFT: see launch_dft_sites
+void launch_dft_sites(const StepParams &p, int n, cudaStream_t s);
+void launch_adjoint_source_rad(const StepParams &p, int n, cudaStream_t s);
 
 struct FilterParams {
     int nrd, nphi, di_max, dj_max;

@@ -185,16 +185,9 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
                 const float2 pn = p.t.ph_n[j], ph = p.t.ph_h[j];
                 jr = c_scale(pn, a);
                 jp = make_float2(-ph.y * a, ph.x * a);
-            } else if (p.src_mode == SRC_ADJOINT) {
-                float2 sr = zero, sp = zero;
-                const float2 *kt = p.t.adj_time + (size_t)n * p.nq;
-                for (int q = 0; q < p.nq; ++q) {
-                    const float2 kq = kt[q];
-                    sr = c_fma(p.beta_r[(size_t)q * nr + i], kq, sr);
-                    sp = c_fma(p.beta_p[(size_t)q * nr + i], kq, sp);
-                }
-                jr = c_mul(p.t.ph_n[j], sr);
-                jp = c_mul(p.t.ph_h[j], sp);
+            } else if (p.src_mode == SRC_ADJOINT) {       // radial profile of this step (k_adjoint_source_rad)
+                jr = c_mul(p.t.ph_n[j], p.src_rad[i]);
+                jp = c_mul(p.t.ph_h[j], p.src_rad[nr + i]);
             }
         }
         const float bzn = kz >= 0 ? __ldg(p.t.bz_n + kk) : 0.f, czn = kz >= 0 ? __ldg(p.t.cz_n + kk) : 0.f;
@@ -240,24 +233,64 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
     if (kz >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
     if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
 
-    // running DFTs of E^{n+1}
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int kk = k + u;
-        if (p.mon && kk == p.mon_k) {
-            const size_t plane = (size_t)nr * nphi;
-            const float2 e2[2] = {*ER[u], *EP[u]};
-            dft_update<2>(p.mon + ij, 2 * plane, plane, p.t.twiddle + (size_t)n * p.nq, p.nq, e2);
-        }
-        if (p.des) {
-            const int dk = kk - p.des_k0;
-            if (dk >= 0 && dk < p.des_nk) {
-                const size_t comp = (size_t)nr * nphi * p.des_nk;
-                const float2 e3[3] = {*ER[u], *EP[u], *EZ[u]};
-                dft_update<3>(p.des + ij * p.des_nk + dk, 3 * comp, comp, p.t.twiddle + (size_t)n * p.nq, p.nq, e3);
-            }
-        }
+}
+
+// Running DFTs of E^{n+1} after the E update: one thread per site (design
+// volume: 3 components; monitor plane: E_r, E_phi), accumulators updated in
+// chunks (dft_update).  A separate launch keeps the E update lean: with the
+// DFT inside, the blocks holding design planes ran long and the extra
+// registers halved the E update's occupancy.
+__global__ void k_dft_sites(const StepParams p, const int n)
+{
+    const int nz = p.nz, nphi = p.nphi, nr = p.nr;
+    const size_t plane = (size_t)nr * nphi;
+    const size_t sj = (size_t)nz, si = (size_t)nphi * nz;
+    const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t ndes = p.des ? plane * p.des_nk : 0;
+    if (t < ndes) {
+        const int kk = (int)(t % p.des_nk);
+        const size_t ij = t / p.des_nk;
+        const size_t c = (ij / nphi) * si + (ij % nphi) * sj + p.des_k0 + kk;
+        const float2 e3[3] = {__ldg(p.f.Er + c), __ldg(p.f.Ep + c), __ldg(p.f.Ez + c)};
+        const size_t comp = plane * p.des_nk;
+        dft_update<3>(p.des + t, 3 * comp, comp, tw, p.nq, e3);
+        return;
     }
+    const size_t u = t - ndes;
+    if (p.mon && u < plane) {
+        const size_t c = (u / nphi) * si + (u % nphi) * sj + p.mon_k;
+        const float2 e2[2] = {__ldg(p.f.Er + c), __ldg(p.f.Ep + c)};
+        dft_update<2>(p.mon + u, 2 * plane, plane, tw, p.nq, e2);
+    }
+}
+
+// Adjoint source of step n per radius: sum_q beta_q(r) k_q(t_{n+1/2}) for the
+// E_r and E_phi sites (the e^{i phi} factor is applied per row).
+__global__ void k_adjoint_source_rad(const StepParams p, const int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.nr) return;
+    const float2 *kt = p.t.adj_time + (size_t)n * p.nq;
+    float2 sr = make_float2(0.f, 0.f), sp = make_float2(0.f, 0.f);
+    for (int q = 0; q < p.nq; ++q) {
+        sr = c_fma(p.beta_r[(size_t)q * p.nr + i], kt[q], sr);
+        sp = c_fma(p.beta_p[(size_t)q * p.nr + i], kt[q], sp);
+    }
+    p.src_rad[i] = sr;
+    p.src_rad[p.nr + i] = sp;
+}
+
+void launch_dft_sites(const StepParams &p, int n, cudaStream_t s)
+{
+    if (!p.des && !p.mon) return;
+    const size_t nsite = (p.des ? (size_t)p.nr * p.nphi * p.des_nk : 0) + (p.mon ? (size_t)p.nr * p.nphi : 0);
+    k_dft_sites<<<(unsigned)((nsite + 255) / 256), 256, 0, s>>>(p, n);
+}
+
+void launch_adjoint_source_rad(const StepParams &p, int n, cudaStream_t s)
+{
+    k_adjoint_source_rad<<<(p.nr + 127) / 128, 128, 0, s>>>(p, n);
 }
 
 bool pair_kernels_apply(const StepParams &p) { return p.nz % 2 == 0 && p.pz % 2 == 0 && !p.bor; }

@@ -204,14 +204,18 @@ class Zone:
         return v.value, t.value, r.value
 
     def set_timing(self, every):
-        """Sample every `every`-th step's H/E launches with CUDA events (0: off)."""
+        """Sample every `every`-th time step's launches with CUDA events (0: off)."""
         check(_lib.lib().zda_zone_set_timing(self.handle, int(every)))
 
     def timing(self):
-        """(H-update ms, E-update ms, sampled launch pairs) since the last call."""
-        h, e, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
-        check(_lib.lib().zda_zone_timing(self.handle, ctypes.byref(h), ctypes.byref(e), ctypes.byref(n)))
-        return h.value, e.value, n.value
+        """([ms of launch 1, 2, 3 summed over the samples], sampled steps) since
+        the last call; split step: H update, E update, DFT update (one z-cell
+        per thread: the DFT is inside the E update); fused step: streaming
+        kernel, 0, DFT kernel."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_longlong()
+        check(_lib.lib().zda_zone_timing(self.handle, ms, ctypes.byref(n)))
+        return list(ms), n.value
 
     @property
     def launches(self):

@@ -166,6 +166,20 @@ def test_forward_is_deterministic():
     assert np.array_equal(a, b) and torch.equal(fa, z.fields().cpu())
 
 
+@pytest.mark.parametrize("kernel", ["split", "split1", "fused2"])
+def test_event_timing_samples_each_launch_of_a_step(kernel):
+    spec = RAGGED["ragged_even"]
+    z = _zone(spec, kernel)
+    z.set_timing(10)
+    z.forward(_dev(rho_for(spec, 3)))
+    ms, n = z.timing()
+    z.set_timing(0)
+    assert n == (spec.n_steps + 9) // 10
+    used = {"split": [0, 1, 2], "split1": [0, 1], "fused2": [0, 2]}[kernel]   # launches of a step
+    assert all(ms[u] > 0 for u in used)
+    assert z.timing() == ([0.0, 0.0, 0.0], 0)             # reset by the read
+
+
 # ------------------------------------------------------------------ adjoint
 GRAD_SPECS = {
     "tiny2": zone_tiny(n_steps=700, filter_radius=0.25, beta=4.0, wavelengths=(0.9, 1.1),
