@@ -33,6 +33,16 @@ __device__ __forceinline__ void st4(float2 *p, C2 c)
     *reinterpret_cast<float4 *>(p) = make_float4(c.a.x, c.a.y, c.b.x, c.b.y);
 }
 __device__ __forceinline__ C2 cmul2(float2 s, C2 c) { return C2{c_mul(s, c.a), c_mul(s, c.b)}; }
+// Inverse permittivity of a site: the hardware reciprocal (rcp.approx, about
+// 1 ulp) instead of an IEEE division; the E update was issue-bound with the
+// division sequence (4 % faster without it), and 1 ulp is far below the
+// single-precision time stepping's own rounding.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 __global__ void __launch_bounds__(PX * PY, 4) k_update_h_pair(const StepParams p)
 {
@@ -198,7 +208,7 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
                 *PR[u] = c_add(c_scale(*PR[u], bzn), c_scale(dz, czn));
                 dz = c_add(dz, *PR[u]);
             }
-            const float ie = 1.0f / (__ldg(p.t.a_n + kk) + __ldg(p.t.d_n + kk) * rbr);
+            const float ie = rcp_approx(__ldg(p.t.a_n + kk) + __ldg(p.t.d_n + kk) * rbr);
             *ER[u] = c_add(*ER[u], c_scale(c_sub(c_sub(dph, dz), jr), dt * ie));
         }
         if (i > 0 && kk > 0) {                              // E_phi
@@ -212,7 +222,7 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
                 *PPR[u] = c_add(c_scale(*PPR[u], brn), c_scale(drr, crn));
                 drr = c_add(drr, *PPR[u]);
             }
-            const float ie = 1.0f / (__ldg(p.t.a_n + kk) + __ldg(p.t.d_n + kk) * rbp);
+            const float ie = rcp_approx(__ldg(p.t.a_n + kk) + __ldg(p.t.d_n + kk) * rbp);
             *EP[u] = c_add(*EP[u], c_scale(c_sub(c_sub(dz, drr), jp), dt * ie));
         }
         if (i > 0) {                                        // E_z
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
                 *PZR[u] = c_add(c_scale(*PZR[u], brn), c_scale(drr, crn));
                 drr = c_add(drr, *PZR[u]);
             }
-            const float ie = 1.0f / (__ldg(p.t.a_c + kk) + __ldg(p.t.d_c + kk) * rbz);
+            const float ie = rcp_approx(__ldg(p.t.a_c + kk) + __ldg(p.t.d_c + kk) * rbz);
             *EZ[u] = c_add(*EZ[u], c_scale(c_sub(drr, dph), dt * ie));
         }
     }
