@@ -93,7 +93,29 @@ SIGNATURES = {
     "zda_lens_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_lens_focal_plane": (_i, [_vp, _vp, _i, _i, _vp, _dp, _vp]),
     "zda_last_error": (ctypes.c_char_p, []),
+    # surrogate network (include/zda_nn.h)
+    "zda_nn_create": (_i, [_i, _vp, _vp]),
+    "zda_nn_destroy": (None, [_vp]),
+    "zda_nn_param_count": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "zda_nn_forward_flops": (_i, [_vp, _dp]),
+    "zda_nn_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "zda_nn_bind_workspace": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "zda_nn_set_params": (_i, [_vp, _vp, _i, _vp]),
+    "zda_nn_get_params": (_i, [_vp, _vp, _i, _vp]),
+    "zda_nn_get_grads": (_i, [_vp, _vp, _i, _vp]),
+    "zda_nn_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "zda_nn_backward": (_i, [_vp, _vp, _vp, _vp]),
+    "zda_nn_mse": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _vp]),
+    "zda_nn_adam": (_i, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
+    "zda_nn_launch_count": (ctypes.c_longlong, [_vp]),
+    "zda_nn_check": (_i, [_vp, _vp]),
 }
+
+
+class NnDesc(ctypes.Structure):
+    """zda_nn_desc of include/zda_nn.h."""
+    _fields_ = [("batch", ctypes.c_int), ("height", ctypes.c_int), ("width", ctypes.c_int),
+                ("in_ch", ctypes.c_int), ("out_ch", ctypes.c_int)]
 
 
 def load(path=None):

@@ -10,10 +10,16 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+HEADERS = ["zda.h", "zda_nn.h"]
+
+
 def _declared():
-    src = open(os.path.join(ROOT, "include", "zda.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(zda_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(zda_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -21,7 +27,7 @@ def libpath():
     import __graft_entry__
     build = __graft_entry__._build_module()
     p = build.lib_path()
-    srcs = [os.path.join(build.CSRC, s) for s in build.SOURCES] + [os.path.join(ROOT, "include", "zda.h")]
+    srcs = [os.path.join(build.CSRC, s) for s in build.SOURCES] + [os.path.join(ROOT, "include", h) for h in HEADERS]
     if not os.path.exists(p) or os.path.getmtime(p) < max(os.path.getmtime(s) for s in srcs):
         build.build()
     return p
@@ -76,3 +82,30 @@ def test_invalid_arguments_return_status_not_crash(libpath):
     assert L.zda_last_error()
     assert L.zda_zone_query(None, None) == _lib.ERR_ARG
     assert L.zda_zone_launch_count(None) == -1
+
+
+def test_surrogate_descriptor_checks_and_sizes_need_no_gpu(libpath):
+    """zda_nn_create validates its descriptor on the host and reports the
+    parameter count and forward FLOPs of the architecture the oracle defines."""
+    from oracle import surrogate as S
+    from paper_2501_07979_gb300 import _lib
+    L = _lib.load(libpath)
+    h = ctypes.c_void_p()
+    bad = _lib.NnDesc(batch=2, height=12, width=16, in_ch=1, out_ch=24)      # H not a multiple of 8
+    assert L.zda_nn_create(0, ctypes.byref(bad), ctypes.byref(h)) == _lib.ERR_ARG
+    bad = _lib.NnDesc(batch=2, height=16, width=16, in_ch=17, out_ch=24)
+    assert L.zda_nn_create(0, ctypes.byref(bad), ctypes.byref(h)) == _lib.ERR_ARG
+    d = _lib.NnDesc(batch=4, height=32, width=24, in_ch=2, out_ch=24)
+    assert L.zda_nn_create(0, ctypes.byref(d), ctypes.byref(h)) == _lib.OK
+    n = ctypes.c_size_t()
+    f = ctypes.c_double()
+    ws = ctypes.c_size_t()
+    assert L.zda_nn_param_count(h, ctypes.byref(n)) == _lib.OK
+    assert L.zda_nn_forward_flops(h, ctypes.byref(f)) == _lib.OK
+    assert L.zda_nn_workspace_bytes(h, ctypes.byref(ws)) == _lib.OK
+    assert n.value == S.param_count(2, 24)
+    assert f.value == S.forward_flops(32, 24, 2, 24)
+    assert ws.value > 4 * 4 * n.value
+    # unbound: calls that need the workspace report a state error
+    assert L.zda_nn_adam(h, 1e-3, 0.9, 0.999, 1e-8, None) == _lib.ERR_STATE
+    L.zda_nn_destroy(h)
