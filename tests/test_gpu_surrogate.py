@@ -2,17 +2,31 @@
 the FP64 oracle in oracle/surrogate.py, which rounds to bfloat16 at the same
 points as the kernels.
 
-Tolerances.  Both sides round every stored activation to bfloat16 (relative
-step 2^-8); they differ only in the accumulation (FP32 in tensor memory vs
-FP64), about 1e-7 relative before rounding.  A rounding decision therefore
-flips on roughly 1e-4 of the elements of a layer, by one bfloat16 step, and
-the flips feed the next layers.  On 16 x 16 images the cascade stays
-negligible (an FP32-accumulating copy of the oracle differs from the FP64
-one by ~4e-8 in the output), so the small case is held to 1e-3; on larger
-images the cascade reaches ~4e-3 in the output and ~2e-2 in the weight
-gradients (the same copy at 64 x 64), so larger cases are held to 2e-2 /
-5e-2 / 1e-1 (output / weight gradients / input gradient).  A wrong tap, a
-transposed operand, a lost bias or mask moves these by O(1).
+Two kinds of cases.
+
+* Exact structure: every convolution has a single unit weight per output
+  channel (one tap, a channel permutation), so every layer copies bf16
+  values and pooling/upsampling/masks/skips only add a few of them: both
+  sides must agree bit for bit on the output, and to FP32 summation order on
+  the input gradient (1e-6; the input layer sums ~20 channels into each of
+  its 3 inputs) and on the weight gradients (1e-5).  This pins every tap
+  offset, the channel order of the weight images, the concatenation halves,
+  pooling, upsampling and the masks, forward and backward.
+* Random weights: the two sides then differ only in the accumulation (FP32
+  in tensor memory vs FP64, ~1e-7 relative before rounding), but bf16
+  storage turns that into one-step rounding flips on ~1e-4 of a layer's
+  elements, and the flips feed the next layers: measured on a 16 x 16 case,
+  the fraction of differing elements grows from 1e-4 after the second
+  convolution to ~12 % at the last decoder layer, every difference one bf16
+  step, and the output differs by ~2e-3 relative.  A copy of the oracle
+  that accumulates in FP32 in K = 16 steps (as the MMA does) shows the same
+  cascade against the FP64 oracle: up to 2e-3 on the output, 1.7e-2 to
+  2.4e-2 on the input gradient and up to 3.6e-2 on a layer's weight
+  gradient (the deepest layers, whose few positions make each flip count).
+  Tolerances, about three times those: 2e-2 on the output, 1e-1 on the
+  input gradient, 1.5e-1 on each layer's weight gradient and 6e-2 on the
+  whole gradient vector; a wrong tap, operand, bias or mask moves these by
+  O(1), and the exact-structure cases above pin the wiring bit for bit.
 """
 import numpy as np
 import pytest
@@ -40,16 +54,58 @@ def _rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
+def _perm_params(ic, oc, take_skip):
+    """One unit weight per output channel: layer i uses tap i mod 9 (3x3) and
+    the channel map c_in = (5 c_out + 3 i) mod 64 (mod ic for the input
+    layer); the decoder's first convolution of level l reads the skip half
+    when take_skip[l], else the upsampled half."""
+    ps = []
+    for i, (name, k, ci, co) in enumerate(S.layer_table(ic, oc)):
+        w = np.zeros((co, k, k, ci))
+        ty, tx = divmod(i % 9, 3) if k == 3 else (0, 0)
+        for o in range(co):
+            if i == 0:
+                c = (5 * o + 3 * i) % ic
+            else:
+                c = (5 * o + 3 * i) % 64
+                if name.startswith("dec") and name.endswith("a") and take_skip[int(name[3])]:
+                    c += 64
+            w[o, ty, tx, c] = 1.0
+        ps.append((w, np.zeros(co)))
+    return ps
+
+
+@pytest.mark.parametrize("take_skip", [(True, False, True), (False, True, False)])
+def test_structure_is_exact_forward_and_backward(take_skip):
+    H, W, ic, oc, B = 24, 40, 3, 24, 2
+    ps = _perm_params(ic, oc, take_skip)
+    r = np.random.default_rng(7)
+    x = S.bf16(r.uniform(0.05, 1, (B, H, W, ic)))
+    dy = S.bf16(r.standard_normal((B, H, W, oc)))
+    net = _net(H, W, ic, oc, B)
+    net.set_params(S.flatten(ps).astype(np.float32))
+    y = net.forward(torch.tensor(x, dtype=torch.float32, device="cuda:0")).cpu().numpy()
+    dx = net.backward(torch.tensor(dy, dtype=torch.float32, device="cuda:0"), want_dx=True).cpu().numpy()
+    g = net.grads().cpu().numpy()
+    net.check()
+    y0, cache = S.forward(ps, x, rounding=True)
+    grads, dx0 = S.backward(ps, cache, dy, want_dx=True)
+    assert np.count_nonzero(y0) > 0.5 * y0.size
+    assert np.array_equal(y, y0)
+    assert _rel(dx, dx0) < 1e-6
+    assert _rel(g, S.flatten(grads)) < 1e-5
+
+
 CASES = {
-    # name: (H, W, in_ch, out_ch, batch, forward tol, weight-grad tol, input-grad tol)
-    "small": (16, 16, 2, 8, 2, 1e-3, 1e-2, 1e-2),
-    "ragged": (24, 40, 1, 24, 3, 2e-2, 5e-2, 1e-1),
+    # name: (H, W, in_ch, out_ch, batch)
+    "small": (16, 16, 2, 8, 2),
+    "ragged": (24, 40, 1, 24, 3),
 }
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_forward_and_backward_match_oracle(name):
-    H, W, ic, oc, B, tf, tg, tx = CASES[name]
+    H, W, ic, oc, B = CASES[name]
     ps = _params(ic, oc, seed=11)
     r = np.random.default_rng(12)
     x = r.uniform(0, 1, (B, H, W, ic))
@@ -63,20 +119,21 @@ def test_forward_and_backward_match_oracle(name):
     net.check()
 
     y0, cache = S.forward(ps, x, rounding=True)
-    assert _rel(y.cpu().numpy(), y0) < tf
     l0, dy0 = S.mse(y.cpu().numpy().astype(np.float64), t)         # the loss of the GPU's own output
-    assert abs(float(loss.item()) - l0) <= 1e-6 * l0
-    assert _rel(dy.cpu().numpy(), dy0) < 1e-6
     grads, dx0 = S.backward(ps, cache, dy.cpu().numpy().astype(np.float64), want_dx=True)
+    errs = {"y": _rel(y.cpu().numpy(), y0), "dx": _rel(dx.cpu().numpy(), dx0)}
     off = 0
     for (lname, *_), (gw, gb) in zip(S.layer_table(ic, oc), grads):
         n = gw.size + gb.size
-        gl = g[off:off + n]
+        errs[lname] = max(_rel(g[off:off + gw.size], gw.ravel()), _rel(g[off + gw.size:off + n], gb))
         off += n
-        assert _rel(gl[:gw.size], gw.ravel()) < tg, lname
-        assert _rel(gl[gw.size:], gb) < tg, lname
     assert off == g.size
-    assert _rel(dx.cpu().numpy(), dx0) < tx
+    assert abs(float(loss.item()) - l0) <= 1e-6 * l0
+    assert _rel(dy.cpu().numpy(), dy0) < 1e-6
+    assert errs["y"] < 2e-2, errs
+    assert errs["dx"] < 1e-1, errs
+    assert max(v for k, v in errs.items() if k not in ("y", "dx")) < 1.5e-1, errs
+    assert _rel(g, S.flatten(grads)) < 6e-2
 
 
 def test_adam_step_matches_oracle():
