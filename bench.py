@@ -21,6 +21,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -37,6 +39,9 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    ap.add_argument("--workload", default="zone", choices=["zone", "surrogate"],
+                    help="zone: forward + adjoint FDTD iteration of the wide zone (headline); "
+                         "surrogate: U-Net inference, 128 x 128 patches, batch 256")
     ap.add_argument("--kernel", default="default", choices=["default", "split", "split1", "fused2", "fused4"],
                     help="time-step kernel (default: the library's choice for the zone)")
     return ap.parse_args()
@@ -326,9 +331,166 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ surrogate workload
+NN_METRIC = "surrogate inference TFLOP/s (U-Net, 128x128 patches, batch 256)"
+NN_UNIT = "TFLOP/s"
+NN_SHAPE = dict(H=128, W=128, in_ch=1, out_ch=24, batch=256)
+
+
+def nn_config():
+    return {"workload": "zone surrogate: 4-level U-Net, width 64, 3x3 convolutions, rho patch 128x128 -> "
+                        "monitor DFT 24 channels (2 components x 6 signed frequencies x re/im), batch 256",
+            "flops": "useful forward FLOPs, 2 per multiply-add, true channel counts",
+            "l2": "no flush: one batch's activations (several GB of bf16) exceed the 129 MB L2"}
+
+
+def nn_oracle_sample(n=24):
+    """The FP64 oracle's forward pass on n 128x128 samples (bounded CPU sample)."""
+    from oracle import surrogate as S
+    sh = NN_SHAPE
+    ps = S.init_params(sh["in_ch"], sh["out_ch"], seed=1)
+    x = np.random.default_rng(2).uniform(0, 1, (n, sh["H"], sh["W"], sh["in_ch"]))
+    t = time.perf_counter()
+    S.forward(ps, x, rounding=True)
+    dt = time.perf_counter() - t
+    fl = n * S.forward_flops(sh["H"], sh["W"], sh["in_ch"], sh["out_ch"])
+    return {"value": fl / dt / 1e12, "unit": NN_UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "FP64 NumPy oracle forward pass of %d 128x128 samples with bf16 rounding (%.1f s)" % (n, dt)}
+
+
+def run_nn_reference(a):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    t0 = time.perf_counter()
+    vals = [nn_oracle_sample() for _ in range(a.steps)]
+    elapsed = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    line = {"metric": NN_METRIC, "value": v, "unit": NN_UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": nn_config(), "cpu_baseline": dict(vals[0], value=v),
+            "e2e": {"value": v, "unit": NN_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_nn(a):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2501_07979_gb300.surrogate import Surrogate
+    sh = NN_SHAPE
+    net = Surrogate(sh["H"], sh["W"], sh["in_ch"], sh["out_ch"], sh["batch"], device=local)
+    net.init_params(1 + rank)
+    g = torch.Generator(device="cpu").manual_seed(3 + rank)
+    x_host = torch.rand((sh["batch"], sh["H"], sh["W"], sh["in_ch"]), generator=g).pin_memory()
+    x = x_host.to(f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(a.warmup, 1)):
+        net.forward(x)
+    barrier()
+    launches0 = net.launches
+    net.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        net.forward(x)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    conv_ms, conv_fl, conv_n = net.timing()
+    net.set_timing(False)
+    launches = net.launches - launches0
+    ms = e0.elapsed_time(e1) / a.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=x.device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    flops = net.flops_per_sample * sh["batch"]
+    value = flops * world / (ms_max * 1e-3) / 1e12
+    # end to end: pinned host input -> device, forward, output -> pinned host
+    y_host = torch.empty((sh["batch"], sh["H"], sh["W"], sh["out_ch"]), dtype=torch.float32).pin_memory()
+    barrier()
+    te = time.perf_counter()
+    n_e2e = max(1, min(a.steps, 3))
+    for _ in range(n_e2e):
+        xd = x_host.to(x.device, non_blocking=True)
+        y = net.forward(xd)
+        y_host.copy_(y, non_blocking=True)
+    barrier()
+    e2e_s = (time.perf_counter() - te) / n_e2e
+    te_t = torch.tensor([e2e_s], dtype=torch.float64, device=x.device)
+    if dist is not None:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    # a training step (forward + MSE + backward + Adam) for context
+    tgt = torch.zeros((sh["batch"], sh["H"], sh["W"], sh["out_ch"]), device=x.device)
+    net.train_step(x, tgt)
+    barrier()
+    e0.record(stream)
+    for _ in range(2):
+        net.train_step(x, tgt)
+    e1.record(stream)
+    barrier()
+    train_ms = e0.elapsed_time(e1) / 2
+    net.check()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    ach = conv_fl / (conv_ms * 1e-3) / 1e12 if conv_ms > 0 else None
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get("k_conv_tc")
+        except ValueError:
+            traffic = None
+    line = {"metric": NN_METRIC, "value": value, "unit": NN_UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": nn_config(),
+            "roofline": {"bound": "tensor", "kernel": "k_conv_tc", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": (ach / peak) if ach else None, "traffic": traffic,
+                         "peak_source": "measured (bf16 burst)" if "bf16_tflops" in peaks else "fallback",
+                         "sampled_launches": conv_n, "conv_ms_per_step": conv_ms / a.steps},
+            "e2e": {"value": flops * world / float(te_t.item()) / 1e12, "unit": NN_UNIT,
+                    "h2d_bytes_per_step": x_host.numel() * 4, "d2h_bytes_per_step": y_host.numel() * 4},
+            "gpu_launches": launches, "clocks": clk,
+            "train_step": {"ms": train_ms, "tflops_3x_forward": 3 * flops / (train_ms * 1e-3) / 1e12}}
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = nn_oracle_sample()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse()
-    if a.impl == "reference":
+    if a.workload == "surrogate":
+        if a.impl == "reference":
+            run_nn_reference(a)
+        else:
+            run_nn(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -181,6 +181,19 @@ zda_status zda_filter_project_backward(zda_zone *zone, const float *rho_dev, con
 zda_status zda_focal_transform(zda_zone *zone, const float *monitor_dft_dev, double *focal_out_host,
                                void *stream);
 
+/* The focal transform evaluated on the zone surrogate's output (zda_nn.h):
+ * y_dev [n][n_r_design][n_phi][4 Q] (device FP32) holds the monitor DFT of
+ * the design rows, channel (q 2 + comp) 2 + part (comp 0 = E_r, 1 = E_phi;
+ * part 0 = real, 1 = imaginary) divided by `scale`.  Writes the focal
+ * phasors S_dev [n][Q] (device, interleaved complex FP64) of "Results and
+ * Discussion" restricted to those rows (the outer-edge E_phi node, weight
+ * dr / 2, is not among them).  The _transpose call is its transpose: from
+ * dS_dev [n][Q] (dobj/dRe S + i dobj/dIm S, device) it writes
+ * dobj/dy [n][n_r_design][n_phi][4 Q] to dy_dev.  Needs a zone (no run). */
+zda_status zda_focal_transform_nn(zda_zone *zone, const float *y_dev, int n, float scale, double *S_dev, void *stream);
+zda_status zda_focal_transform_nn_transpose(zda_zone *zone, const double *dS_dev, int n, float scale, float *dy_dev,
+                                    void *stream);
+
 /* Copies of internal state after zda_forward / zda_adjoint (complex floats):
  *   zda_copy_fields:  [6][n_r][n_phi][n_z]  E_r, E_phi, E_z, H_r, H_phi, H_z
  *   zda_copy_monitor_dft: [n_freq][2][n_r][n_phi]

@@ -95,6 +95,14 @@ zda_status zda_nn_mse(zda_nn *net, const float *y_dev, const float *target_dev, 
  * current gradient; the step counter starts at 1 after zda_nn_set_params. */
 zda_status zda_nn_adam(zda_nn *net, float lr, float beta1, float beta2, float eps, void *stream);
 
+/* CUDA-event timing of the forward convolution launches (k_conv_tc), on
+ * the launching stream: with on != 0 every forward convolution is bracketed
+ * by two events.  zda_nn_timing waits for them and returns the summed
+ * durations (ms), the useful FLOPs of those launches (true channel counts,
+ * H x W outputs per sample) and the number of launches, then resets. */
+zda_status zda_nn_set_timing(zda_nn *net, int on);
+zda_status zda_nn_timing(zda_nn *net, double *conv_ms_host, double *conv_flops_host, int *launches_host);
+
 /* Kernel launches issued by this network so far. */
 long long zda_nn_launch_count(const zda_nn *net);
 

@@ -93,6 +93,8 @@ SIGNATURES = {
     "zda_lens_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_lens_focal_plane": (_i, [_vp, _vp, _i, _i, _vp, _dp, _vp]),
     "zda_last_error": (ctypes.c_char_p, []),
+    "zda_focal_transform_nn": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp]),
+    "zda_focal_transform_nn_transpose": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp]),
     # surrogate network (include/zda_nn.h)
     "zda_nn_create": (_i, [_i, _vp, _vp]),
     "zda_nn_destroy": (None, [_vp]),
@@ -108,6 +110,8 @@ SIGNATURES = {
     "zda_nn_mse": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _vp]),
     "zda_nn_adam": (_i, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
     "zda_nn_launch_count": (ctypes.c_longlong, [_vp]),
+    "zda_nn_set_timing": (_i, [_vp, _i]),
+    "zda_nn_timing": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int)]),
     "zda_nn_check": (_i, [_vp, _vp]),
 }
 

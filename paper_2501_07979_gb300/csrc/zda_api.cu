@@ -987,6 +987,34 @@ zda_status zda_focal_transform(zda_zone *z, const float *mon, double *out, void 
     return focal(*z, (const float2 *)mon, out, (cudaStream_t)stream);
 }
 
+zda_status zda_focal_transform_nn(zda_zone *z, const float *y, int n, float scale, double *S, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!y || !S) return fail(ZDA_ERR_ARG, "null pointer");
+    if (n < 1 || !(scale > 0.f)) return fail(ZDA_ERR_ARG, "n >= 1 and scale > 0 required");
+    zda::launch_focal_nn(y, n, z->nq, z->i_d0, z->nrd, z->d.n_phi, z->d.n_r, scale, P<double2>(*z, z->L.Gr),
+                         P<double2>(*z, z->L.Gp), P<double2>(*z, z->L.emph_n), P<double2>(*z, z->L.emph_h),
+                         reinterpret_cast<double2 *>(S), (cudaStream_t)stream);
+    z->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
+zda_status zda_focal_transform_nn_transpose(zda_zone *z, const double *dS, int n, float scale, float *dy, void *stream)
+{
+    zda_status st = ready(z);
+    if (st) return st;
+    if (!dS || !dy) return fail(ZDA_ERR_ARG, "null pointer");
+    if (n < 1 || !(scale > 0.f)) return fail(ZDA_ERR_ARG, "n >= 1 and scale > 0 required");
+    zda::launch_focal_nn_T(reinterpret_cast<const double2 *>(dS), n, z->nq, z->i_d0, z->nrd, z->d.n_phi, z->d.n_r,
+                           scale, P<double2>(*z, z->L.Gr), P<double2>(*z, z->L.Gp), P<double2>(*z, z->L.emph_n),
+                           P<double2>(*z, z->L.emph_h), dy, (cudaStream_t)stream);
+    z->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return ZDA_OK;
+}
+
 zda_status zda_copy_fields(zda_zone *z, float *out, void *stream)
 {
     zda_status st = ready(z);

@@ -117,6 +117,12 @@ void launch_rho_bar(const float *rho_t, int nr, int nphi, int i_d0, int i_d1, fl
 
 void launch_focal_partial(const float2 *mon, const double2 *Gr, const double2 *Gp, const double2 *emph_n,
                           const double2 *emph_h, int nq, int nr, int nphi, double2 *partial, cudaStream_t s);
+void launch_focal_nn(const float *y, int n, int nq, int i_d0, int nrd, int nphi, int nr, float scale,
+                     const double2 *Gr, const double2 *Gp, const double2 *emph_n, const double2 *emph_h, double2 *S,
+                     cudaStream_t s);
+void launch_focal_nn_T(const double2 *G, int n, int nq, int i_d0, int nrd, int nphi, int nr, float scale,
+                       const double2 *Gr, const double2 *Gp, const double2 *emph_n, const double2 *emph_h, float *dy,
+                       cudaStream_t s);
 void launch_focal_sum(const double2 *partial, int nq, int nr, double2 *S, int *status, cudaStream_t s);
 void launch_adjoint_profiles(const double2 *g, const double2 *Gr, const double2 *Gp, const float *wt, int nq,
                              int nr, double r_lo, double dr, double vol_scale, float2 *beta_r, float2 *beta_p,

@@ -477,6 +477,71 @@ void launch_focal_sum(const double2 *partial, int nq, int nr, double2 *S, int *s
     k_focal_sum<<<nq, 256, 0, s>>>(partial, nr, S, status);
 }
 
+// ------------------------------------------------ focal transform on surrogate outputs
+// The surrogate's output y[b][id][j][ch] holds the monitor DFT of design row
+// i = i_d0 + id in channels ch = (q 2 + comp) 2 + part (part 0 real, 1
+// imaginary), divided by `scale`.  S[b][q] = sum_i Gr_q(i) sum_j emph_n(j) E_r
+// + Gp_q(i) sum_j emph_h(j) E_phi over those rows (the outer edge node of
+// E_phi, i = i_d1, is not among them).
+__global__ void k_focal_nn(const float *__restrict__ y, int nq, int i_d0, int nrd, int nphi, int nr, float scale,
+                           const double2 *__restrict__ Gr, const double2 *__restrict__ Gp,
+                           const double2 *__restrict__ emph_n, const double2 *__restrict__ emph_h, double2 *S)
+{
+    const int q = blockIdx.x, b = blockIdx.y;
+    const int nch = 4 * nq;
+    double2 acc = make_double2(0, 0);
+    for (int t = threadIdx.x; t < nrd * nphi; t += blockDim.x) {
+        const int id = t / nphi, j = t % nphi, i = i_d0 + id;
+        const float *v = y + (((size_t)b * nrd + id) * nphi + j) * nch + q * 4;
+        const double2 er = make_double2((double)v[0] * scale, (double)v[1] * scale);
+        const double2 ep = make_double2((double)v[2] * scale, (double)v[3] * scale);
+        const double2 a = d_cmul(Gr[(size_t)q * nr + i], d_cmul(emph_n[j], er));
+        const double2 c = d_cmul(Gp[(size_t)q * nr + i], d_cmul(emph_h[j], ep));
+        acc.x += a.x + c.x;
+        acc.y += a.y + c.y;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0) S[(size_t)b * nq + q] = acc;
+}
+
+// Transpose: dy = d obj / d y for G = dobj/dRe S + i dobj/dIm S per (b, q):
+// with w the site weight, d/dRe m = Re(conj(G) w), d/dIm m = Im(G conj(w)), times scale.
+__global__ void k_focal_nn_T(const double2 *__restrict__ G, int nq, int i_d0, int nrd, int nphi, int nr, int n,
+                             float scale, const double2 *__restrict__ Gr, const double2 *__restrict__ Gp,
+                             const double2 *__restrict__ emph_n, const double2 *__restrict__ emph_h, float *dy)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long tot = (long)n * nrd * nphi * nq * 2;
+    if (t >= tot) return;
+    const int comp = (int)(t % 2), q = (int)((t / 2) % nq);
+    const long pix = t / (2 * nq);
+    const int j = (int)(pix % nphi), id = (int)((pix / nphi) % nrd);
+    const int b = (int)(pix / ((long)nphi * nrd)), i = i_d0 + id;
+    const double2 w = comp == 0 ? d_cmul(Gr[(size_t)q * nr + i], emph_n[j]) : d_cmul(Gp[(size_t)q * nr + i], emph_h[j]);
+    const double2 g = G[(size_t)b * nq + q];
+    const double dre = g.x * w.x + g.y * w.y;      // Re(conj(G) w)
+    const double dim = g.y * w.x - g.x * w.y;      // Im(G conj(w))
+    float *o = dy + pix * (4 * nq) + (q * 2 + comp) * 2;
+    o[0] = (float)(dre * scale);
+    o[1] = (float)(dim * scale);
+}
+
+void launch_focal_nn(const float *y, int n, int nq, int i_d0, int nrd, int nphi, int nr, float scale,
+                     const double2 *Gr, const double2 *Gp, const double2 *emph_n, const double2 *emph_h, double2 *S,
+                     cudaStream_t s)
+{
+    k_focal_nn<<<dim3(nq, n), 256, 0, s>>>(y, nq, i_d0, nrd, nphi, nr, scale, Gr, Gp, emph_n, emph_h, S);
+}
+
+void launch_focal_nn_T(const double2 *G, int n, int nq, int i_d0, int nrd, int nphi, int nr, float scale,
+                       const double2 *Gr, const double2 *Gp, const double2 *emph_n, const double2 *emph_h, float *dy,
+                       cudaStream_t s)
+{
+    const long tot = (long)n * nrd * nphi * nq * 2;
+    k_focal_nn_T<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, nq, i_d0, nrd, nphi, nr, n, scale, Gr, Gp, emph_n,
+                                                              emph_h, dy);
+}
+
 // ------------------------------------------------ adjoint source profiles
 // The transpose of the focal transform gives the sensitivity
 // a_q = conj(g_q) w_q on the monitor sites; the adjoint (+m) run is driven by

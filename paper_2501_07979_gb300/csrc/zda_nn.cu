@@ -365,6 +365,15 @@ struct zda_nn {
     long long launches = 0;
     int n_fwd = 0;
     bool bound = false;
+    // optional CUDA-event timing of the convolution launches
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;       // pairs (before, after)
+    std::vector<double> ev_flops;      // useful FLOPs of each timed launch
+    size_t ev_used = 0;
+    ~zda_nn()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
 };
 
 namespace {
@@ -434,7 +443,7 @@ int round_up(int a, int b) { return (a + b - 1) / b * b; }
 //   cg        : channels per input tensor;  N : GEMM output channels
 zda_status conv(zda_nn *net, int lev, int n, int taps, const uint16_t *in0, const uint16_t *in1, int cg, int N,
                 const uint16_t *wimg, const float *bias, int nbias, int epi, void *out0, void *out1, int out_ld,
-                const uint16_t *mask0, const uint16_t *mask1, cudaStream_t s)
+                const uint16_t *mask0, const uint16_t *mask1, cudaStream_t s, double flops = 0.0)
 {
     ConvParams p{};
     p.Hp = net->H[lev] + 2;
@@ -469,8 +478,24 @@ zda_status conv(zda_nn *net, int lev, int n, int taps, const uint16_t *in0, cons
     const CUtensorMap t0 = tmap(net, in0, cg, p.P, p.br, &st);
     const CUtensorMap t1 = in1 ? tmap(net, in1, cg, p.P, p.br, &st) : t0;
     if (st != ZDA_OK) return st;
+    const bool timed = net->timing && flops > 0.0;
+    if (timed) {
+        if (net->ev_used + 2 > net->ev.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t ev;
+                NN_CUDA(cudaEventCreate(&ev));
+                net->ev.push_back(ev);
+            }
+        }
+        NN_CUDA(cudaEventRecord(net->ev[net->ev_used], s));
+    }
     cudaError_t e = launch_conv(t0, t1, p, s);
     if (e != cudaSuccess) return nn_fail(ZDA_ERR_CUDA, std::string("conv launch: ") + cudaGetErrorString(e));
+    if (timed) {
+        NN_CUDA(cudaEventRecord(net->ev[net->ev_used + 1], s));
+        net->ev_used += 2;
+        net->ev_flops.push_back(flops);
+    }
     net->launches++;
     return ZDA_OK;
 }
@@ -531,6 +556,13 @@ zda_status pack_all(zda_nn *net, cudaStream_t s)
     }
     NN_CUDA(cudaGetLastError());
     return ZDA_OK;
+}
+
+// useful forward FLOPs of layer i over n samples (true channel counts, H_l x W_l outputs)
+double lf(const zda_nn *net, int i, int n)
+{
+    const Layer &l = net->L[i];
+    return 2.0 * n * net->H[l.level] * net->W[l.level] * l.k * l.k * l.cin * l.cout;
 }
 
 const uint16_t *A(zda_nn *net, int lev, int k) { return at<uint16_t>(net, net->o.act[lev][k]); }
@@ -709,9 +741,9 @@ zda_status zda_nn_forward(zda_nn *net, const float *x, int n, float *y, void *st
     int cin = 16;
     for (int l = 0; l < 3; ++l) {
         TRY(conv(net, l, n, 9, inp, nullptr, cin, C, Wf(net, 2 * l), Bias(net, 2 * l), C, EPI_RELU_BF16, Aw(net, l, A_ENCA),
-                 nullptr, C, nullptr, nullptr, s));
+                 nullptr, C, nullptr, nullptr, s, lf(net, 2 * l, n)));
         TRY(conv(net, l, n, 9, A(net, l, A_ENCA), nullptr, C, C, Wf(net, 2 * l + 1), Bias(net, 2 * l + 1), C, EPI_RELU_BF16,
-                 Aw(net, l, A_ENCB), nullptr, C, nullptr, nullptr, s));
+                 Aw(net, l, A_ENCB), nullptr, C, nullptr, nullptr, s, lf(net, 2 * l + 1, n)));
         k_pool<<<nblocks(pos_count(net, l + 1, n) * 8), 256, 0, s>>>(A(net, l, A_ENCB), n, net->H[l + 1], net->W[l + 1],
                                                                     Aw(net, l + 1, A_IN));
         net->launches++;
@@ -719,23 +751,23 @@ zda_status zda_nn_forward(zda_nn *net, const float *x, int n, float *y, void *st
         cin = C;
     }
     TRY(conv(net, 3, n, 9, inp, nullptr, C, C, Wf(net, 6), Bias(net, 6), C, EPI_RELU_BF16, Aw(net, 3, A_ENCA), nullptr, C,
-             nullptr, nullptr, s));
+             nullptr, nullptr, s, lf(net, 6, n)));
     TRY(conv(net, 3, n, 9, A(net, 3, A_ENCA), nullptr, C, C, Wf(net, 7), Bias(net, 7), C, EPI_RELU_BF16,
-             Aw(net, 3, A_ENCB), nullptr, C, nullptr, nullptr, s));
+             Aw(net, 3, A_ENCB), nullptr, C, nullptr, nullptr, s, lf(net, 7, n)));
     const uint16_t *below = A(net, 3, A_ENCB);
     for (int l = 2; l >= 0; --l) {
         const int li = 8 + 2 * (2 - l);
         k_up<<<nblocks(pos_count(net, l, n) * 8), 256, 0, s>>>(below, n, net->H[l], net->W[l], Aw(net, l, A_UP));
         net->launches++;
         TRY(conv(net, l, n, 9, A(net, l, A_UP), A(net, l, A_ENCB), C, C, Wf(net, li), Bias(net, li), C, EPI_RELU_BF16,
-                 Aw(net, l, A_DECA), nullptr, C, nullptr, nullptr, s));
+                 Aw(net, l, A_DECA), nullptr, C, nullptr, nullptr, s, lf(net, li, n)));
         TRY(conv(net, l, n, 9, A(net, l, A_DECA), nullptr, C, C, Wf(net, li + 1), Bias(net, li + 1), C, EPI_RELU_BF16,
-                 Aw(net, l, A_DECB), nullptr, C, nullptr, nullptr, s));
+                 Aw(net, l, A_DECB), nullptr, C, nullptr, nullptr, s, lf(net, li + 1, n)));
         below = A(net, l, A_DECB);
     }
     float *yh = at<float>(net, net->o.yh);
     TRY(conv(net, 0, n, 1, below, nullptr, C, 32, Wf(net, 14), Bias(net, 14), net->d.out_ch, EPI_F32, yh, nullptr, 32, nullptr,
-             nullptr, s));
+             nullptr, s, lf(net, 14, n)));
     k_unpack_f32<<<nblocks((long)n * H * W * net->d.out_ch), 256, 0, s>>>(yh, 32, n, H, W, net->d.out_ch, y);
     net->launches++;
     NN_CUDA(cudaGetLastError());
@@ -840,6 +872,34 @@ zda_status zda_nn_adam(zda_nn *net, float lr, float b1, float b2, float eps, voi
 }
 
 long long zda_nn_launch_count(const zda_nn *net) { return net ? net->launches : 0; }
+
+zda_status zda_nn_set_timing(zda_nn *net, int on)
+{
+    if (!net) return nn_fail(ZDA_ERR_ARG, "null network");
+    net->timing = on != 0;
+    net->ev_used = 0;
+    net->ev_flops.clear();
+    return ZDA_OK;
+}
+
+zda_status zda_nn_timing(zda_nn *net, double *conv_ms, double *conv_flops, int *launches)
+{
+    if (!net || !conv_ms || !conv_flops || !launches) return nn_fail(ZDA_ERR_ARG, "null argument");
+    double ms = 0.0, fl = 0.0;
+    for (size_t k = 0; k + 1 < net->ev_used; k += 2) {
+        NN_CUDA(cudaEventSynchronize(net->ev[k + 1]));
+        float t = 0.f;
+        NN_CUDA(cudaEventElapsedTime(&t, net->ev[k], net->ev[k + 1]));
+        ms += t;
+        fl += net->ev_flops[k / 2];
+    }
+    *conv_ms = ms;
+    *conv_flops = fl;
+    *launches = (int)(net->ev_used / 2);
+    net->ev_used = 0;
+    net->ev_flops.clear();
+    return ZDA_OK;
+}
 
 zda_status zda_nn_check(zda_nn *net, void *stream)
 {

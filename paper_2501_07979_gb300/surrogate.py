@@ -70,6 +70,30 @@ class Surrogate:
         return t
 
     # ------------------------------------------------------------ parameters
+    def layer_shapes(self):
+        """(k, c_in, c_out) of the 15 layers in parameter order (include/zda_nn.h)."""
+        C = 64
+        layers = []
+        for lev in range(3):
+            layers += [(3, self.in_ch if lev == 0 else C, C), (3, C, C)]
+        layers += [(3, C, C), (3, C, C)]
+        for _ in range(3):
+            layers += [(3, 2 * C, C), (3, C, C)]
+        return layers + [(1, C, self.out_ch)]
+
+    def init_params(self, seed):
+        """He-normal weights (std sqrt(2 / fan_in)), zero biases, the head
+        scaled by 0.1; sets them (and resets Adam)."""
+        rng = np.random.default_rng(seed)
+        shapes = self.layer_shapes()
+        parts = []
+        for i, (k, ci, co) in enumerate(shapes):
+            std = np.sqrt(2.0 / (k * k * ci)) * (0.1 if i == len(shapes) - 1 else 1.0)
+            parts += [rng.standard_normal(co * k * k * ci) * std, np.zeros(co)]
+        v = np.concatenate(parts).astype(np.float32)
+        assert v.size == self.n_params
+        self.set_params(v)
+
     def set_params(self, vec):
         v = self._f32(np.asarray(vec, dtype=np.float32) if not hasattr(vec, "data_ptr") else vec)
         if v.numel() != self.n_params:
@@ -131,6 +155,15 @@ class Surrogate:
         self.backward(dy)
         self.adam(lr)
         return loss
+
+    def set_timing(self, on=True):
+        check(_lib.lib().zda_nn_set_timing(self.handle, int(bool(on))))
+
+    def timing(self):
+        """(summed ms, useful FLOPs, launches) of the timed forward convolutions."""
+        ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        check(_lib.lib().zda_nn_timing(self.handle, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+        return ms.value, fl.value, n.value
 
     def check(self):
         check(_lib.lib().zda_nn_check(self.handle, self._stream()))
