@@ -28,7 +28,7 @@ def test_focal_transform_on_surrogate_layout_matches_oracle():
     mon = r.standard_normal((Q, 2, spec.n_r, spec.n_phi)) + 1j * r.standard_normal((Q, 2, spec.n_r, spec.n_phi))
     scale = 0.37
     y = np.stack([S.target_from_monitor(mon, g.i_d0, g.i_d1, scale), S.target_from_monitor(2 * mon, g.i_d0, g.i_d1, scale)])
-    yt = torch.tensor(y, dtype=torch.float32, device="cuda:0")
+    yt = torch.tensor(np.ascontiguousarray(y), dtype=torch.float32, device="cuda:0").contiguous()
     Sd = torch.empty((2, Q, 2), dtype=torch.float64, device="cuda:0")
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     _lib.check(_lib.lib().zda_focal_transform_nn(z.handle, ctypes.c_void_p(yt.data_ptr()), 2, scale,
@@ -43,7 +43,7 @@ def test_focal_transform_on_surrogate_layout_matches_oracle():
     # transpose: dobj/dy for G = dobj/dRe S + i dobj/dIm S
     G = r.standard_normal((2, Q)) + 1j * r.standard_normal((2, Q))
     Gd = torch.tensor(np.stack([G.real, G.imag], -1), dtype=torch.float64, device="cuda:0").contiguous()
-    dy = torch.empty_like(yt)
+    dy = torch.empty(tuple(yt.shape), dtype=torch.float32, device="cuda:0")
     _lib.check(_lib.lib().zda_focal_transform_nn_transpose(z.handle, ctypes.c_void_p(Gd.data_ptr()), 2, scale,
                                                    ctypes.c_void_p(dy.data_ptr()), st))
     dy = dy.cpu().numpy()
