@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--workload", default="zone", choices=["zone", "surrogate"],
                     help="zone: forward + adjoint FDTD iteration of the wide zone (headline); "
                          "surrogate: U-Net inference, 128 x 128 patches, batch 256")
+    ap.add_argument("--batch", type=int, default=256, help="surrogate workload: samples per forward")
     ap.add_argument("--kernel", default="default", choices=["default", "split", "split1", "fused2", "fused4"],
                     help="time-step kernel (default: the library's choice for the zone)")
     return ap.parse_args()
@@ -384,7 +385,7 @@ def run_nn(a):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_2501_07979_gb300.surrogate import Surrogate
-    sh = NN_SHAPE
+    sh = dict(NN_SHAPE, batch=a.batch)
     net = Surrogate(sh["H"], sh["W"], sh["in_ch"], sh["out_ch"], sh["batch"], device=local)
     net.init_params(1 + rank)
     g = torch.Generator(device="cpu").manual_seed(3 + rank)
@@ -467,7 +468,7 @@ def run_nn(a):
             traffic = None
     line = {"metric": NN_METRIC, "value": value, "unit": NN_UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": nn_config(),
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": dict(nn_config(), batch=sh["batch"]),
             "roofline": {"bound": "tensor", "kernel": "k_conv_tc", "achieved": ach, "peak": peak,
                          "unit": "TFLOP/s", "frac": (ach / peak) if ach else None, "traffic": traffic,
                          "peak_source": "measured (bf16 burst)" if "bf16_tflops" in peaks else "fallback",
