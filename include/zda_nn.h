@@ -49,7 +49,8 @@ typedef struct zda_nn zda_nn;
 typedef struct {
     int batch;      /* largest number of samples per call (>= 1) */
     int height;     /* H, a multiple of 8, 8 .. 1024 */
-    int width;      /* W, a multiple of 8, 8 .. 1024 */
+    int width;      /* W, a multiple of 8, 8 .. 176 (the convolution's shared-memory window
+                       holds 2 x (256 + 2 (W + 3)) positions x 64 channels) */
     int in_ch;      /* input channels, 1 .. 16 */
     int out_ch;     /* output channels, 1 .. 32 */
 } zda_nn_desc;

@@ -51,19 +51,28 @@ __device__ __forceinline__ uint16_t f2bf(float f)
 __device__ __forceinline__ bool interior(int y, int x, int Hp, int Wp) { return y > 0 && y < Hp - 1 && x > 0 && x < Wp - 1; }
 
 // ---------------------------------------------------------------- helper kernels
-// x [n][H][W][ic] f32 -> padded bf16 [n][H+2][W+2][16]
-__global__ void k_pack_input(const float *x, int n, int H, int W, int ic, uint16_t *out)
+// Planar element offset of (channel plane c8, position pos) in a tensor of `rows` rows per plane.
+__device__ __forceinline__ size_t pofs(long rows, int c8, long pos) { return ((size_t)c8 * rows + LEAD + pos) * 8; }
+
+// x [n][H][W][ic] f32 -> planar bf16, 16 channels (2 planes), positions < Pt (zero border, zero tail)
+__global__ void k_pack_input(const float *x, int n, int H, int W, int ic, long Pt, long rows, uint16_t *out)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * Pt) return;
+    const int c8 = (int)(i / Pt);
+    const long pos = i % Pt;
     const int Hp = H + 2, Wp = W + 2;
     const long P = (long)n * Hp * Wp;
-    if (i >= P * 16) return;
-    const int c = (int)(i % 16);
-    const long pos = i / 16;
     const int rem = (int)(pos % (Hp * Wp)), y = rem / Wp, xx = rem % Wp;
-    float v = 0.f;
-    if (c < ic && interior(y, xx, Hp, Wp)) v = x[(((pos / (Hp * Wp)) * H + (y - 1)) * W + (xx - 1)) * ic + c];
-    out[i] = f2bf(v);
+    uint16_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (pos < P && interior(y, xx, Hp, Wp)) {
+        const float *src = x + (((pos / (Hp * Wp)) * H + (y - 1)) * W + (xx - 1)) * ic;
+        for (int e = 0; e < 8; ++e) {
+            const int c = c8 * 8 + e;
+            if (c < ic) r[e] = f2bf(src[c]);
+        }
+    }
+    *reinterpret_cast<uint4 *>(out + pofs(rows, c8, pos)) = *reinterpret_cast<uint4 *>(r);
 }
 
 // padded f32 [P][ld] (channels < nc) -> [n][H][W][nc] f32
@@ -78,38 +87,60 @@ __global__ void k_unpack_f32(const float *in, int ld, int n, int H, int W, int n
     out[i] = in[((s * (H + 2) + y + 1) * (W + 2) + x + 1) * ld + c];
 }
 
-// [n][H][W][nc] f32 -> padded bf16 [P][32] (zeros on the border and for c >= nc)
-__global__ void k_pack_grad(const float *dy, int n, int H, int W, int nc, uint16_t *out)
+// [n][H][W][nc] f32 -> planar bf16, 32 channels (4 planes), positions < Pt (zeros elsewhere)
+__global__ void k_pack_grad(const float *dy, int n, int H, int W, int nc, long Pt, long rows, uint16_t *out)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * Pt) return;
+    const int c8 = (int)(i / Pt);
+    const long pos = i % Pt;
     const int Hp = H + 2, Wp = W + 2;
-    if (i >= (long)n * Hp * Wp * 32) return;
-    const int c = (int)(i % 32);
-    const long pos = i / 32;
+    const long P = (long)n * Hp * Wp;
     const int rem = (int)(pos % (Hp * Wp)), y = rem / Wp, x = rem % Wp;
-    float v = 0.f;
-    if (c < nc && interior(y, x, Hp, Wp)) v = dy[(((pos / (Hp * Wp)) * H + (y - 1)) * W + (x - 1)) * nc + c];
-    out[i] = f2bf(v);
+    uint16_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (pos < P && interior(y, x, Hp, Wp)) {
+        const float *src = dy + (((pos / (Hp * Wp)) * H + (y - 1)) * W + (x - 1)) * nc;
+        for (int e = 0; e < 8; ++e) {
+            const int c = c8 * 8 + e;
+            if (c < nc) r[e] = f2bf(src[c]);
+        }
+    }
+    *reinterpret_cast<uint4 *>(out + pofs(rows, c8, pos)) = *reinterpret_cast<uint4 *>(r);
 }
 
-// One thread per (coarse position, 8 channels); 64-channel tensors.
+// The position-parallel kernels below run one thread per (plane, position)
+// over Pt positions (the 256-rounded tail is written as zeros), 64 channels.
+struct Lev {
+    int n, H, W;        // samples, interior size of this level
+    long rows, Pt;      // rows per plane, positions covered (multiple of 256)
+};
+
+__device__ __forceinline__ bool decode(const Lev &L, long pos, long &s, int &y, int &x)
+{
+    const int Hp = L.H + 2, Wp = L.W + 2;
+    s = pos / (Hp * Wp);
+    const int rem = (int)(pos % (Hp * Wp));
+    y = rem / Wp;
+    x = rem % Wp;
+    return s < L.n && interior(y, x, Hp, Wp);
+}
+
 // avgpool: coarse interior (i, j) = mean of fine interior (2i .. 2i+1, 2j .. 2j+1)
-__global__ void k_pool(const uint16_t *in, int n, int Hc, int Wc, uint16_t *out)
+__global__ void k_pool(const uint16_t *in, Lev F, uint16_t *out, Lev Cc)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Hp = Hc + 2, Wp = Wc + 2, Wf = 2 * Wc + 2;
-    if (i >= (long)n * Hp * Wp * 8) return;
-    const int c8 = (int)(i % 8);
-    const long pos = i / 8;
-    const long s = pos / (Hp * Wp);
-    const int rem = (int)(pos % (Hp * Wp)), y = rem / Wp, x = rem % Wp;
+    if (i >= 8 * Cc.Pt) return;
+    const int c8 = (int)(i / Cc.Pt);
+    const long pos = i % Cc.Pt;
+    long s;
+    int y, x;
     uint4 o = make_uint4(0, 0, 0, 0);
-    if (interior(y, x, Hp, Wp)) {
+    if (decode(Cc, pos, s, y, x)) {
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
-                const long fp = (s * (2 * Hc + 2) + 2 * y - 1 + a) * Wf + 2 * x - 1 + b;
-                const uint4 q = *reinterpret_cast<const uint4 *>(in + fp * C + c8 * 8);
+                const long fp = (s * (F.H + 2) + 2 * y - 1 + a) * (F.W + 2) + 2 * x - 1 + b;
+                const uint4 q = *reinterpret_cast<const uint4 *>(in + pofs(F.rows, c8, fp));
                 const uint16_t *h = reinterpret_cast<const uint16_t *>(&q);
                 for (int e = 0; e < 8; ++e) acc[e] += bf2f(h[e]);
             }
@@ -117,95 +148,99 @@ __global__ void k_pool(const uint16_t *in, int n, int Hc, int Wc, uint16_t *out)
         for (int e = 0; e < 8; ++e) r[e] = f2bf(0.25f * acc[e]);
         o = *reinterpret_cast<uint4 *>(r);
     }
-    *reinterpret_cast<uint4 *>(out + pos * C + c8 * 8) = o;
+    *reinterpret_cast<uint4 *>(out + pofs(Cc.rows, c8, pos)) = o;
 }
 
 // nearest upsampling: fine interior (i, j) = coarse interior (i / 2, j / 2)
-__global__ void k_up(const uint16_t *in, int n, int Hf, int Wf, uint16_t *out)
+__global__ void k_up(const uint16_t *in, Lev Cc, uint16_t *out, Lev F)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Hp = Hf + 2, Wp = Wf + 2, Hcp = Hf / 2 + 2, Wcp = Wf / 2 + 2;
-    if (i >= (long)n * Hp * Wp * 8) return;
-    const int c8 = (int)(i % 8);
-    const long pos = i / 8;
-    const long s = pos / (Hp * Wp);
-    const int rem = (int)(pos % (Hp * Wp)), y = rem / Wp, x = rem % Wp;
+    if (i >= 8 * F.Pt) return;
+    const int c8 = (int)(i / F.Pt);
+    const long pos = i % F.Pt;
+    long s;
+    int y, x;
     uint4 o = make_uint4(0, 0, 0, 0);
-    if (interior(y, x, Hp, Wp))
-        o = *reinterpret_cast<const uint4 *>(in + ((s * Hcp + (y - 1) / 2 + 1) * Wcp + (x - 1) / 2 + 1) * C + c8 * 8);
-    *reinterpret_cast<uint4 *>(out + pos * C + c8 * 8) = o;
+    if (decode(F, pos, s, y, x)) {
+        const long cp = (s * (Cc.H + 2) + (y - 1) / 2 + 1) * (Cc.W + 2) + (x - 1) / 2 + 1;
+        o = *reinterpret_cast<const uint4 *>(in + pofs(Cc.rows, c8, cp));
+    }
+    *reinterpret_cast<uint4 *>(out + pofs(F.rows, c8, pos)) = o;
 }
 
 // transpose of nearest upsampling (sum over each 2x2 block) times the sign
 // mask of the coarse activation: coarse output
-__global__ void k_up_bwd_mask(const uint16_t *g, const uint16_t *act, int n, int Hc, int Wc, uint16_t *out)
+__global__ void k_up_bwd_mask(const uint16_t *g, Lev F, const uint16_t *act, uint16_t *out, Lev Cc)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Hp = Hc + 2, Wp = Wc + 2, Wf = 2 * Wc + 2;
-    if (i >= (long)n * Hp * Wp * 8) return;
-    const int c8 = (int)(i % 8);
-    const long pos = i / 8;
-    const long s = pos / (Hp * Wp);
-    const int rem = (int)(pos % (Hp * Wp)), y = rem / Wp, x = rem % Wp;
+    if (i >= 8 * Cc.Pt) return;
+    const int c8 = (int)(i / Cc.Pt);
+    const long pos = i % Cc.Pt;
+    long s;
+    int y, x;
     uint4 o = make_uint4(0, 0, 0, 0);
-    if (interior(y, x, Hp, Wp)) {
+    if (decode(Cc, pos, s, y, x)) {
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
-                const long fp = (s * (2 * Hc + 2) + 2 * y - 1 + a) * Wf + 2 * x - 1 + b;
-                const uint4 q = *reinterpret_cast<const uint4 *>(g + fp * C + c8 * 8);
+                const long fp = (s * (F.H + 2) + 2 * y - 1 + a) * (F.W + 2) + 2 * x - 1 + b;
+                const uint4 q = *reinterpret_cast<const uint4 *>(g + pofs(F.rows, c8, fp));
                 const uint16_t *h = reinterpret_cast<const uint16_t *>(&q);
                 for (int e = 0; e < 8; ++e) acc[e] += bf2f(h[e]);
             }
-        const uint4 mq = *reinterpret_cast<const uint4 *>(act + pos * C + c8 * 8);
+        const uint4 mq = *reinterpret_cast<const uint4 *>(act + pofs(Cc.rows, c8, pos));
         const uint16_t *m = reinterpret_cast<const uint16_t *>(&mq);
         uint16_t r[8];
         for (int e = 0; e < 8; ++e) r[e] = f2bf(bf2f(m[e]) > 0.f ? acc[e] : 0.f);
         o = *reinterpret_cast<uint4 *>(r);
     }
-    *reinterpret_cast<uint4 *>(out + pos * C + c8 * 8) = o;
+    *reinterpret_cast<uint4 *>(out + pofs(Cc.rows, c8, pos)) = o;
 }
 
 // skip gradient of level l: mask(act > 0) * (g_skip + transpose of avgpool applied to g_coarse)
-__global__ void k_skip_combine(const uint16_t *gs, const uint16_t *gc, const uint16_t *act, int n, int Hf, int Wf,
-                               uint16_t *out)
+__global__ void k_skip_combine(const uint16_t *gs, const uint16_t *gc, Lev Cc, const uint16_t *act, uint16_t *out,
+                               Lev F)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Hp = Hf + 2, Wp = Wf + 2, Hcp = Hf / 2 + 2, Wcp = Wf / 2 + 2;
-    if (i >= (long)n * Hp * Wp * 8) return;
-    const int c8 = (int)(i % 8);
-    const long pos = i / 8;
-    const long s = pos / (Hp * Wp);
-    const int rem = (int)(pos % (Hp * Wp)), y = rem / Wp, x = rem % Wp;
+    if (i >= 8 * F.Pt) return;
+    const int c8 = (int)(i / F.Pt);
+    const long pos = i % F.Pt;
+    long s;
+    int y, x;
     uint4 o = make_uint4(0, 0, 0, 0);
-    if (interior(y, x, Hp, Wp)) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(gs + pos * C + c8 * 8);
-        const uint4 b = *reinterpret_cast<const uint4 *>(
-            gc + ((s * Hcp + (y - 1) / 2 + 1) * Wcp + (x - 1) / 2 + 1) * C + c8 * 8);
-        const uint4 mq = *reinterpret_cast<const uint4 *>(act + pos * C + c8 * 8);
+    if (decode(F, pos, s, y, x)) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(gs + pofs(F.rows, c8, pos));
+        const long cp = (s * (Cc.H + 2) + (y - 1) / 2 + 1) * (Cc.W + 2) + (x - 1) / 2 + 1;
+        const uint4 b = *reinterpret_cast<const uint4 *>(gc + pofs(Cc.rows, c8, cp));
+        const uint4 mq = *reinterpret_cast<const uint4 *>(act + pofs(F.rows, c8, pos));
         const uint16_t *ha = reinterpret_cast<const uint16_t *>(&a), *hb = reinterpret_cast<const uint16_t *>(&b),
                        *m = reinterpret_cast<const uint16_t *>(&mq);
         uint16_t r[8];
         for (int e = 0; e < 8; ++e) r[e] = f2bf(bf2f(m[e]) > 0.f ? bf2f(ha[e]) + 0.25f * bf2f(hb[e]) : 0.f);
         o = *reinterpret_cast<uint4 *>(r);
     }
-    *reinterpret_cast<uint4 *>(out + pos * C + c8 * 8) = o;
+    *reinterpret_cast<uint4 *>(out + pofs(F.rows, c8, pos)) = o;
 }
 
-// column sums of a bf16 [P][ld] array (channels < nc): partial[block][c]
-__global__ void k_colsum(const uint16_t *g, long P, int ld, int nc, float *partial)
+// column sums of a planar bf16 tensor of `planes` planes over positions < P
+// (channels < nc): partial[block][c]; thread t covers channel t % 8 of rows
+// t / 8, t / 8 + 32, ... of each plane.
+__global__ void k_colsum(const uint16_t *g, long rows, long P, int planes, int nc, float *partial)
 {
     __shared__ float red[256];
-    const int rows = 256 / ld;              // ld in {16, 32, 64}
-    const int c = threadIdx.x % ld, r0 = threadIdx.x / ld;
-    float acc = 0.f;
-    for (long p = (long)blockIdx.x * rows + r0; p < P; p += (long)gridDim.x * rows) acc += bf2f(g[p * ld + c]);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < ld) {
-        float s = 0.f;
-        for (int r = 0; r < rows; ++r) s += red[r * ld + threadIdx.x];
-        if (threadIdx.x < nc) partial[(size_t)blockIdx.x * nc + threadIdx.x] = s;
+    const int e = threadIdx.x % 8, r0 = threadIdx.x / 8;
+    for (int c8 = 0; c8 < planes; ++c8) {
+        float acc = 0.f;
+        for (long p = (long)blockIdx.x * 32 + r0; p < P; p += (long)gridDim.x * 32) acc += bf2f(g[pofs(rows, c8, p) + e]);
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            float s = 0.f;
+            for (int r = 0; r < 32; ++r) s += red[r * 8 + threadIdx.x];
+            const int c = c8 * 8 + threadIdx.x;
+            if (c < nc) partial[(size_t)blockIdx.x * nc + c] = s;
+        }
+        __syncthreads();
     }
 }
 
@@ -323,31 +358,13 @@ struct Layer {
     long img_f, img_d; // image offsets (elements)
 };
 
-typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeFn encode_fn()
-{
-    static std::once_flag once;
-    static EncodeFn fn = nullptr;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeFn>(p);
-    });
-    return fn;
-}
-
 }  // namespace
 
 struct zda_nn {
     int device = 0;
     zda_nn_desc d{};
     int H[LEV], W[LEV];
+    long rows[LEV];        // rows per plane of the level's planar tensors (batch capacity)
     Layer L[NL];
     long nparam = 0, img_elems = 0;
     double flops = 0;
@@ -384,6 +401,8 @@ enum { G_A = 0, G_B, G_U, G_S };
 template <class T> T *at(zda_nn *net, size_t off) { return reinterpret_cast<T *>(net->ws + off); }
 
 long pos_count(const zda_nn *net, int lev, int n) { return (long)n * (net->H[lev] + 2) * (net->W[lev] + 2); }
+long pos_tiles(const zda_nn *net, int lev, int n) { return (pos_count(net, lev, n) + 255) / 256 * 256; }
+Lev lev(const zda_nn *net, int l, int n) { return Lev{n, net->H[l], net->W[l], net->rows[l], pos_tiles(net, l, n)}; }
 
 void build_layers(zda_nn *net)
 {
@@ -415,54 +434,39 @@ void build_layers(zda_nn *net)
     net->flops = fl;
 }
 
-CUtensorMap tmap(zda_nn *net, const void *base, int ch, long rows, int box_rows, zda_status *st)
-{
-    CUtensorMap m;
-    std::memset(&m, 0, sizeof(m));
-    EncodeFn fn = encode_fn();
-    if (!fn) {
-        *st = nn_fail(ZDA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-        return m;
-    }
-    cuuint64_t dims[2] = {(cuuint64_t)ch, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ch * 2};
-    cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) *st = nn_fail(ZDA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    (void)net;
-    return m;
-}
-
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // Convolution (forward or input gradient) of one layer.
 //   in0 / in1 : input tensors (in1 = second half of a concatenated input or null)
 //   cg        : channels per input tensor;  N : GEMM output channels
-zda_status conv(zda_nn *net, int lev, int n, int taps, const uint16_t *in0, const uint16_t *in1, int cg, int N,
+zda_status conv(zda_nn *net, int lv, int n, int taps, const uint16_t *in0, const uint16_t *in1, int cg, int N,
                 const uint16_t *wimg, const float *bias, int nbias, int epi, void *out0, void *out1, int out_ld,
                 const uint16_t *mask0, const uint16_t *mask1, cudaStream_t s, double flops = 0.0)
 {
     ConvParams p{};
-    p.Hp = net->H[lev] + 2;
-    p.Wp = net->W[lev] + 2;
-    p.P = (int)pos_count(net, lev, n);
+    p.Hp = net->H[lv] + 2;
+    p.Wp = net->W[lv] + 2;
+    p.P = (int)pos_count(net, lv, n);
     p.taps = taps;
     p.halo = taps == 9 ? p.Wp + 1 : 0;
     p.mt = 2;
-    const int R = p.mt * 128 + 2 * p.halo;
-    p.npiece = (R + 255) / 256;
-    p.br = round_up((R + p.npiece - 1) / p.npiece, 8);
-    p.plane = p.npiece * p.br * 16;
+    p.R = p.mt * 128 + 2 * p.halo;
+    p.plane = round_up(p.R, 8) * 16;
+    p.rows = net->rows[lv];
     p.cg = cg;
     p.ngroups = in1 ? 2 : 1;
     p.N = N;
-    p.slots = N >= 128 ? 2 : 4;
+    // weights resident if they fit beside the two window stages, else a ring
+    // of as many per-tap slots as fit (at most 8)
+    const size_t budget = 220 * 1024;
+    const size_t win2 = 2 * (size_t)(cg / 8) * p.plane, wslot = (size_t)N * cg * 2;
+    p.resident = win2 + (size_t)p.ngroups * taps * wslot <= budget ? 1 : 0;
+    p.slots = p.resident ? 1 : (int)std::max<size_t>(2, std::min<size_t>(8, (budget - win2) / wslot));
     uint32_t nc = 32;
-    while (nc < (uint32_t)(p.mt * N)) nc <<= 1;
+    while (nc < (uint32_t)(2 * p.mt * N)) nc <<= 1;   // two accumulators (double buffering)
     p.ncols = nc;
+    p.in0 = in0;
+    p.in1 = in1;
     p.wimg = wimg;
     p.bias = bias;
     p.nbias = nbias;
@@ -474,10 +478,6 @@ zda_status conv(zda_nn *net, int lev, int n, int taps, const uint16_t *in0, cons
     p.mask1 = mask1;
     p.err = at<int>(net, net->o.err);
     p.wait_limit = 1 << 22;
-    zda_status st = ZDA_OK;
-    const CUtensorMap t0 = tmap(net, in0, cg, p.P, p.br, &st);
-    const CUtensorMap t1 = in1 ? tmap(net, in1, cg, p.P, p.br, &st) : t0;
-    if (st != ZDA_OK) return st;
     const bool timed = net->timing && flops > 0.0;
     if (timed) {
         if (net->ev_used + 2 > net->ev.size()) {
@@ -489,7 +489,7 @@ zda_status conv(zda_nn *net, int lev, int n, int taps, const uint16_t *in0, cons
         }
         NN_CUDA(cudaEventRecord(net->ev[net->ev_used], s));
     }
-    cudaError_t e = launch_conv(t0, t1, p, s);
+    cudaError_t e = launch_conv(p, s);
     if (e != cudaSuccess) return nn_fail(ZDA_ERR_CUDA, std::string("conv launch: ") + cudaGetErrorString(e));
     if (timed) {
         NN_CUDA(cudaEventRecord(net->ev[net->ev_used + 1], s));
@@ -523,18 +523,16 @@ zda_status layer_grad(zda_nn *net, int li, int n, const uint16_t *x0, const uint
     splits = (p.ntiles + p.tiles_per_cta - 1) / p.tiles_per_cta;
     if ((size_t)splits * p.ngroups * 128 * p.N > net->wpart_floats)
         return nn_fail(ZDA_ERR_OOM, "weight-gradient partial buffer too small");
+    p.rows = net->rows[l.level];
+    p.x0 = x0;
+    p.x1 = x1;
+    p.dy = g;
     p.partial = at<float>(net, net->o.wpart);
     p.err = at<int>(net, net->o.err);
     p.wait_limit = 1 << 22;
-    zda_status st = ZDA_OK;
-    const int cgx = x1 ? 64 : l.cin_pad;
-    const CUtensorMap tx0 = tmap(net, x0, cgx, p.P, p.kt, &st);
-    const CUtensorMap tx1 = x1 ? tmap(net, x1, cgx, p.P, p.kt, &st) : tx0;
-    const CUtensorMap tg = tmap(net, g, ldg, p.P, p.kt, &st);
-    if (st != ZDA_OK) return st;
-    cudaError_t e = launch_wgrad(tx0, tx1, tg, p, splits, s);
+    cudaError_t e = launch_wgrad(p, splits, s);
     if (e != cudaSuccess) return nn_fail(ZDA_ERR_CUDA, std::string("wgrad launch: ") + cudaGetErrorString(e));
-    k_colsum<<<net->bpart_blocks, 256, 0, s>>>(g, p.P, ldg, l.cout, at<float>(net, net->o.bpart));
+    k_colsum<<<net->bpart_blocks, 256, 0, s>>>(g, p.rows, p.P, ldg / 8, l.cout, at<float>(net, net->o.bpart));
     const long nw = (long)l.cout * p.taps * l.cin + l.cout;
     k_layer_grad<<<nblocks(nw), 256, 0, s>>>(at<float>(net, net->o.wpart), splits, p.ngroups, p.ntap_grp, l.cin_pad,
                                              p.N, at<float>(net, net->o.bpart), net->bpart_blocks, l.cout, l.cin,
@@ -582,9 +580,9 @@ zda_status zda_nn_create(int device, const zda_nn_desc *d, zda_nn **out)
     if (!d || !out) return nn_fail(ZDA_ERR_ARG, "null argument");
     *out = nullptr;
     if (d->batch < 1 || d->height < 8 || d->width < 8 || d->height % 8 || d->width % 8 || d->height > 1024 ||
-        d->width > 1024 || d->in_ch < 1 || d->in_ch > 16 || d->out_ch < 1 || d->out_ch > 32)
-        return nn_fail(ZDA_ERR_ARG, "invalid network descriptor (H, W multiples of 8 in 8..1024; 1..16 inputs; "
-                                    "1..32 outputs; batch >= 1)");
+        d->width > 176 || d->in_ch < 1 || d->in_ch > 16 || d->out_ch < 1 || d->out_ch > 32)
+        return nn_fail(ZDA_ERR_ARG, "invalid network descriptor (H multiple of 8 in 8..1024, W multiple of 8 in "
+                                    "8..176; 1..16 inputs; 1..32 outputs; batch >= 1)");
     const long P0 = (long)d->batch * (d->height + 2) * (d->width + 2);
     if (P0 * 64 > (1L << 31) - 1) return nn_fail(ZDA_ERR_ARG, "batch x image too large for 32-bit positions");
     zda_nn *net = new zda_nn();
@@ -593,6 +591,7 @@ zda_status zda_nn_create(int device, const zda_nn_desc *d, zda_nn **out)
     for (int l = 0; l < LEV; ++l) {
         net->H[l] = d->height >> l;
         net->W[l] = d->width >> l;
+        net->rows[l] = LEAD + pos_tiles(net, l, d->batch) + 256;   // zero lead rows, tiles, zero trail rows
     }
     build_layers(net);
     // workspace layout
@@ -608,12 +607,12 @@ zda_status zda_nn_create(int device, const zda_nn_desc *d, zda_nn **out)
     net->o.m = take(net->nparam * 4);
     net->o.v = take(net->nparam * 4);
     net->o.img = take(net->img_elems * 2);
-    net->o.x16 = take((size_t)pos_count(net, 0, B) * 16 * 2);
+    net->o.x16 = take((size_t)net->rows[0] * 16 * 2);
     net->o.yh = take((size_t)pos_count(net, 0, B) * 32 * 4);
-    net->o.gy = take((size_t)pos_count(net, 0, B) * 32 * 2);
+    net->o.gy = take((size_t)net->rows[0] * 32 * 2);
     net->o.gx = take((size_t)pos_count(net, 0, B) * 16 * 4);
     for (int l = 0; l < LEV; ++l) {
-        const size_t t = (size_t)pos_count(net, l, B) * C * 2;
+        const size_t t = (size_t)net->rows[l] * C * 2;
         for (int k = 0; k < 6; ++k) net->o.act[l][k] = take(t);
         for (int k = 0; k < 4; ++k) net->o.g[l][k] = take(t);
     }
@@ -730,7 +729,8 @@ zda_status zda_nn_forward(zda_nn *net, const float *x, int n, float *y, void *st
     cudaStream_t s = (cudaStream_t)stream;
     const int H = net->d.height, W = net->d.width;
     uint16_t *x16 = at<uint16_t>(net, net->o.x16);
-    k_pack_input<<<nblocks(pos_count(net, 0, n) * 16), 256, 0, s>>>(x, n, H, W, net->d.in_ch, x16);
+    k_pack_input<<<nblocks(2 * pos_tiles(net, 0, n)), 256, 0, s>>>(x, n, H, W, net->d.in_ch, pos_tiles(net, 0, n),
+                                                                  net->rows[0], x16);
     net->launches++;
 #define TRY(e)                          \
     do {                                \
@@ -744,8 +744,8 @@ zda_status zda_nn_forward(zda_nn *net, const float *x, int n, float *y, void *st
                  nullptr, C, nullptr, nullptr, s, lf(net, 2 * l, n)));
         TRY(conv(net, l, n, 9, A(net, l, A_ENCA), nullptr, C, C, Wf(net, 2 * l + 1), Bias(net, 2 * l + 1), C, EPI_RELU_BF16,
                  Aw(net, l, A_ENCB), nullptr, C, nullptr, nullptr, s, lf(net, 2 * l + 1, n)));
-        k_pool<<<nblocks(pos_count(net, l + 1, n) * 8), 256, 0, s>>>(A(net, l, A_ENCB), n, net->H[l + 1], net->W[l + 1],
-                                                                    Aw(net, l + 1, A_IN));
+        k_pool<<<nblocks(8 * pos_tiles(net, l + 1, n)), 256, 0, s>>>(A(net, l, A_ENCB), lev(net, l, n),
+                                                                    Aw(net, l + 1, A_IN), lev(net, l + 1, n));
         net->launches++;
         inp = A(net, l + 1, A_IN);
         cin = C;
@@ -757,7 +757,8 @@ zda_status zda_nn_forward(zda_nn *net, const float *x, int n, float *y, void *st
     const uint16_t *below = A(net, 3, A_ENCB);
     for (int l = 2; l >= 0; --l) {
         const int li = 8 + 2 * (2 - l);
-        k_up<<<nblocks(pos_count(net, l, n) * 8), 256, 0, s>>>(below, n, net->H[l], net->W[l], Aw(net, l, A_UP));
+        k_up<<<nblocks(8 * pos_tiles(net, l, n)), 256, 0, s>>>(below, lev(net, l + 1, n), Aw(net, l, A_UP),
+                                                              lev(net, l, n));
         net->launches++;
         TRY(conv(net, l, n, 9, A(net, l, A_UP), A(net, l, A_ENCB), C, C, Wf(net, li), Bias(net, li), C, EPI_RELU_BF16,
                  Aw(net, l, A_DECA), nullptr, C, nullptr, nullptr, s, lf(net, li, n)));
@@ -784,7 +785,8 @@ zda_status zda_nn_backward(zda_nn *net, const float *dy, float *dx, void *stream
     cudaStream_t s = (cudaStream_t)stream;
     const int n = net->n_fwd, H = net->d.height, W = net->d.width;
     uint16_t *gy = at<uint16_t>(net, net->o.gy);
-    k_pack_grad<<<nblocks(pos_count(net, 0, n) * 32), 256, 0, s>>>(dy, n, H, W, net->d.out_ch, gy);
+    k_pack_grad<<<nblocks(4 * pos_tiles(net, 0, n)), 256, 0, s>>>(dy, n, H, W, net->d.out_ch, pos_tiles(net, 0, n),
+                                                                 net->rows[0], gy);
     net->launches++;
     // head
     TRY(layer_grad(net, 14, n, A(net, 0, A_DECB), nullptr, gy, 32, s));
@@ -800,8 +802,8 @@ zda_status zda_nn_backward(zda_nn *net, const float *dy, float *dx, void *stream
         TRY(conv(net, l, n, 9, Gb(net, l, G_A), nullptr, C, 2 * C, Wd(net, li), nullptr, 0, EPI_GRAD_BF16,
                  Gb(net, l, G_U), Gb(net, l, G_S), C, nullptr, nullptr, s));
         const uint16_t *below = l == 2 ? A(net, 3, A_ENCB) : A(net, l + 1, A_DECB);
-        k_up_bwd_mask<<<nblocks(pos_count(net, l + 1, n) * 8), 256, 0, s>>>(Gb(net, l, G_U), below, n, net->H[l + 1],
-                                                                           net->W[l + 1], Gb(net, l + 1, G_B));
+        k_up_bwd_mask<<<nblocks(8 * pos_tiles(net, l + 1, n)), 256, 0, s>>>(Gb(net, l, G_U), lev(net, l, n), below,
+                                                                           Gb(net, l + 1, G_B), lev(net, l + 1, n));
         net->launches++;
     }
     // bottleneck (level 3: A_ENCA = bot_a, A_ENCB = bot_b)
@@ -813,9 +815,9 @@ zda_status zda_nn_backward(zda_nn *net, const float *dy, float *dx, void *stream
              nullptr, C, nullptr, nullptr, s));
     // encoder, coarse to fine: G_U of level l + 1 holds the gradient of in_{l+1}
     for (int l = 2; l >= 0; --l) {
-        k_skip_combine<<<nblocks(pos_count(net, l, n) * 8), 256, 0, s>>>(Gb(net, l, G_S), Gb(net, l + 1, G_U),
-                                                                        A(net, l, A_ENCB), n, net->H[l], net->W[l],
-                                                                        Gb(net, l, G_B));
+        k_skip_combine<<<nblocks(8 * pos_tiles(net, l, n)), 256, 0, s>>>(Gb(net, l, G_S), Gb(net, l + 1, G_U),
+                                                                        lev(net, l + 1, n), A(net, l, A_ENCB),
+                                                                        Gb(net, l, G_B), lev(net, l, n));
         net->launches++;
         TRY(layer_grad(net, 2 * l + 1, n, A(net, l, A_ENCA), nullptr, Gb(net, l, G_B), C, s));
         TRY(conv(net, l, n, 9, Gb(net, l, G_B), nullptr, C, C, Wd(net, 2 * l + 1), nullptr, 0, EPI_GRAD_BF16,

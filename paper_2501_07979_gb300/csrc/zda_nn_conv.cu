@@ -1,24 +1,28 @@
 // Tensor-core kernels of the surrogate network (sm_103a): BF16 operands
-// staged in shared memory by TMA / bulk copies, tcgen05.mma accumulating in
-// FP32 in tensor memory, epilogues reading TMEM with tcgen05.ld.
+// staged in shared memory by bulk copies (cp.async.bulk on mbarriers),
+// tcgen05.mma accumulating in FP32 in tensor memory, epilogues reading TMEM
+// with tcgen05.ld.  Activations are planar (see zda_nn_internal.h): each
+// 8-channel plane of a window is one contiguous run of rows, which is also
+// the canonical no-swizzle operand layout (core matrix = 8 rows x 16 B).
 //
 // k_conv_tc  -- forward convolution and its input-gradient (transposed)
-//               convolution.  A CTA owns mt x 128 consecutive padded
-//               positions and all N output channels.  One TMA window of the
-//               input (the CTA's positions plus a halo of Wp + 1 rows on each
-//               side) serves all taps: tap t is the same window seen from
-//               start row halo + off(t), i.e. a different descriptor start
-//               address, so no im2col copy is ever made.  Weights stream
-//               through a ring of per-tap slots (bulk copies).
+//               convolution.  A tile is mt x 128 consecutive padded
+//               positions with all N output channels.  One window of the
+//               input (the tile's positions plus a halo of Wp + 1 rows on
+//               each side) serves all taps: tap t is the same window seen
+//               from start row halo + off(t), i.e. a different descriptor
+//               start address, so no im2col copy is ever made.
 // k_wgrad_tc -- weight gradient: both operands MN-major (channels contiguous),
 //               reduction over positions; M = 128 rows hold 128 / c_in taps'
-//               shifted copies of the input, each loaded pre-shifted by TMA.
+//               shifted copies of the input, each copied pre-shifted.
 //
 // Roles (128 threads): warp 0 lane 0 = producer (TMA), warp 1 lane 0 = MMA
 // issuer, warp 2 = TMEM allocator, all four warps = epilogue (warp w reads
 // TMEM lanes 32w .. 32w + 31).  Every mbarrier wait is bounded; a timeout sets
 // the error word and the CTA skips its stores, frees TMEM and exits.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "zda_nn_internal.h"
 #include "zda_nn_tc.cuh"
@@ -34,167 +38,300 @@ static __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Bounded wait that also gives up when another role has aborted.
+static __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, int limit, volatile int *abort,
+                                                     int *err, int code)
+{
+    for (int it = 0; it < limit; ++it) {
+        if (mb_try(bar, parity)) return true;
+        if ((it & 63) == 63 && *abort) return false;
+    }
+    *abort = 1;
+    if (err) atomicCAS(err, 0, code);
+    return false;
+}
+
+// Epilogue of one 16-channel chunk (channels cc .. cc + 15) of one position.
+__device__ __forceinline__ void epilogue_chunk(const ConvParams &p, float *v, int cc, int pos, bool valid, bool inner,
+                                               const float *bias)
+{
+    if (p.epi == EPI_F32 || p.epi == EPI_GRAD_F32) {
+        if (!valid || cc >= p.out_ld) return;
+        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(p.out0) + (size_t)pos * p.out_ld + cc);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = inner ? v[i] + bias[i] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        return;
+    }
+    const int half = cc >= p.out_ld ? 1 : 0;
+    const int c = cc - half * p.out_ld;           // channel within the output tensor
+    if (p.epi == EPI_RELU_BF16) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = inner ? fmaxf(v[i] + bias[i], 0.f) : 0.f;
+    } else {   // EPI_GRAD_BF16
+        const uint16_t *mk = half ? p.mask1 : p.mask0;
+        if (mk && inner) {
+            const uint4 m0 = __ldg(reinterpret_cast<const uint4 *>(mk + ((size_t)(c / 8) * p.rows + LEAD + pos) * 8));
+            const uint4 m1 = __ldg(reinterpret_cast<const uint4 *>(mk + ((size_t)(c / 8 + 1) * p.rows + LEAD + pos) * 8));
+            const uint16_t *h0 = reinterpret_cast<const uint16_t *>(&m0);
+            const uint16_t *h1 = reinterpret_cast<const uint16_t *>(&m1);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (!bf16_pos(h0[i])) v[i] = 0.f;
+                if (!bf16_pos(h1[i])) v[8 + i] = 0.f;
+            }
+        }
+        if (!inner) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        }
+    }
+    uint16_t *ob = static_cast<uint16_t *>(half ? p.out1 : p.out0);
+    *reinterpret_cast<uint4 *>(ob + ((size_t)(c / 8) * p.rows + LEAD + pos) * 8) =
+        make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    *reinterpret_cast<uint4 *>(ob + ((size_t)(c / 8 + 1) * p.rows + LEAD + pos) * 8) =
+        make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
+}
+
+// The MMAs of one tap for the tile's M tiles: NKS K-steps of 16 channels each.
+template <int NKS, int MT>
+__device__ __forceinline__ void issue_tap(uint32_t d0, uint32_t dn, uint64_t a0, uint32_t a_ks, uint64_t b0, uint32_t b_ks,
+                                          uint32_t idesc, uint32_t acc0)
+{
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+        const uint64_t am = a0 + (uint64_t)(m * 128);            // 128 rows x 16 B
+        const uint32_t dm = d0 + m * dn;
+        tc_mma(dm, am, b0, idesc, acc0);
+#pragma unroll
+        for (int ks = 1; ks < NKS; ++ks) tc_mma(dm, am + (uint64_t)(ks * a_ks), b0 + (uint64_t)(ks * b_ks), idesc, 1u);
+    }
+}
+
+// All MMAs of one input group of one tile with resident weights, fully
+// unrolled over taps, M tiles and K steps.  abase: descriptor of the
+// window at row `halo` (a tap adds its row offset: one 16-byte unit per
+// row); bbase: descriptor of the first resident weight block.
+template <int TAPS, int NKS>
+__device__ __forceinline__ void issue_group(uint32_t d0, uint32_t dn, uint64_t abase, int Wp, uint64_t bbase,
+                                            uint32_t wunits, uint32_t a_ks, uint32_t b_ks, uint32_t idesc, int g)
+{
+#pragma unroll
+    for (int tap = 0; tap < TAPS; ++tap) {
+        const int off = TAPS == 9 ? (tap / 3 - 1) * Wp + (tap % 3 - 1) : 0;
+        const uint64_t a0 = abase + (uint64_t)(int64_t)off;
+        const uint64_t b0 = bbase + (uint64_t)((g * TAPS + tap) * wunits);
+        issue_tap<NKS, 2>(d0, dn, a0, a_ks, b0, b_ks, idesc, (g | tap) != 0);
+    }
+}
+
+__device__ __forceinline__ void mb_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent, warp-specialised convolution.  Warp 0 (one lane) streams, per
+// tile and input group, the TMA window into one of two window stages; the
+// weight blocks are either loaded once per CTA (resident: every layer whose
+// weights fit beside the two windows) or streamed per tap through a ring
+// (the concatenating layers); warp 1 (one lane) issues the MMAs
+// into one of two TMEM accumulators (2 x mt x N columns); warps 2..9 drain
+// the other accumulator (warp w reads lane quarter w mod 4, column half
+// (w - 2) / 4) while the next tile's MMAs run.
 __global__ void __launch_bounds__(CONV_THREADS, 1)
-    k_conv_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1, const ConvParams p)
+    k_conv_tc(const ConvParams p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t raw = su32(smem), base = (raw + 1023u) & ~1023u;   // TMA destinations: 1024-aligned window
-    const uint32_t a_bytes = (uint32_t)(p.cg / 8) * p.plane;
+    const uint32_t raw = su32(smem), base = (raw + 1023u) & ~1023u;   // TMA destinations: 1024-aligned
+    const uint32_t win_bytes = (uint32_t)(p.cg / 8) * p.plane;
     const uint32_t wslot = (uint32_t)p.N * p.cg * 2;
-    const uint32_t sA = base, sW = base + a_bytes;
-    const uint32_t sBar = sW + p.slots * wslot;             // 8-byte barriers
-    const uint32_t barA_full = sBar, barA_free = sBar + 8, bar_done = sBar + 16;
-    const uint32_t barW_full = sBar + 24, barW_empty = barW_full + 8 * p.slots;
-    const uint32_t sTmem = barW_empty + 8 * p.slots;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + (sTmem - raw));
+    const uint32_t sWin = base, sW = base + 2 * win_bytes;
+    const int wblocks = p.resident ? p.ngroups * p.taps : p.slots;
+    const uint32_t sBar = sW + wblocks * wslot;
+    const uint32_t winFull = sBar, winEmpty = sBar + 16, accFull = sBar + 32, accEmpty = sBar + 48;
+    const uint32_t wFull = sBar + 64, wEmpty = wFull + 8 * p.slots;
+    const uint32_t sMisc = wEmpty + 8 * p.slots;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + (sMisc - raw));
+    volatile int *abort = reinterpret_cast<volatile int *>(smem + (sMisc + 4 - raw));
 
-    const int p0 = blockIdx.x * p.mt * 128;
+    const int tile_pos = p.mt * 128;
+    const int ntiles = (p.P + tile_pos - 1) / tile_pos;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t acc_cols = (uint32_t)(p.mt * p.N);
 
     if (threadIdx.x == 0) {
-        mb_init(barA_full, 1);
-        mb_init(barA_free, 1);
-        mb_init(bar_done, 1);
-        for (int s = 0; s < p.slots; ++s) {
-            mb_init(barW_full + 8 * s, 1);
-            mb_init(barW_empty + 8 * s, 1);
+        for (int s = 0; s < 2; ++s) {
+            mb_init(winFull + 8 * s, 1);
+            mb_init(winEmpty + 8 * s, 1);
+            mb_init(accFull + 8 * s, 1);
+            mb_init(accEmpty + 8 * s, 8);          // one arrival per epilogue warp
         }
+        for (int s = 0; s < p.slots; ++s) {
+            mb_init(wFull + 8 * s, 1);
+            mb_init(wEmpty + 8 * s, 1);
+        }
+        *abort = 0;
         mb_fence_init();
     }
-    if (warp == 2) tm_alloc(sTmem, p.ncols);
+    if (warp == 1) tm_alloc(sMisc, p.ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- producer
-        int it = 0;
-        for (int g = 0; g < p.ngroups; ++g) {
-            if (g > 0 && !mb_wait(barA_free, (g - 1) & 1, p.wait_limit, p.err, 11)) break;
-            const CUtensorMap *tm = g == 0 ? &tm0 : &tm1;
-            mb_expect_tx(barA_full, a_bytes);
-            for (int c8 = 0; c8 < p.cg / 8; ++c8)
-                for (int k = 0; k < p.npiece; ++k)
-                    tma_load_2d(sA + c8 * p.plane + k * p.br * 16, tm, c8 * 8, p0 - p.halo + k * p.br, barA_full);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer
+            int u = 0, it = 0;
             bool ok = true;
-            for (int t = 0; t < p.taps; ++t, ++it) {
-                const int s = it % p.slots, u = it / p.slots;
-                if (u > 0 && !mb_wait(barW_empty + 8 * s, (u - 1) & 1, p.wait_limit, p.err, 12)) {
-                    ok = false;
-                    break;
+            if (p.resident && my_tiles > 0) {
+                mb_expect_tx(wFull, (uint32_t)(p.ngroups * p.taps) * wslot);
+                for (int blk = 0; blk < p.ngroups * p.taps; ++blk)
+                    bulk_load(sW + blk * wslot, p.wimg + (size_t)blk * p.N * p.cg, wslot, wFull);
+            }
+            for (int t = 0; t < my_tiles && ok; ++t) {
+                const int p0 = ((int)blockIdx.x + t * (int)gridDim.x) * tile_pos;
+                for (int g = 0; g < p.ngroups && ok; ++g, ++u) {
+                    const int s = u & 1, k = u >> 1;
+                    if (k > 0 && !wait_or_abort(winEmpty + 8 * s, (k - 1) & 1, p.wait_limit, abort, p.err, 11)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint16_t *src = g == 0 ? p.in0 : p.in1;
+                    const uint32_t dst = sWin + s * win_bytes;
+                    mb_expect_tx(winFull + 8 * s, (uint32_t)(p.cg / 8) * p.R * 16);
+                    for (int c8 = 0; c8 < p.cg / 8; ++c8)
+                        bulk_load(dst + c8 * p.plane, src + ((size_t)c8 * p.rows + LEAD + p0 - p.halo) * 8,
+                                  (uint32_t)p.R * 16, winFull + 8 * s);
+                    for (int tap = 0; tap < p.taps && !p.resident; ++tap, ++it) {
+                        const int sl = it % p.slots, kk = it / p.slots;
+                        if (kk > 0 && !wait_or_abort(wEmpty + 8 * sl, (kk - 1) & 1, p.wait_limit, abort, p.err, 12)) {
+                            ok = false;
+                            break;
+                        }
+                        mb_expect_tx(wFull + 8 * sl, wslot);
+                        bulk_load(sW + sl * wslot, p.wimg + (size_t)(g * p.taps + tap) * p.N * p.cg, wslot,
+                                  wFull + 8 * sl);
+                    }
                 }
-                mb_expect_tx(barW_full + 8 * s, wslot);
-                bulk_load(sW + s * wslot, p.wimg + (size_t)(g * p.taps + t) * p.N * p.cg, wslot, barW_full + 8 * s);
             }
-            if (!ok) break;
         }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
-        const uint32_t idesc = idesc_bf16(128, p.N, 0, 0);
-        int it = 0;
-        bool ok = true;
-        for (int g = 0; g < p.ngroups && ok; ++g) {
-            if (!mb_wait(barA_full, g & 1, p.wait_limit, p.err, 13)) {
-                ok = false;
-                break;
-            }
-            for (int t = 0; t < p.taps; ++t, ++it) {
-                const int s = it % p.slots, u = it / p.slots;
-                if (!mb_wait(barW_full + 8 * s, u & 1, p.wait_limit, p.err, 14)) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            const uint32_t idesc = idesc_bf16(128, p.N, 0, 0);
+            const uint32_t a_ks = (2 * (uint32_t)p.plane) >> 4, b_ks = ((uint32_t)p.N * 32) >> 4;
+            const int taps = p.taps, Wp = p.Wp, halo = p.halo, nks = p.cg / 16, N = p.N, ngroups = p.ngroups;
+            const uint32_t plane = (uint32_t)p.plane;
+            const bool resident = p.resident != 0;
+            int u = 0, it = 0;
+            bool ok = true;
+            if (p.resident && my_tiles > 0) ok = wait_or_abort(wFull, 0, p.wait_limit, abort, p.err, 17);
+            for (int t = 0; t < my_tiles && ok; ++t) {
+                const int b = t & 1, kb = t >> 1;
+                if (kb > 0 && !wait_or_abort(accEmpty + 8 * b, (kb - 1) & 1, p.wait_limit, abort, p.err, 13)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const int off = p.taps == 9 ? (t / 3 - 1) * p.Wp + (t % 3 - 1) : 0;
-                for (int m = 0; m < p.mt; ++m) {
-                    const uint32_t row0 = (uint32_t)(p.halo + off + m * 128);
-                    for (int ks = 0; ks < p.cg / 16; ++ks) {
-                        const uint64_t ad = sdesc(sA + 2 * ks * p.plane + row0 * 16, p.plane, 128);
-                        const uint64_t bd = sdesc(sW + s * wslot + ks * p.N * 32, 128, 256);
-                        tc_mma(tmem + m * p.N, ad, bd, idesc, (g | t | ks) != 0);
+                for (int g = 0; g < ngroups && ok; ++g, ++u) {
+                    const int s = u & 1, k = u >> 1;
+                    if (!wait_or_abort(winFull + 8 * s, k & 1, p.wait_limit, abort, p.err, 14)) {
+                        ok = false;
+                        break;
                     }
+                    const uint32_t win = sWin + s * win_bytes;
+                    if (resident) {
+                        tc_fence_after();
+                        const uint64_t abase = sdesc(win + (uint32_t)halo * 16, plane, 128);
+                        const uint64_t bbase = sdesc(sW, 128, 256);
+                        const uint32_t d0 = tmem + b * acc_cols, wunits = wslot >> 4;
+                        const int kind = taps * 8 + nks;
+                        if (kind == 9 * 8 + 4) issue_group<9, 4>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
+                        else if (kind == 9 * 8 + 2) issue_group<9, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
+                        else if (kind == 9 * 8 + 1) issue_group<9, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
+                        else if (kind == 1 * 8 + 4) issue_group<1, 4>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
+                        else if (kind == 1 * 8 + 2) issue_group<1, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
+                        else issue_group<1, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
+                        it += taps;
+                    } else {
+                    for (int tap = 0; tap < taps; ++tap, ++it) {
+                        const int sl = it % p.slots, kk = it / p.slots;
+                        if (!wait_or_abort(wFull + 8 * sl, kk & 1, p.wait_limit, abort, p.err, 15)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t wblk = sW + sl * wslot;
+                        const int off = taps == 9 ? (tap / 3 - 1) * Wp + (tap % 3 - 1) : 0;
+                        // descriptors advance by plain adds: the start-address field is the low
+                        // 14 bits in 16-byte units and every address stays below 256 KB
+                        const uint64_t a0 = sdesc(win + (uint32_t)(halo + off) * 16, plane, 128);
+                        const uint64_t b0 = sdesc(wblk, 128, 256);
+                        const uint32_t acc0 = (g | tap) != 0;
+                        const uint32_t d0 = tmem + b * acc_cols;
+                        if (nks == 4) issue_tap<4, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
+                        else if (nks == 2) issue_tap<2, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
+                        else issue_tap<1, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
+                        tc_commit(wEmpty + 8 * sl);
+                    }
+                    }
+                    if (ok) tc_commit(winEmpty + 8 * s);
                 }
-                tc_commit(barW_empty + 8 * s);
+                if (ok) tc_commit(accFull + 8 * b);
             }
-            if (ok) tc_commit(barA_free);
         }
-        if (ok) tc_commit(bar_done);
+    } else {
+        // ---------------- epilogue (warps 2..9)
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int HW = p.Hp * p.Wp, nchunk = p.N / 16;
+        // this warp's chunks: c16 = h, h + 2, h + 4, h + 6 (those < nchunk); biases in registers
+        float bias_r[2][16];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int c = (h + 2 * j) * 16 + i;
+                bias_r[j][i] = (p.bias && c < p.nbias) ? __ldg(p.bias + c) : 0.f;
+            }
+        for (int t = 0; t < my_tiles; ++t) {
+            const int b = t & 1, kb = t >> 1;
+            bool ok = true;
+            if (lane == 0) ok = wait_or_abort(accFull + 8 * b, kb & 1, p.wait_limit, abort, p.err, 16);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            const int p0 = ((int)blockIdx.x + t * (int)gridDim.x) * tile_pos;
+            for (int m = 0; m < p.mt; ++m) {
+                const int pos = p0 + m * 128 + q * 32 + lane;
+                const bool valid = pos < p.P;             // rows up to the tile end exist (zeroed past P)
+                const int rem = pos % HW, y = rem / p.Wp, x = rem % p.Wp;
+                const bool inner = valid && y > 0 && y < p.Hp - 1 && x > 0 && x < p.Wp - 1;
+                const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols + m * p.N;
+                for (int c16 = h; c16 < nchunk; c16 += 4) {
+                    float va[16], vb[16];
+                    const bool two = c16 + 2 < nchunk;
+                    if (two) tm_ld16x2(trow + c16 * 16, trow + (c16 + 2) * 16, va, vb);
+                    else tm_ld16(trow + c16 * 16, va);
+                    epilogue_chunk(p, va, c16 * 16, pos, valid, inner, bias_r[0]);   // biases only when N <= 64
+                    if (two) epilogue_chunk(p, vb, (c16 + 2) * 16, pos, valid, inner, bias_r[1]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mb_arrive(accEmpty + 8 * b);
+        }
     }
     __syncwarp();
-
-    // ---------------- epilogue
-    const bool done = mb_wait(bar_done, 0, p.wait_limit, p.err, 15);
-    tc_fence_after();
-    const int HW = p.Hp * p.Wp;
-    for (int m = 0; m < p.mt; ++m) {
-        const int pos = p0 + m * 128 + warp * 32 + lane;
-        const bool valid = done && pos < p.P;
-        const int rem = pos % HW, y = rem / p.Wp, x = rem % p.Wp;
-        const bool inner = y > 0 && y < p.Hp - 1 && x > 0 && x < p.Wp - 1;
-        for (int c16 = 0; c16 < p.N / 16; ++c16) {
-            float v[16];
-            tm_ld16(tmem + ((uint32_t)(warp * 32) << 16) + m * p.N + c16 * 16, v);
-            if (!valid) continue;
-            const int cc = c16 * 16;
-            if (p.epi == EPI_RELU_BF16 || p.epi == EPI_F32) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    float t = v[i] + ((p.bias && cc + i < p.nbias) ? __ldg(p.bias + cc + i) : 0.f);
-                    if (p.epi == EPI_RELU_BF16) t = fmaxf(t, 0.f);
-                    v[i] = inner ? t : 0.f;
-                }
-                if (p.epi == EPI_RELU_BF16) {
-                    uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(p.out0) + (size_t)pos * p.out_ld + cc);
-                    o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                                      pack_bf16(v[6], v[7]));
-                    o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
-                                      pack_bf16(v[14], v[15]));
-                } else {
-                    float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(p.out0) + (size_t)pos * p.out_ld + cc);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                }
-            } else if (p.epi == EPI_GRAD_BF16) {
-                const int half = cc >= p.out_ld ? 1 : 0;
-                const int c = cc - half * p.out_ld;
-                const uint16_t *mk = half ? p.mask1 : p.mask0;
-                if (mk) {
-                    const uint4 *mp = reinterpret_cast<const uint4 *>(mk + (size_t)pos * p.out_ld + c);
-                    uint4 q[2] = {__ldg(mp), __ldg(mp + 1)};
-                    const uint16_t *h = reinterpret_cast<const uint16_t *>(q);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (!bf16_pos(h[i])) v[i] = 0.f;
-                }
-                if (!inner) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
-                }
-                uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(half ? p.out1 : p.out0) +
-                                                     (size_t)pos * p.out_ld + c);
-                o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                                  pack_bf16(v[6], v[7]));
-                o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
-                                  pack_bf16(v[14], v[15]));
-            } else {   // EPI_GRAD_F32
-                if (cc >= p.out_ld) continue;
-                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(p.out0) + (size_t)pos * p.out_ld + cc);
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    o[i] = inner ? make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3])
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 2) tm_dealloc(tmem, p.ncols);
+    if (warp == 1) tm_dealloc(tmem, p.ncols);
 }
 
-__global__ void __launch_bounds__(CONV_THREADS, 1)
-    k_wgrad_tc(const __grid_constant__ CUtensorMap tx0, const __grid_constant__ CUtensorMap tx1,
-               const __grid_constant__ CUtensorMap tdy, const WgradParams p)
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    k_wgrad_tc(const WgradParams p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -239,11 +376,14 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 const int off = p.taps == 9 ? (t / 3 - 1) * p.Wp + (t % 3 - 1) : 0;
                 for (int c = 0; c < p.cin_planes; ++c) {
                     const bool second = p.two_inputs && c >= 8;
-                    tma_load_2d(sa + (j * p.cin_planes + c) * planeb, second ? &tx1 : &tx0, (second ? c - 8 : c) * 8,
-                                y + off, barF + 8 * s);
+                    const uint16_t *x = second ? p.x1 : p.x0;
+                    const int cc = second ? c - 8 : c;
+                    bulk_load(sa + (j * p.cin_planes + c) * planeb, x + ((size_t)cc * p.rows + LEAD + y + off) * 8, planeb,
+                              barF + 8 * s);
                 }
             }
-            for (int c = 0; c < p.N / 8; ++c) tma_load_2d(sb + c * planeb, &tdy, c * 8, y, barF + 8 * s);
+            for (int c = 0; c < p.N / 8; ++c)
+                bulk_load(sb + c * planeb, p.dy + ((size_t)c * p.rows + LEAD + y) * 8, planeb, barF + 8 * s);
         }
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = idesc_bf16(128, p.N, 1, 1);
@@ -256,11 +396,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t sa = base + s * stage, sb = sa + a_bytes;
-            for (int ks = 0; ks < p.kt / 16; ++ks) {
-                const uint64_t ad = sdesc(sa + ks * 256, 128, planeb);
-                const uint64_t bd = sdesc(sb + ks * 256, 128, planeb);
-                tc_mma(tmem, ad, bd, idesc, (i | ks) != 0);
-            }
+            const uint64_t ad = sdesc(sa, 128, planeb), bd = sdesc(sb, 128, planeb);
+            tc_mma(tmem, ad, bd, idesc, i != 0);
+#pragma unroll 8
+            for (int ks = 1; ks < p.kt / 16; ++ks)            // 16 rows x 16 B = 16 units per step
+                tc_mma(tmem, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc, 1u);
             tc_commit(barE + 8 * s);
         }
         if (ok && ntile > 0) tc_commit(bar_done);
@@ -288,7 +428,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
 
 size_t conv_smem_bytes(const ConvParams &p)
 {
-    return (size_t)(p.cg / 8) * p.plane + (size_t)p.slots * p.N * p.cg * 2 + 24 + 16 * p.slots + 16 + 1024;
+    const size_t wblocks = p.resident ? (size_t)p.ngroups * p.taps : (size_t)p.slots;
+    return 2 * (size_t)(p.cg / 8) * p.plane + wblocks * p.N * p.cg * 2 + 64 + 16 * p.slots + 8 + 1024;
 }
 
 size_t wgrad_smem_bytes(const WgradParams &p)
@@ -306,25 +447,32 @@ static size_t smem_for_tmem(size_t smem, uint32_t ncols)
     return smem < need ? need : smem;
 }
 
-cudaError_t launch_conv(const CUtensorMap &tm0, const CUtensorMap &tm1, const ConvParams &p, cudaStream_t s)
+cudaError_t launch_conv(const ConvParams &p, cudaStream_t s)
 {
-    size_t smem = smem_for_tmem(conv_smem_bytes(p), p.ncols);
+    const size_t smem = smem_for_tmem(conv_smem_bytes(p), p.ncols);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = (p.P + p.mt * 128 - 1) / (p.mt * 128);
-    k_conv_tc<<<grid, CONV_THREADS, smem, s>>>(tm0, tm1, p);
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc, CONV_THREADS, smem)) != cudaSuccess)
+        return e;
+    per_sm = std::max(1, std::min(per_sm, (int)(512 / p.ncols)));
+    if (p.mt != 2) return cudaErrorInvalidValue;     // the MMA issue loop is unrolled for two M tiles
+    const int ntiles = (p.P + p.mt * 128 - 1) / (p.mt * 128);
+    const int grid = std::max(1, std::min(ntiles, sms * per_sm));
+    k_conv_tc<<<grid, CONV_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_wgrad(const CUtensorMap &tx0, const CUtensorMap &tx1, const CUtensorMap &tdy, const WgradParams &p,
-                         int splits, cudaStream_t s)
+cudaError_t launch_wgrad(const WgradParams &p, int splits, cudaStream_t s)
 {
     size_t smem = smem_for_tmem(wgrad_smem_bytes(p), p.N < 32 ? 32 : p.N);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_wgrad_tc<<<dim3(p.ngroups, splits), CONV_THREADS, smem, s>>>(tx0, tx1, tdy, p);
+    k_wgrad_tc<<<dim3(p.ngroups, splits), WG_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 

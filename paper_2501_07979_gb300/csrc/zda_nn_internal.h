@@ -1,6 +1,5 @@
 // Internal declarations of the surrogate network (libzda, sm_103a).
 #pragma once
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -14,30 +13,41 @@ enum Epilogue {
     EPI_GRAD_F32 = 3     // -> f32 (gradient of the network input)
 };
 
-// Implicit-GEMM 3x3 (or 1x1) convolution on zero-bordered ("padded") NHWC
-// activations: output position p, tap t reads input position p + off(t),
-// off = (dy - 1) Wp + (dx - 1), so every tap's A operand is the same shared
-// memory window seen from another start row.
+// Activation layout ("planar"): a tensor of C channels (a multiple of 8)
+// over the zero-bordered positions of one level (n samples x (H + 2) x
+// (W + 2)) is stored as C / 8 planes of `rows` rows of 8 channels (16 B);
+// position p lives at row LEAD + p.  The rows before LEAD and after the
+// last 256-position tile are zero, so every convolution window is one
+// contiguous run of rows per plane (a single bulk copy).
+constexpr int LEAD = 256;
+
+// Implicit-GEMM 3x3 (or 1x1) convolution: output position p, tap t reads
+// input position p + off(t), off = (dy - 1) Wp + (dx - 1), so every tap's A
+// operand is the same shared-memory window seen from another start row.
 struct ConvParams {
-    int P;                 // positions (rows) of the activation arrays: n Hp Wp
+    int P;                 // positions of the level: n Hp Wp
     int Hp, Wp;            // padded image size
     int taps;              // 9 or 1
-    int halo;              // window rows before the CTA's first position
-    int br, npiece;        // TMA box rows, boxes per channel-chunk plane
-    int plane;             // bytes per 8-channel plane of the window (npiece br 16)
+    int halo;              // window rows before the tile's first position (Wp + 1, or 0)
+    int R;                 // window rows: mt 128 + 2 halo
+    int plane;             // bytes per 8-channel plane of the window in shared memory (>= R 16)
+    long rows;             // rows per plane of the input / output tensors
     int cg;                // input channels per group (16, 32 or 64)
     int ngroups;           // 1, or 2 when the input is the concatenation of two tensors
     int N;                 // GEMM N = output channels (16 .. 128)
-    int mt;                // 128-row M tiles per CTA (one window)
-    int slots;             // weight ring slots
+    int mt;                // 128-row M tiles per tile (one window)
+    int slots;             // weight ring slots (streamed weights)
+    int resident;          // 1: all weight blocks loaded once per CTA (no ring)
     uint32_t ncols;        // TMEM columns allocated
+    const uint16_t *in0, *in1;   // planar inputs of group 0 / 1 (cg channels each)
     const uint16_t *wimg;  // weight images [ngroups][taps][N cg] (bf16, operand layout)
     const float *bias;     // [nbias] or null (channels >= nbias get no bias)
     int nbias;
     int epi;
-    void *out0, *out1;     // outputs [P][out_ld]; out1 receives channels >= out_ld when N = 2 out_ld
+    void *out0, *out1;     // bf16 planar outputs of out_ld channels (out1: channels >= out_ld when
+                           // N = 2 out_ld), or f32 [P][out_ld] (EPI_F32, EPI_GRAD_F32)
     int out_ld;
-    const uint16_t *mask0, *mask1;   // gradient masks (post-activation tensors, [P][out_ld]) or null
+    const uint16_t *mask0, *mask1;   // gradient masks: planar post-activation tensors (out_ld channels) or null
     int *err;
     int wait_limit;
 };
@@ -55,20 +65,22 @@ struct WgradParams {
     int kt;                // positions per stage (128)
     int ntiles;            // ceil(P / kt)
     int tiles_per_cta;
+    long rows;             // rows per plane of x0, x1 and dy
+    const uint16_t *x0, *x1, *dy;   // planar input(s) and output gradient
     float *partial;        // [splits][ngroups][128][N]
     int *err;
     int wait_limit;
 };
 
-constexpr int CONV_THREADS = 128;
+constexpr int CONV_THREADS = 320;   // persistent convolution: producer, MMA and 8 epilogue warps
+constexpr int WG_THREADS = 128;
 constexpr int WG_KT = 128;
 constexpr int WG_STAGES = 2;
 
 size_t conv_smem_bytes(const ConvParams &p);
 size_t wgrad_smem_bytes(const WgradParams &p);
-cudaError_t launch_conv(const CUtensorMap &tm0, const CUtensorMap &tm1, const ConvParams &p, cudaStream_t s);
-cudaError_t launch_wgrad(const CUtensorMap &tx0, const CUtensorMap &tx1, const CUtensorMap &tdy, const WgradParams &p,
-                         int splits, cudaStream_t s);
+cudaError_t launch_conv(const ConvParams &p, cudaStream_t s);
+cudaError_t launch_wgrad(const WgradParams &p, int splits, cudaStream_t s);
 
 }  // namespace nn
 }  // namespace zda

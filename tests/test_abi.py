@@ -95,6 +95,8 @@ def test_surrogate_descriptor_checks_and_sizes_need_no_gpu(libpath):
     assert L.zda_nn_create(0, ctypes.byref(bad), ctypes.byref(h)) == _lib.ERR_ARG
     bad = _lib.NnDesc(batch=2, height=16, width=16, in_ch=17, out_ch=24)
     assert L.zda_nn_create(0, ctypes.byref(bad), ctypes.byref(h)) == _lib.ERR_ARG
+    bad = _lib.NnDesc(batch=2, height=16, width=184, in_ch=1, out_ch=24)      # window would not fit
+    assert L.zda_nn_create(0, ctypes.byref(bad), ctypes.byref(h)) == _lib.ERR_ARG
     d = _lib.NnDesc(batch=4, height=32, width=24, in_ch=2, out_ch=24)
     assert L.zda_nn_create(0, ctypes.byref(d), ctypes.byref(h)) == _lib.OK
     n = ctypes.c_size_t()
