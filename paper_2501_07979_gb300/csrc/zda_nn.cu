@@ -459,9 +459,10 @@ zda_status conv(zda_nn *net, int lv, int n, int taps, const uint16_t *in0, const
     // weights resident if they fit beside the two window stages, else a ring
     // of as many per-tap slots as fit (at most 8)
     const size_t budget = 220 * 1024;
-    const size_t win2 = 2 * (size_t)(cg / 8) * p.plane, wslot = (size_t)N * cg * 2;
+    const size_t upl = std::min(cg / 8, 4);                    // window planes per unit (32 channels)
+    const size_t win2 = 2 * upl * p.plane, wslot = (size_t)N * cg * 2, uslot = (size_t)N * upl * 16;
     p.resident = win2 + (size_t)p.ngroups * taps * wslot <= budget ? 1 : 0;
-    p.slots = p.resident ? 1 : (int)std::max<size_t>(2, std::min<size_t>(8, (budget - win2) / wslot));
+    p.slots = p.resident ? 1 : (int)std::max<size_t>(2, std::min<size_t>(8, (budget - win2) / uslot));
     uint32_t nc = 32;
     while (nc < (uint32_t)(2 * p.mt * N)) nc <<= 1;   // two accumulators (double buffering)
     p.ncols = nc;

@@ -109,20 +109,21 @@ __device__ __forceinline__ void issue_tap(uint32_t d0, uint32_t dn, uint64_t a0,
     }
 }
 
-// All MMAs of one input group of one tile with resident weights, fully
-// unrolled over taps, M tiles and K steps.  abase: descriptor of the
-// window at row `halo` (a tap adds its row offset: one 16-byte unit per
-// row); bbase: descriptor of the first resident weight block.
+// All MMAs of one unit (up to 32 input channels) of one tile with resident
+// weights, fully unrolled over taps, M tiles and K steps.  abase: descriptor
+// of the window at row `halo` (a tap adds its row offset: one 16-byte unit
+// per row); bbase: descriptor of the unit's half of the first weight block
+// of its group.
 template <int TAPS, int NKS>
-__device__ __forceinline__ void issue_group(uint32_t d0, uint32_t dn, uint64_t abase, int Wp, uint64_t bbase,
-                                            uint32_t wunits, uint32_t a_ks, uint32_t b_ks, uint32_t idesc, int g)
+__device__ __forceinline__ void issue_unit(uint32_t d0, uint32_t dn, uint64_t abase, int Wp, uint64_t bbase,
+                                           uint32_t wunits, uint32_t a_ks, uint32_t b_ks, uint32_t idesc, int uu)
 {
 #pragma unroll
     for (int tap = 0; tap < TAPS; ++tap) {
         const int off = TAPS == 9 ? (tap / 3 - 1) * Wp + (tap % 3 - 1) : 0;
         const uint64_t a0 = abase + (uint64_t)(int64_t)off;
-        const uint64_t b0 = bbase + (uint64_t)((g * TAPS + tap) * wunits);
-        issue_tap<NKS, 2>(d0, dn, a0, a_ks, b0, b_ks, idesc, (g | tap) != 0);
+        const uint64_t b0 = bbase + (uint64_t)(tap * wunits);
+        issue_tap<NKS, 2>(d0, dn, a0, a_ks, b0, b_ks, idesc, (uu | tap) != 0);
     }
 }
 
@@ -145,11 +146,13 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     extern __shared__ __align__(1024) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw = su32(smem), base = (raw + 1023u) & ~1023u;   // TMA destinations: 1024-aligned
-    const uint32_t win_bytes = (uint32_t)(p.cg / 8) * p.plane;
-    const uint32_t wslot = (uint32_t)p.N * p.cg * 2;
+    // a unit = up to 4 planes (32 channels) of one input group; window stages hold one unit
+    const int upl = p.cg / 8 < 4 ? p.cg / 8 : 4, uh = (p.cg / 8) / upl, nunits = p.ngroups * uh;
+    const uint32_t win_bytes = (uint32_t)upl * p.plane;
+    const uint32_t wslot = (uint32_t)p.N * p.cg * 2;              // one (group, tap) weight block
+    const uint32_t uslot = (uint32_t)p.N * upl * 16;              // its share for one unit (streamed ring)
     const uint32_t sWin = base, sW = base + 2 * win_bytes;
-    const int wblocks = p.resident ? p.ngroups * p.taps : p.slots;
-    const uint32_t sBar = sW + wblocks * wslot;
+    const uint32_t sBar = sW + (p.resident ? p.ngroups * p.taps * wslot : p.slots * uslot);
     const uint32_t winFull = sBar, winEmpty = sBar + 16, accFull = sBar + 32, accEmpty = sBar + 48;
     const uint32_t wFull = sBar + 64, wEmpty = wFull + 8 * p.slots;
     const uint32_t sMisc = wEmpty + 8 * p.slots;
@@ -193,7 +196,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             }
             for (int t = 0; t < my_tiles && ok; ++t) {
                 const int p0 = ((int)blockIdx.x + t * (int)gridDim.x) * tile_pos;
-                for (int g = 0; g < p.ngroups && ok; ++g, ++u) {
+                for (int uu = 0; uu < nunits && ok; ++uu, ++u) {
+                    const int g = uu / uh, hf = uu % uh;
                     const int s = u & 1, k = u >> 1;
                     if (k > 0 && !wait_or_abort(winEmpty + 8 * s, (k - 1) & 1, p.wait_limit, abort, p.err, 11)) {
                         ok = false;
@@ -201,9 +205,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     }
                     const uint16_t *src = g == 0 ? p.in0 : p.in1;
                     const uint32_t dst = sWin + s * win_bytes;
-                    mb_expect_tx(winFull + 8 * s, (uint32_t)(p.cg / 8) * p.R * 16);
-                    for (int c8 = 0; c8 < p.cg / 8; ++c8)
-                        bulk_load(dst + c8 * p.plane, src + ((size_t)c8 * p.rows + LEAD + p0 - p.halo) * 8,
+                    mb_expect_tx(winFull + 8 * s, (uint32_t)upl * p.R * 16);
+                    for (int j = 0; j < upl; ++j)
+                        bulk_load(dst + j * p.plane, src + ((size_t)(hf * upl + j) * p.rows + LEAD + p0 - p.halo) * 8,
                                   (uint32_t)p.R * 16, winFull + 8 * s);
                     for (int tap = 0; tap < p.taps && !p.resident; ++tap, ++it) {
                         const int sl = it % p.slots, kk = it / p.slots;
@@ -211,8 +215,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                             ok = false;
                             break;
                         }
-                        mb_expect_tx(wFull + 8 * sl, wslot);
-                        bulk_load(sW + sl * wslot, p.wimg + (size_t)(g * p.taps + tap) * p.N * p.cg, wslot,
+                        mb_expect_tx(wFull + 8 * sl, uslot);
+                        bulk_load(sW + sl * uslot,
+                                  p.wimg + (size_t)(g * p.taps + tap) * p.N * p.cg + (size_t)hf * p.N * upl * 8, uslot,
                                   wFull + 8 * sl);
                     }
                 }
@@ -223,12 +228,12 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             // ---------------- MMA issuer
             const uint32_t idesc = idesc_bf16(128, p.N, 0, 0);
             const uint32_t a_ks = (2 * (uint32_t)p.plane) >> 4, b_ks = ((uint32_t)p.N * 32) >> 4;
-            const int taps = p.taps, Wp = p.Wp, halo = p.halo, nks = p.cg / 16, N = p.N, ngroups = p.ngroups;
+            const int taps = p.taps, Wp = p.Wp, halo = p.halo, nks = upl / 2, N = p.N;
             const uint32_t plane = (uint32_t)p.plane;
             const bool resident = p.resident != 0;
             int u = 0, it = 0;
             bool ok = true;
-            if (p.resident && my_tiles > 0) ok = wait_or_abort(wFull, 0, p.wait_limit, abort, p.err, 17);
+            if (resident && my_tiles > 0) ok = wait_or_abort(wFull, 0, p.wait_limit, abort, p.err, 17);
             for (int t = 0; t < my_tiles && ok; ++t) {
                 const int b = t & 1, kb = t >> 1;
                 if (kb > 0 && !wait_or_abort(accEmpty + 8 * b, (kb - 1) & 1, p.wait_limit, abort, p.err, 13)) {
@@ -236,7 +241,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                for (int g = 0; g < ngroups && ok; ++g, ++u) {
+                const uint32_t d0 = tmem + b * acc_cols;
+                for (int uu = 0; uu < nunits && ok; ++uu, ++u) {
+                    const int g = uu / uh, hf = uu % uh;
                     const int s = u & 1, k = u >> 1;
                     if (!wait_or_abort(winFull + 8 * s, k & 1, p.wait_limit, abort, p.err, 14)) {
                         ok = false;
@@ -245,38 +252,33 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     const uint32_t win = sWin + s * win_bytes;
                     if (resident) {
                         tc_fence_after();
-                        const uint64_t abase = sdesc(win + (uint32_t)halo * 16, plane, 128);
-                        const uint64_t bbase = sdesc(sW, 128, 256);
-                        const uint32_t d0 = tmem + b * acc_cols, wunits = wslot >> 4;
-                        const int kind = taps * 8 + nks;
-                        if (kind == 9 * 8 + 4) issue_group<9, 4>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
-                        else if (kind == 9 * 8 + 2) issue_group<9, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
-                        else if (kind == 9 * 8 + 1) issue_group<9, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
-                        else if (kind == 1 * 8 + 4) issue_group<1, 4>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
-                        else if (kind == 1 * 8 + 2) issue_group<1, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
-                        else issue_group<1, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, g);
-                        it += taps;
-                    } else {
-                    for (int tap = 0; tap < taps; ++tap, ++it) {
-                        const int sl = it % p.slots, kk = it / p.slots;
-                        if (!wait_or_abort(wFull + 8 * sl, kk & 1, p.wait_limit, abort, p.err, 15)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t wblk = sW + sl * wslot;
-                        const int off = taps == 9 ? (tap / 3 - 1) * Wp + (tap % 3 - 1) : 0;
                         // descriptors advance by plain adds: the start-address field is the low
                         // 14 bits in 16-byte units and every address stays below 256 KB
-                        const uint64_t a0 = sdesc(win + (uint32_t)(halo + off) * 16, plane, 128);
-                        const uint64_t b0 = sdesc(wblk, 128, 256);
-                        const uint32_t acc0 = (g | tap) != 0;
-                        const uint32_t d0 = tmem + b * acc_cols;
-                        if (nks == 4) issue_tap<4, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
-                        else if (nks == 2) issue_tap<2, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
-                        else issue_tap<1, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
-                        tc_commit(wEmpty + 8 * sl);
-                    }
+                        const uint64_t abase = sdesc(win + (uint32_t)halo * 16, plane, 128);
+                        const uint64_t bbase = sdesc(sW + (uint32_t)(g * taps) * wslot, 128, 256) +
+                                               (uint64_t)(hf * nks * b_ks);
+                        const uint32_t wunits = wslot >> 4;
+                        const int kind = taps * 8 + nks;
+                        if (kind == 9 * 8 + 2) issue_unit<9, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                        else if (kind == 9 * 8 + 1) issue_unit<9, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                        else if (kind == 1 * 8 + 2) issue_unit<1, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                        else issue_unit<1, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                    } else {
+                        for (int tap = 0; tap < taps; ++tap, ++it) {
+                            const int sl = it % p.slots, kk = it / p.slots;
+                            if (!wait_or_abort(wFull + 8 * sl, kk & 1, p.wait_limit, abort, p.err, 15)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const int off = taps == 9 ? (tap / 3 - 1) * Wp + (tap % 3 - 1) : 0;
+                            const uint64_t a0 = sdesc(win + (uint32_t)(halo + off) * 16, plane, 128);
+                            const uint64_t b0 = sdesc(sW + sl * uslot, 128, 256);
+                            const uint32_t acc0 = (uu | tap) != 0;
+                            if (nks == 2) issue_tap<2, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
+                            else issue_tap<1, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
+                            tc_commit(wEmpty + 8 * sl);
+                        }
                     }
                     if (ok) tc_commit(winEmpty + 8 * s);
                 }
@@ -428,8 +430,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
 
 size_t conv_smem_bytes(const ConvParams &p)
 {
-    const size_t wblocks = p.resident ? (size_t)p.ngroups * p.taps : (size_t)p.slots;
-    return 2 * (size_t)(p.cg / 8) * p.plane + wblocks * p.N * p.cg * 2 + 64 + 16 * p.slots + 8 + 1024;
+    const size_t upl = p.cg / 8 < 4 ? p.cg / 8 : 4;
+    const size_t wbytes = p.resident ? (size_t)p.ngroups * p.taps * p.N * p.cg * 2 : (size_t)p.slots * p.N * upl * 16;
+    return 2 * upl * p.plane + wbytes + 64 + 16 * p.slots + 8 + 1024;
 }
 
 size_t wgrad_smem_bytes(const WgradParams &p)
