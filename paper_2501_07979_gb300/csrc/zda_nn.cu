@@ -75,18 +75,6 @@ __global__ void k_pack_input(const float *x, int n, int H, int W, int ic, long P
     *reinterpret_cast<uint4 *>(out + pofs(rows, c8, pos)) = *reinterpret_cast<uint4 *>(r);
 }
 
-// padded f32 [P][ld] (channels < nc) -> [n][H][W][nc] f32
-__global__ void k_unpack_f32(const float *in, int ld, int n, int H, int W, int nc, float *out)
-{
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long)n * H * W * nc) return;
-    const int c = (int)(i % nc);
-    const long pix = i / nc;
-    const int x = (int)(pix % W), y = (int)((pix / W) % H);
-    const long s = pix / ((long)H * W);
-    out[i] = in[((s * (H + 2) + y + 1) * (W + 2) + x + 1) * ld + c];
-}
-
 // [n][H][W][nc] f32 -> planar bf16, 32 channels (4 planes), positions < Pt (zeros elsewhere)
 __global__ void k_pack_grad(const float *dy, int n, int H, int W, int nc, long Pt, long rows, uint16_t *out)
 {
@@ -372,7 +360,7 @@ struct zda_nn {
     uint8_t *ws = nullptr;
     size_t ws_bytes = 0, need = 0;
     struct Off {
-        size_t params, grads, m, v, img, x16, yh, gy, gx, wpart, bpart, mpart, err;
+        size_t params, grads, m, v, img, x16, gy, wpart, bpart, mpart, err;
         size_t act[LEV][8];   // per level: enc_a, enc_b, in (pooled input), up, dec_a, dec_b, (level 3: bot_a, bot_b)
         size_t g[LEV][4];     // per level: gA, gB, gU, gS
     } o{};
@@ -609,9 +597,7 @@ zda_status zda_nn_create(int device, const zda_nn_desc *d, zda_nn **out)
     net->o.v = take(net->nparam * 4);
     net->o.img = take(net->img_elems * 2);
     net->o.x16 = take((size_t)net->rows[0] * 16 * 2);
-    net->o.yh = take((size_t)pos_count(net, 0, B) * 32 * 4);
     net->o.gy = take((size_t)net->rows[0] * 32 * 2);
-    net->o.gx = take((size_t)pos_count(net, 0, B) * 16 * 4);
     for (int l = 0; l < LEV; ++l) {
         const size_t t = (size_t)net->rows[l] * C * 2;
         for (int k = 0; k < 6; ++k) net->o.act[l][k] = take(t);
@@ -767,11 +753,8 @@ zda_status zda_nn_forward(zda_nn *net, const float *x, int n, float *y, void *st
                  Aw(net, l, A_DECB), nullptr, C, nullptr, nullptr, s, lf(net, li + 1, n)));
         below = A(net, l, A_DECB);
     }
-    float *yh = at<float>(net, net->o.yh);
-    TRY(conv(net, 0, n, 1, below, nullptr, C, 32, Wf(net, 14), Bias(net, 14), net->d.out_ch, EPI_F32, yh, nullptr, 32, nullptr,
-             nullptr, s, lf(net, 14, n)));
-    k_unpack_f32<<<nblocks((long)n * H * W * net->d.out_ch), 256, 0, s>>>(yh, 32, n, H, W, net->d.out_ch, y);
-    net->launches++;
+    TRY(conv(net, 0, n, 1, below, nullptr, C, 32, Wf(net, 14), Bias(net, 14), net->d.out_ch, EPI_F32, y, nullptr,
+             net->d.out_ch, nullptr, nullptr, s, lf(net, 14, n)));
     NN_CUDA(cudaGetLastError());
     net->n_fwd = n;
     return ZDA_OK;
@@ -829,11 +812,8 @@ zda_status zda_nn_backward(zda_nn *net, const float *dy, float *dx, void *stream
             TRY(conv(net, l, n, 9, Gb(net, l, G_A), nullptr, C, C, Wd(net, 2 * l), nullptr, 0, EPI_GRAD_BF16,
                      Gb(net, l, G_U), nullptr, C, nullptr, nullptr, s));
         else if (dx) {
-            float *gx = at<float>(net, net->o.gx);
-            TRY(conv(net, 0, n, 9, Gb(net, 0, G_A), nullptr, C, 16, Wd(net, 0), nullptr, 0, EPI_GRAD_F32, gx, nullptr, 16,
-                     nullptr, nullptr, s));
-            k_unpack_f32<<<nblocks((long)n * H * W * net->d.in_ch), 256, 0, s>>>(gx, 16, n, H, W, net->d.in_ch, dx);
-            net->launches++;
+            TRY(conv(net, 0, n, 9, Gb(net, 0, G_A), nullptr, C, 16, Wd(net, 0), nullptr, 0, EPI_GRAD_F32, dx, nullptr,
+                     net->d.in_ch, nullptr, nullptr, s));
         }
     }
     NN_CUDA(cudaGetLastError());

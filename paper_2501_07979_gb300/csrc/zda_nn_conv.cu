@@ -56,12 +56,24 @@ __device__ __forceinline__ void epilogue_chunk(const ConvParams &p, float *v, in
                                                const float *bias)
 {
     if (p.epi == EPI_F32 || p.epi == EPI_GRAD_F32) {
-        if (!valid || cc >= p.out_ld) return;
-        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(p.out0) + (size_t)pos * p.out_ld + cc);
+        // straight into the caller's [n][H][W][out_ld] tensor (interior positions only)
+        if (!inner || cc >= p.out_ld) return;
+        const int HW = p.Hp * p.Wp, rem = pos % HW, y = rem / p.Wp, x = rem % p.Wp;
+        const size_t pix = ((size_t)(pos / HW) * (p.Hp - 2) + (y - 1)) * (p.Wp - 2) + (x - 1);
+        float *o = static_cast<float *>(p.out0) + pix * p.out_ld + cc;
+        const int nc = p.out_ld - cc < 16 ? p.out_ld - cc : 16;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = inner ? v[i] + bias[i] : 0.f;
+        for (int i = 0; i < 16; ++i) v[i] += bias[i];
+        if ((p.out_ld & 3) == 0) {
+            float4 *o4 = reinterpret_cast<float4 *>(o);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            for (int i = 0; i < 4; ++i)
+                if (4 * i < nc) o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (i < nc) o[i] = v[i];
+        }
         return;
     }
     const int half = cc >= p.out_ld ? 1 : 0;

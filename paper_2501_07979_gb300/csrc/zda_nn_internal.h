@@ -45,7 +45,8 @@ struct ConvParams {
     int nbias;
     int epi;
     void *out0, *out1;     // bf16 planar outputs of out_ld channels (out1: channels >= out_ld when
-                           // N = 2 out_ld), or f32 [P][out_ld] (EPI_F32, EPI_GRAD_F32)
+                           // N = 2 out_ld), or the caller's f32 tensor [n][H][W][out_ld]
+                           // (EPI_F32, EPI_GRAD_F32: interior positions only)
     int out_ld;
     const uint16_t *mask0, *mask1;   // gradient masks: planar post-activation tensors (out_ld channels) or null
     int *err;
