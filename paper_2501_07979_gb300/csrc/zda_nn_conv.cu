@@ -16,9 +16,9 @@
 //               reduction over positions; M = 128 rows hold 128 / c_in taps'
 //               shifted copies of the input, each copied pre-shifted.
 //
-// Roles (128 threads): warp 0 lane 0 = producer (TMA), warp 1 lane 0 = MMA
-// issuer, warp 2 = TMEM allocator, all four warps = epilogue (warp w reads
-// TMEM lanes 32w .. 32w + 31).  Every mbarrier wait is bounded; a timeout sets
+// Roles of k_conv_tc (352 threads): warp 0 lane 0 = producer, warps 1 and 10
+// lane 0 = MMA issuers (M tile 0 / 1 of each tile, warp 1 also allocates
+// TMEM), warps 2..9 = epilogue (warp w reads TMEM lanes 32 (w mod 4) ..).  Every mbarrier wait is bounded; a timeout sets
 // the error word and the CTA skips its stores, frees TMEM and exits.
 #include <cuda_bf16.h>
 
@@ -106,19 +106,16 @@ __device__ __forceinline__ void epilogue_chunk(const ConvParams &p, float *v, in
         make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
 }
 
-// The MMAs of one tap for the tile's M tiles: NKS K-steps of 16 channels each.
-template <int NKS, int MT>
-__device__ __forceinline__ void issue_tap(uint32_t d0, uint32_t dn, uint64_t a0, uint32_t a_ks, uint64_t b0, uint32_t b_ks,
-                                          uint32_t idesc, uint32_t acc0)
+// The MMAs of one tap for M tile m0 of the tile: NKS K-steps of 16 channels each.
+template <int NKS>
+__device__ __forceinline__ void issue_tap(uint32_t d0, uint32_t dn, int m0, uint64_t a0, uint32_t a_ks, uint64_t b0,
+                                          uint32_t b_ks, uint32_t idesc, uint32_t acc0)
 {
+    const uint64_t am = a0 + (uint64_t)(m0 * 128);            // 128 rows x 16 B
+    const uint32_t dm = d0 + m0 * dn;
+    tc_mma(dm, am, b0, idesc, acc0);
 #pragma unroll
-    for (int m = 0; m < MT; ++m) {
-        const uint64_t am = a0 + (uint64_t)(m * 128);            // 128 rows x 16 B
-        const uint32_t dm = d0 + m * dn;
-        tc_mma(dm, am, b0, idesc, acc0);
-#pragma unroll
-        for (int ks = 1; ks < NKS; ++ks) tc_mma(dm, am + (uint64_t)(ks * a_ks), b0 + (uint64_t)(ks * b_ks), idesc, 1u);
-    }
+    for (int ks = 1; ks < NKS; ++ks) tc_mma(dm, am + (uint64_t)(ks * a_ks), b0 + (uint64_t)(ks * b_ks), idesc, 1u);
 }
 
 // All MMAs of one unit (up to 32 input channels) of one tile with resident
@@ -127,7 +124,7 @@ __device__ __forceinline__ void issue_tap(uint32_t d0, uint32_t dn, uint64_t a0,
 // per row); bbase: descriptor of the unit's half of the first weight block
 // of its group.
 template <int TAPS, int NKS>
-__device__ __forceinline__ void issue_unit(uint32_t d0, uint32_t dn, uint64_t abase, int Wp, uint64_t bbase,
+__device__ __forceinline__ void issue_unit(uint32_t d0, uint32_t dn, int m0, uint64_t abase, int Wp, uint64_t bbase,
                                            uint32_t wunits, uint32_t a_ks, uint32_t b_ks, uint32_t idesc, int uu)
 {
 #pragma unroll
@@ -135,7 +132,7 @@ __device__ __forceinline__ void issue_unit(uint32_t d0, uint32_t dn, uint64_t ab
         const int off = TAPS == 9 ? (tap / 3 - 1) * Wp + (tap % 3 - 1) : 0;
         const uint64_t a0 = abase + (uint64_t)(int64_t)off;
         const uint64_t b0 = bbase + (uint64_t)(tap * wunits);
-        issue_tap<NKS, 2>(d0, dn, a0, a_ks, b0, b_ks, idesc, (uu | tap) != 0);
+        issue_tap<NKS>(d0, dn, m0, a0, a_ks, b0, b_ks, idesc, (uu | tap) != 0);
     }
 }
 
@@ -179,13 +176,13 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
             mb_init(winFull + 8 * s, 1);
-            mb_init(winEmpty + 8 * s, 1);
-            mb_init(accFull + 8 * s, 1);
+            mb_init(winEmpty + 8 * s, 2);          // one commit per MMA warp
+            mb_init(accFull + 8 * s, 2);
             mb_init(accEmpty + 8 * s, 8);          // one arrival per epilogue warp
         }
         for (int s = 0; s < p.slots; ++s) {
             mb_init(wFull + 8 * s, 1);
-            mb_init(wEmpty + 8 * s, 1);
+            mb_init(wEmpty + 8 * s, 2);
         }
         *abort = 0;
         mb_fence_init();
@@ -235,9 +232,10 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 }
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 || warp == 10) {
         if (lane == 0) {
-            // ---------------- MMA issuer
+            // ---------------- MMA issuers: warp 1 issues M tile 0, warp 10 M tile 1 (separate accumulators)
+            const int m0 = warp == 1 ? 0 : 1;
             const uint32_t idesc = idesc_bf16(128, p.N, 0, 0);
             const uint32_t a_ks = (2 * (uint32_t)p.plane) >> 4, b_ks = ((uint32_t)p.N * 32) >> 4;
             const int taps = p.taps, Wp = p.Wp, halo = p.halo, nks = upl / 2, N = p.N;
@@ -271,10 +269,10 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                                                (uint64_t)(hf * nks * b_ks);
                         const uint32_t wunits = wslot >> 4;
                         const int kind = taps * 8 + nks;
-                        if (kind == 9 * 8 + 2) issue_unit<9, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
-                        else if (kind == 9 * 8 + 1) issue_unit<9, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
-                        else if (kind == 1 * 8 + 2) issue_unit<1, 2>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
-                        else issue_unit<1, 1>(d0, N, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                        if (kind == 9 * 8 + 2) issue_unit<9, 2>(d0, N, m0, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                        else if (kind == 9 * 8 + 1) issue_unit<9, 1>(d0, N, m0, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                        else if (kind == 1 * 8 + 2) issue_unit<1, 2>(d0, N, m0, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
+                        else issue_unit<1, 1>(d0, N, m0, abase, Wp, bbase, wunits, a_ks, b_ks, idesc, uu);
                     } else {
                         for (int tap = 0; tap < taps; ++tap, ++it) {
                             const int sl = it % p.slots, kk = it / p.slots;
@@ -287,8 +285,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                             const uint64_t a0 = sdesc(win + (uint32_t)(halo + off) * 16, plane, 128);
                             const uint64_t b0 = sdesc(sW + sl * uslot, 128, 256);
                             const uint32_t acc0 = (uu | tap) != 0;
-                            if (nks == 2) issue_tap<2, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
-                            else issue_tap<1, 2>(d0, N, a0, a_ks, b0, b_ks, idesc, acc0);
+                            if (nks == 2) issue_tap<2>(d0, N, m0, a0, a_ks, b0, b_ks, idesc, acc0);
+                            else issue_tap<1>(d0, N, m0, a0, a_ks, b0, b_ks, idesc, acc0);
                             tc_commit(wEmpty + 8 * sl);
                         }
                     }

@@ -73,7 +73,7 @@ struct WgradParams {
     int wait_limit;
 };
 
-constexpr int CONV_THREADS = 320;   // persistent convolution: producer, MMA and 8 epilogue warps
+constexpr int CONV_THREADS = 352;   // persistent convolution: producer, 2 MMA and 8 epilogue warps
 constexpr int WG_THREADS = 128;
 constexpr int WG_KT = 128;
 constexpr int WG_STAGES = 2;
