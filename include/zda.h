@@ -234,13 +234,15 @@ zda_status zda_zone_time_steps(zda_zone *zone, int steps, double *ms_out_host, v
 zda_status zda_zone_set_wait_limit(zda_zone *zone, int polls, int inject_timeout);
 
 /* Kernel timing with CUDA events recorded on the launching stream: with
- * every > 0, every every-th time step's main launches are bracketed by
- * events (a ring of 64 samples; the host waits for a sample 64 samples old
+ * every > 0, the main launches of steps every - 1, 2 every - 1, ... are
+ * bracketed by events (a ring of 64 samples; the host waits for a sample 64 samples old
  * before reusing its slot).  every = 0 turns it off.
  * zda_zone_timing waits for pending samples and writes ms3_host[0..2], the
  * summed durations (ms) of the step's launches 1, 2, 3 over the sampled
  * steps, and the number of sampled steps, then resets.  Launches 1, 2, 3 are:
- * split step with two z-cells per thread: H update, E update, DFT update;
+ * split step with two z-cells per thread: H update, E update (which also
+ * writes the DFT history), DFT flush (only on steps 31, 63, ...: sample
+ * with every = 32 to time it);
  * split step with one z-cell per thread: H update, E update (with the DFTs), -;
  * fused step: streaming E/H kernel, -, DFT kernel ("-" reads 0). */
 zda_status zda_zone_set_timing(zda_zone *zone, int every);

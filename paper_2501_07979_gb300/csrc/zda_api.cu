@@ -39,6 +39,8 @@ void zda_internal_set_error(const char *msg) { g_err = msg ? msg : ""; }
             return fail(ZDA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));     \
     } while (0)
 
+static_assert(ZDA_DFT_MAXQ == ZDA_MAX_FREQ, "the blocked DFT keeps one accumulator per signed frequency");
+
 struct zda_ctx {
     int device;
 };
@@ -47,7 +49,7 @@ namespace {
 
 struct Layout {           // byte offsets inside the workspace
     size_t fields, psi_z, psi_r, fields2, psi_h2, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
-        norm, src_rad, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
+        norm, src_rad, dft_hist, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
         ph_h, pulse, twiddle, adj_time, Gr, Gp, emph_n, emph_h, wt, beta_r, beta_p, g_in, partial, S,
         umean, pt_row, qr, qw, qp, qwp, kk, status, total;
 };
@@ -208,6 +210,8 @@ static void compute_layout(zda_zone &z)
     L.g_rho = take((size_t)z.nrd * np * sizeof(float));
     L.norm = take((size_t)z.nrd * sizeof(float));
     L.src_rad = take(2 * nr * sizeof(float2));
+    // history of the time-blocked DFT: design (3 components) + monitor (2) sites per slot
+    L.dft_hist = take((size_t)zda::DFT_BLOCK * (3 * plane * z.nk + 2 * plane) * sizeof(float2));
     L.inv_r_n = take((nr + 1) * sizeof(float));
     L.inv_r_h = take(nr * sizeof(float));
     L.br_n = take((nr + 1) * sizeof(float));
@@ -530,6 +534,7 @@ static zda::StepParams step_params(zda_zone &z)
     p.beta_r = P<float2>(z, z.L.beta_r);
     p.beta_p = P<float2>(z, z.L.beta_p);
     p.src_rad = P<float2>(z, z.L.src_rad);
+    p.dft_hist = P<float2>(z, z.L.dft_hist);
     p.nq = z.nq;
     p.src_scale = (float)(0.5 / d.dz);
     p.des_k0 = d.design_k0;
@@ -642,7 +647,7 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
         zda::FusedParams f[2] = {fused_params(z, p, 0), fused_params(z, p, 1)};
         // timed samples: [stream kernel] between events 0 and 1, [DFT kernel] between 1 and 2
         for (int n = 0; n < z.d.n_steps; ++n) {
-            const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
+            const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == z.time_every - 1;
             int slot = 0;
             const zda::FusedParams &fp = f[n & 1];
             cudaError_t e = zda::launch_fused_pre(fp, n, s);
@@ -673,8 +678,10 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
     z.last_parity = 0;
     const bool pair = z.pair_kernels && zda::pair_kernels_apply(p);
     const bool dft = pair && (p.des || p.mon);
+    p.dft_ne = zda::dft_entries(p);
+    if (!pair) p.dft_hist = nullptr;
     for (int n = 0; n < z.d.n_steps; ++n) {
-        const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == 0;
+        const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == z.time_every - 1;
         int slot = 0;
         if (pair && p.src_mode == zda::SRC_ADJOINT) zda::launch_adjoint_source_rad(p, n, s);
         if (timed) {
@@ -689,13 +696,16 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
         if (pair) zda::launch_update_e_pair(p, n, s);
         else zda::launch_update_e(p, n, s);
         if (timed) CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 2], s));
-        if (dft) zda::launch_dft_sites(p, n, s);
+        if (dft && zda::dft_flush_due(p, n, z.d.n_steps)) {
+            zda::launch_dft_flush(p, n, s);
+            ++z.launches;
+        }
         if (timed) {
             CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 3], s));
             z.ev_pending[slot] = 1;
         }
     }
-    if (pair) z.launches += (long long)z.d.n_steps * ((dft ? 1 : 0) + (p.src_mode == zda::SRC_ADJOINT ? 1 : 0));
+    if (pair) z.launches += (long long)z.d.n_steps * (p.src_mode == zda::SRC_ADJOINT ? 1 : 0);
     z.launches += 2LL * z.d.n_steps;
     CUDA_TRY(cudaGetLastError());
     return ZDA_OK;

@@ -84,6 +84,8 @@ struct StepParams {
     float src_scale;                           // 1/(2 dz) for the plane wave
     const float2 *beta_r, *beta_p;             // adjoint radial profiles [Q][n_r]
     float2 *src_rad;                           // adjoint source of the current step [2][n_r]
+    float2 *dft_hist;                          // DFT_BLOCK slots of E at the DFT sites (time-blocked DFT)
+    size_t dft_ne;                             // entries per slot
     int nq;
     int mon_k;                                 // < 0: no monitor DFT
     float2 *mon;
@@ -98,7 +100,12 @@ void launch_update_e(const StepParams &p, int n, cudaStream_t s);
 bool pair_kernels_apply(const StepParams &p);
 void launch_update_h_pair(const StepParams &p, cudaStream_t s);
 void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s);   // no DFT: see launch_dft_sites
-void launch_dft_sites(const StepParams &p, int n, cudaStream_t s);
+// Time-blocked running DFT of the split step (two z-cells per thread).
+constexpr int DFT_BLOCK = 32;
+#define ZDA_DFT_MAXQ 16
+size_t dft_entries(const StepParams &p);
+bool dft_flush_due(const StepParams &p, int n, int n_steps);
+void launch_dft_flush(const StepParams &p, int n, cudaStream_t s);
 void launch_adjoint_source_rad(const StepParams &p, int n, cudaStream_t s);
 
 struct FilterParams {

@@ -243,36 +243,104 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
     if (kz >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
     if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
 
+    // history slot of the time-blocked DFT (entries as in dft_site)
+    if (p.dft_hist && (p.des || p.mon)) {
+        const size_t plane = (size_t)nr * nphi, ndes = p.des ? plane * p.des_nk : 0;
+        float2 *hs = p.dft_hist + (size_t)(n % DFT_BLOCK) * p.dft_ne;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int dk = k + u - p.des_k0;
+            if (p.des && dk >= 0 && dk < p.des_nk) {
+                const size_t t = ij * p.des_nk + dk;
+                hs[t] = *ER[u];
+                hs[ndes + t] = *EP[u];
+                hs[2 * ndes + t] = *EZ[u];
+            }
+            if (p.mon && k + u == p.mon_k) {
+                hs[3 * ndes + ij] = *ER[u];
+                hs[3 * ndes + plane + ij] = *EP[u];
+            }
+        }
+    }
 }
 
-// Running DFTs of E^{n+1} after the E update: one thread per site (design
-// volume: 3 components; monitor plane: E_r, E_phi), accumulators updated in
-// chunks (dft_update).  A separate launch keeps the E update lean: with the
-// DFT inside, the blocks holding design planes ran long and the extra
-// registers halved the E update's occupancy.
-__global__ void k_dft_sites(const StepParams p, const int n)
+// Running DFTs of E^{n+1}, blocked over time.  Each step the E update writes
+// E at the DFT sites (design volume: 3 components x n_r n_phi design_nk;
+// monitor plane: E_r, E_phi x n_r n_phi) into slot n mod DFT_BLOCK of a
+// history buffer; every DFT_BLOCK steps (and after the last step)
+// k_dft_flush adds sum_l E_l e^{i w_q (n0 + l) dt} dt to each accumulator,
+// which it reads and writes once per block instead of once per step.
+// Entry e: design e = c ndes + (ij nk + kk) (c < 3), then monitor
+// 3 ndes + c plane + ij (c < 2).
+// One thread per DFT site (design: 3 components, monitor: E_r, E_phi); the
+// block's twiddles for the flushed steps sit in shared memory; frequencies
+// in chunks of 8.
+__global__ void k_dft_flush(const StepParams p, int nslots, int n0)
 {
-    const int nz = p.nz, nphi = p.nphi, nr = p.nr;
-    const size_t plane = (size_t)nr * nphi;
-    const size_t sj = (size_t)nz, si = (size_t)nphi * nz;
-    const float2 *tw = p.t.twiddle + (size_t)n * p.nq;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t ndes = p.des ? plane * p.des_nk : 0;
-    if (t < ndes) {
-        const int kk = (int)(t % p.des_nk);
-        const size_t ij = t / p.des_nk;
-        const size_t c = (ij / nphi) * si + (ij % nphi) * sj + p.des_k0 + kk;
-        const float2 e3[3] = {__ldg(p.f.Er + c), __ldg(p.f.Ep + c), __ldg(p.f.Ez + c)};
-        const size_t comp = plane * p.des_nk;
-        dft_update<3>(p.des + t, 3 * comp, comp, tw, p.nq, e3);
-        return;
+    __shared__ float2 tws[DFT_BLOCK * ZDA_DFT_MAXQ];
+    const int nq = p.nq;
+    for (int i = threadIdx.x; i < nslots * nq; i += blockDim.x) tws[i] = p.t.twiddle[(size_t)n0 * nq + i];
+    __syncthreads();
+    const size_t plane = (size_t)p.nr * p.nphi, ndes = p.des ? plane * p.des_nk : 0;
+    const size_t nsites = ndes + (p.mon ? plane : 0), ne = p.dft_ne;
+    const size_t site = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= nsites) return;
+    const bool des = site < ndes;
+    const int ncomp = des ? 3 : 2;
+    const size_t u = des ? site : site - ndes;
+    const size_t e0 = des ? site : 3 * ndes + u, estride = des ? ndes : plane;   // history entries
+    float2 *d = des ? p.des + site : p.mon + u;
+    const size_t cstride = des ? ndes : plane, qstride = des ? 3 * ndes : 2 * plane;
+    for (int q0 = 0; q0 < nq; q0 += 8) {
+        float2 acc[3][8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[c][q] = make_float2(0.f, 0.f);
+        for (int l = 0; l < nslots; ++l) {
+            const float2 *h = p.dft_hist + (size_t)l * ne + e0;
+            float2 x[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = c < ncomp ? h[c * estride] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q0 + q >= nq) break;
+                const float2 w = tws[l * nq + q0 + q];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c][q] = c_fma(x[c], w, acc[c][q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q0 + q >= nq) break;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (c >= ncomp) break;
+                float2 *dd = d + (size_t)(q0 + q) * qstride + c * cstride;
+                const float2 v = *dd;
+                *dd = make_float2(v.x + acc[c][q].x, v.y + acc[c][q].y);
+            }
+        }
     }
-    const size_t u = t - ndes;
-    if (p.mon && u < plane) {
-        const size_t c = (u / nphi) * si + (u % nphi) * sj + p.mon_k;
-        const float2 e2[2] = {__ldg(p.f.Er + c), __ldg(p.f.Ep + c)};
-        dft_update<2>(p.mon + u, 2 * plane, plane, tw, p.nq, e2);
-    }
+}
+
+size_t dft_entries(const StepParams &p)
+{
+    const size_t plane = (size_t)p.nr * p.nphi;
+    return (p.des ? 3 * plane * p.des_nk : 0) + (p.mon ? 2 * plane : 0);
+}
+
+bool dft_flush_due(const StepParams &p, int n, int n_steps)
+{
+    return dft_entries(p) > 0 && ((n % DFT_BLOCK) == DFT_BLOCK - 1 || n == n_steps - 1);
+}
+
+void launch_dft_flush(const StepParams &p, int n, cudaStream_t s)
+{
+    const size_t plane = (size_t)p.nr * p.nphi;
+    const size_t nsites = (p.des ? plane * p.des_nk : 0) + (p.mon ? plane : 0);
+    const int nslots = n % DFT_BLOCK + 1;
+    k_dft_flush<<<(unsigned)((nsites + 255) / 256), 256, 0, s>>>(p, nslots, n - (nslots - 1));
 }
 
 // Adjoint source of step n per radius: sum_q beta_q(r) k_q(t_{n+1/2}) for the
@@ -289,13 +357,6 @@ __global__ void k_adjoint_source_rad(const StepParams p, const int n)
     }
     p.src_rad[i] = sr;
     p.src_rad[p.nr + i] = sp;
-}
-
-void launch_dft_sites(const StepParams &p, int n, cudaStream_t s)
-{
-    if (!p.des && !p.mon) return;
-    const size_t nsite = (p.des ? (size_t)p.nr * p.nphi * p.des_nk : 0) + (p.mon ? (size_t)p.nr * p.nphi : 0);
-    k_dft_sites<<<(unsigned)((nsite + 255) / 256), 256, 0, s>>>(p, n);
 }
 
 void launch_adjoint_source_rad(const StepParams &p, int n, cudaStream_t s)
