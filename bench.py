@@ -39,8 +39,9 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
-    ap.add_argument("--workload", default="zone", choices=["zone", "surrogate"],
+    ap.add_argument("--workload", default="zone", choices=["zone", "lwir", "surrogate"],
                     help="zone: forward + adjoint FDTD iteration of the wide zone (headline); "
+                         "lwir: the same on zone 16 of the paper's LWIR lens at its lambda/50 grid; "
                          "surrogate: U-Net inference, 128 x 128 patches, batch 256")
     ap.add_argument("--batch", type=int, default=256, help="surrogate workload: samples per forward")
     ap.add_argument("--kernel", default="default", choices=["default", "split", "split1", "fused2", "fused4"],
@@ -48,12 +49,23 @@ def parse():
     return ap.parse_args()
 
 
+WORKLOAD = "zone"
+
+
 def workload(n_steps):
-    from zda_inputs import zone_cfg2
-    return zone_cfg2(n_steps=n_steps)
+    from zda_inputs import zone_cfg2, zone_lwir
+    return zone_lwir(16, n_steps) if WORKLOAD == "lwir" else zone_cfg2(n_steps=n_steps)
 
 
 def config(spec, n_steps):
+    if WORKLOAD == "lwir":
+        return {"workload": "LWIR zone 16 of the paper's lens: r=[375,400] lambda, n=11520, lambda/50 grid, "
+                            "%dx%dx%d cells, Si n=3.42, 1 wavelength, forward+adjoint TopOpt iteration"
+                            % (spec.n_r, spec.n_phi, spec.n_z),
+                "n_steps_per_run": n_steps, "cells": spec.cells, "runs_per_step": 2,
+                "design_pixels": spec.n_r_design * spec.n_phi,
+                "l2": "no flush: the 75 MB field state fits in the 129 MB L2, and the time loop keeps it there as "
+                      "the real workload does; the HBM roofline fraction is not meaningful for this zone"}
     return {"workload": "wide zone r=[200,215], n=4000, 300x320x160 cells, 3 wavelengths, "
                         "forward+adjoint TopOpt iteration",
             "n_steps_per_run": n_steps, "cells": spec.cells, "runs_per_step": 2,
@@ -504,7 +516,9 @@ def run_nn(a):
 
 
 def main():
+    global WORKLOAD
     a = parse()
+    WORKLOAD = a.workload
     if a.workload == "surrogate":
         if a.impl == "reference":
             run_nn_reference(a)

@@ -106,6 +106,28 @@ def zone_cfg2(n_steps: int = 20000) -> ZoneSpec:
         focal=300.0, label="cfg2 wide zone 300x320x160, n=4000, 3 wavelengths")
 
 
+def zone_lwir(ell: int = 16, n_steps: int = 4000) -> ZoneSpec:
+    """Zone l (2..16) of the paper's LWIR lens at its own discretisation
+    (section "Centimeter-scale metalens at long-wave infrared"): 25 lambda
+    wide, r in [25 (l - 1), 25 l], fold n = 720 l, dr = dz = lambda / 50,
+    r dphi < 0.021 lambda (11 phi cells), silicon (n = 3.42) substrate and
+    0.6 lambda design layer, NA 0.3 focus of the 800-lambda lens.  A
+    throughput workload: the z stack (0.64 lambda of substrate below the
+    layer, the monitor 0.5 lambda above it, 8-cell CPMLs) is this build's
+    choice."""
+    eps_si = 3.42 ** 2
+    n_phi = int(np.ceil(25.0 * ell * 2 * np.pi / (720 * ell) / 0.021))
+    return ZoneSpec(
+        r_lo=25.0 * (ell - 1) - 8 * 0.02, n_r=1250 + 16, n_phi=n_phi, n_z=112, n_fold=720 * ell,
+        dr=0.02, dz=0.02, pml_r_in=8, pml_r_out=8, pml_z=8,
+        layer_k0=(0, 40, 70), layer_eps=(eps_si, 1.0, 1.0),
+        design_k0=40, design_k1=70, eps_lo=1.0, eps_hi=eps_si,
+        source_k=20, monitor_k=95, courant=0.5, n_steps=n_steps,
+        filter_radius=0.08, beta=8.0, eta=0.5, wavelengths=(1.0,),
+        pulse_sigma=0.5, pulse_t0=2.0, focal=focal_from_na(400.0, 0.3),
+        label="LWIR zone %d: 25 lambda, lambda/50, n = %d" % (ell, 720 * ell))
+
+
 def zone_tiny(**kw) -> ZoneSpec:
     """A small zone for oracle pins and quick parity cases (defaults: 24 r-cells
     with 4-cell PMLs, 8 phi cells, 40 z-cells, coarse lambda/10 grid)."""
