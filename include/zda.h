@@ -302,6 +302,14 @@ long long zda_lens_launch_count(const zda_lens *lens);   /* graph launches (or d
 zda_status zda_lens_focal_plane(zda_lens *lens, const double *pts_dev, int n_pts, int n_phi_samples,
                                 double *field_dev, double *p_trans_host, void *stream);
 
+/* The same field at points off the focal plane (the far-field maps of
+ * "Results and Discussion", e.g. the xz-plane intensity): pts_dev holds
+ * n_pts (x, y, h) doubles, h = height above the focal plane (the
+ * propagation distance from each monitor plane becomes its focal distance
+ * + h).  field_dev as for zda_lens_focal_plane.  Synchronises `stream`. */
+zda_status zda_lens_field_points(zda_lens *lens, const double *pts_dev, int n_pts, int n_phi_samples,
+                                 double *field_dev, void *stream);
+
 /* Thread-local message of the last error ("" if none). */
 const char *zda_last_error(void);
 

@@ -624,7 +624,8 @@ def focal_plane_bruteforce(spec, geom, mon, pts):
     qp[geom.i_d0] *= 0.5
     qp[geom.i_d1] *= 0.5
     qp = qp[:s.n_r]
-    pts = np.asarray(pts, dtype=np.float64).reshape(-1, 2)
+    pts = np.asarray(pts, dtype=np.float64)
+    pts = np.concatenate([pts, np.zeros((len(pts), 1))], axis=1) if pts.shape[-1] == 2 else pts.reshape(-1, 3)
     if geom.bor:
         ncopy, dphi, nphi = 1, 2 * math.pi / 256, 256
     else:
@@ -663,9 +664,10 @@ def focal_plane_bruteforce(spec, geom, mon, pts):
             X = r[:, None] * cs
             Y = r[:, None] * sn
             wt = (w * r)[:, None] * dphi
-            for p, (x, y) in enumerate(pts):
-                R = np.sqrt(zf * zf + (x - X) ** 2 + (y - Y) ** 2)
-                K = (1 / (2 * math.pi)) * (zf / R) * (1 / R - 1j * kk) * np.exp(1j * kk * R) / R
+            for p, (x, y, h) in enumerate(pts):
+                zp = zf + h
+                R = np.sqrt(zp * zp + (x - X) ** 2 + (y - Y) ** 2)
+                K = (1 / (2 * math.pi)) * (zp / R) * (1 / R - 1j * kk) * np.exp(1j * kk * R) / R
                 ex[l, p] += np.sum(K * fx * wt)
                 ey[l, p] += np.sum(K * fy * wt)
     return ex, ey

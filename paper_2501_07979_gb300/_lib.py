@@ -92,6 +92,7 @@ SIGNATURES = {
     "zda_lens_zone_focal": (_i, [_vp, _i, _dp]),
     "zda_lens_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_lens_focal_plane": (_i, [_vp, _vp, _i, _i, _vp, _dp, _vp]),
+    "zda_lens_field_points": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
     "zda_last_error": (ctypes.c_char_p, []),
     "zda_focal_transform_nn": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp]),
     "zda_focal_transform_nn_transpose": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp]),

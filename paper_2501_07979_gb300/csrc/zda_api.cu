@@ -1433,11 +1433,11 @@ zda_status zda_lens_adjoint(zda_lens *L, const double *dI, float *const *grad_rh
 
 long long zda_lens_launch_count(const zda_lens *L) { return L ? L->launches : -1; }
 
-zda_status zda_lens_focal_plane(zda_lens *L, const double *pts_dev, int n_pts, int n_phi_samples, double *field_dev,
-                                double *p_trans_host, void *stream)
+static zda_status lens_field(zda_lens *L, const double *pts_dev, int pstride, int n_pts, int n_phi_samples,
+                             double *field_dev, double *p_trans_host, void *stream)
 {
     if (!L || !pts_dev || n_pts < 1 || n_phi_samples < 8 || !field_dev) return fail(ZDA_ERR_ARG, "bad argument");
-    if (!L->have_forward) return fail(ZDA_ERR_STATE, "zda_lens_focal_plane needs a preceding zda_lens_forward");
+    if (!L->have_forward) return fail(ZDA_ERR_STATE, "the lens field needs a preceding zda_lens_forward");
     cudaStream_t s = (cudaStream_t)stream;
     const int nl = L->nq / 2;
     double2 *ex = (double2 *)field_dev, *ey = ex + (size_t)nl * n_pts;
@@ -1449,7 +1449,7 @@ zda_status zda_lens_focal_plane(zda_lens *L, const double *pts_dev, int n_pts, i
                               Z->nq, d.n_r, d.n_phi, P<double2>(*Z, Z->L.umean), P<double>(*Z, Z->L.pt_row), s);
         const double zf = d.focal - (d.monitor_k * d.dz - d.design_k1 * d.dz);
         zda::launch_focal_plane(P<double2>(*Z, Z->L.umean), P<double>(*Z, Z->L.qr), P<double>(*Z, Z->L.qw),
-                                P<double>(*Z, Z->L.qp), P<double>(*Z, Z->L.qwp), d.n_r, nl, pts_dev, n_pts, zf,
+                                P<double>(*Z, Z->L.qp), P<double>(*Z, Z->L.qwp), d.n_r, nl, pts_dev, pstride, n_pts, zf,
                                 P<double>(*Z, Z->L.kk), n_phi_samples, ex, ey, s);
         CUDA_TRY(cudaGetLastError());
         Z->launches += 2;
@@ -1468,6 +1468,18 @@ zda_status zda_lens_focal_plane(zda_lens *L, const double *pts_dev, int n_pts, i
         for (int l = 0; l < nl; ++l) p_trans_host[l] = ptrans[l];
     CUDA_TRY(cudaStreamSynchronize(s));
     return ZDA_OK;
+}
+
+zda_status zda_lens_focal_plane(zda_lens *L, const double *pts_dev, int n_pts, int n_phi_samples, double *field_dev,
+                                double *p_trans_host, void *stream)
+{
+    return lens_field(L, pts_dev, 2, n_pts, n_phi_samples, field_dev, p_trans_host, stream);
+}
+
+zda_status zda_lens_field_points(zda_lens *L, const double *pts_dev, int n_pts, int n_phi_samples, double *field_dev,
+                                 void *stream)
+{
+    return lens_field(L, pts_dev, 3, n_pts, n_phi_samples, field_dev, nullptr, stream);
 }
 
 }  // extern "C"

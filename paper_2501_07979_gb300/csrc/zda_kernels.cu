@@ -725,10 +725,12 @@ void launch_phi_means(const float2 *mon, const double2 *emph_n, const double2 *e
 __global__ void k_focal_plane(const double2 *__restrict__ umean, const double *__restrict__ rr,
                               const double *__restrict__ wr, const double *__restrict__ rp,
                               const double *__restrict__ wp, int nr, int nl, const double *__restrict__ pts,
-                              int npts, double zf, const double *__restrict__ kk, int ns, double2 *ex, double2 *ey)
+                              int pstride, int npts, double zf0, const double *__restrict__ kk, int ns, double2 *ex,
+                              double2 *ey)
 {
     const int pidx = blockIdx.x, l = blockIdx.y;
-    const double px = pts[2 * pidx], py = pts[2 * pidx + 1];
+    const double px = pts[pstride * pidx], py = pts[pstride * pidx + 1];
+    const double zf = zf0 + (pstride == 3 ? pts[3 * pidx + 2] : 0.0);      // height above the focal plane
     const double k = kk[l];
     const double2 *upr = umean + ((size_t)l * 2 + 0) * nr, *upp = umean + ((size_t)l * 2 + 1) * nr;
     const double2 *umr = umean + ((size_t)(l + nl) * 2 + 0) * nr, *ump = umean + ((size_t)(l + nl) * 2 + 1) * nr;
@@ -781,11 +783,11 @@ __global__ void k_focal_plane(const double2 *__restrict__ umean, const double *_
 }
 
 void launch_focal_plane(const double2 *umean, const double *rr, const double *wr, const double *rp, const double *wp,
-                        int nr, int nl, const double *pts, int npts, double zf, const double *kk, int ns, double2 *ex,
-                        double2 *ey, cudaStream_t s)
+                        int nr, int nl, const double *pts, int pstride, int npts, double zf, const double *kk, int ns,
+                        double2 *ex, double2 *ey, cudaStream_t s)
 {
     dim3 g(npts, nl);
-    k_focal_plane<<<g, 256, 0, s>>>(umean, rr, wr, rp, wp, nr, nl, pts, npts, zf, kk, ns, ex, ey);
+    k_focal_plane<<<g, 256, 0, s>>>(umean, rr, wr, rp, wp, nr, nl, pts, pstride, npts, zf, kk, ns, ex, ey);
 }
 
 __global__ void k_status_check(const float *x, size_t n, int *status)

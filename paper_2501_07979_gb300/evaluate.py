@@ -78,3 +78,22 @@ def evaluate_lens(lens, lens_radius, focal, incident, n_top=1.0, n_rad=48, n_ang
                     "transmittance": p_trans[l] / p_inc,
                     "strehl": float(I0 * lam[l] ** 2 * focal ** 2 / (p_trans[l] * area))})
     return res, xs, I_line
+
+
+def xz_map(lens, xs, hs, n_top=1.0, n_phi_samples=128):
+    """Intensity (n/2)(|E_x|^2 + |E_y|^2) on the xz plane through the axis:
+    [n_lambda][len(hs)][len(xs)], h = height above the focal plane."""
+    X, Hh = np.meshgrid(np.asarray(xs, dtype=np.float64), np.asarray(hs, dtype=np.float64))
+    pts = np.stack([X.ravel(), np.zeros(X.size), Hh.ravel()], axis=1)
+    ex, ey = lens.field_points(pts, n_phi_samples=n_phi_samples)
+    return intensity(ex, ey, n_top).reshape(ex.shape[0], len(hs), len(xs))
+
+
+def encircled_power(radii, I_of_r):
+    """Encircled power P(rho) = int_0^rho I(r) 2 pi r dr of a radially
+    symmetric focal spot sampled at increasing radii (trapezoid rule)."""
+    r = np.asarray(radii, dtype=np.float64)
+    f = np.asarray(I_of_r, dtype=np.float64) * 2 * math.pi * r
+    out = np.zeros_like(r)
+    out[1:] = np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(r))
+    return out

@@ -161,3 +161,18 @@ class Lens:
                                               ctypes.c_void_p(out.data_ptr()), pt, self._stream()))
         o = out.cpu().numpy()
         return o[0, ..., 0] + 1j * o[0, ..., 1], o[1, ..., 0] + 1j * o[1, ..., 1], np.array(pt[:])
+
+    def field_points(self, pts_xyh, n_phi_samples=128):
+        """Field of the last forward at points (x, y, h), h = height above the
+        focal plane: returns (E_x, E_y) as complex arrays [n_lambda][n_pts]."""
+        import torch
+        from . import _lib
+        from ._lib import check
+        pts = torch.tensor(np.asarray(pts_xyh, dtype=np.float64).reshape(-1, 3), device=self.zones[0].device)
+        n = pts.shape[0]
+        nl = self.n_freq // 2
+        out = torch.empty((2, nl, n, 2), dtype=torch.float64, device=pts.device)
+        check(_lib.lib().zda_lens_field_points(self.handle, ctypes.c_void_p(pts.data_ptr()), int(n),
+                                               int(n_phi_samples), ctypes.c_void_p(out.data_ptr()), self._stream()))
+        o = out.cpu().numpy()
+        return o[0, ..., 0] + 1j * o[0, ..., 1], o[1, ..., 0] + 1j * o[1, ..., 1]

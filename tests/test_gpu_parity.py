@@ -15,7 +15,7 @@ import pytest
 import torch
 
 import oracle as O
-from zda_inputs import zone_cfg1, zone_cfg2, zone_tiny, smoothed_rho, rho_for
+from zda_inputs import zone_lwir, zone_cfg1, zone_cfg2, zone_tiny, smoothed_rho, rho_for
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +71,8 @@ RAGGED = {
                              pulse_t0=1.6),
     "one_phi_cell": zone_tiny(n_phi=1, n_fold=300, n_steps=200, r_lo=8.0),
     "no_inner_pml": zone_tiny(pml_r_in=0, n_steps=200),
+    # a 1-lambda strip of the paper's LWIR zone 16: lambda/50 grid, silicon, 11 phi cells
+    "lwir_strip": zone_lwir(16, 1500).replace(n_r=66, r_lo=395.0),
 }
 
 
@@ -417,6 +419,15 @@ def test_lens_focal_plane_matches_bruteforce_oracle():
         p_ref = p_ref + O.transmitted_power(s, f["geom"], f["mon"])
     assert _rel(ex, rx) < 1e-4 and _rel(ey, ry) < 1e-4
     assert _rel(pt, p_ref) < 1e-4
+    # off the focal plane (x, y, h): the xz-map path
+    pts3 = [(0.0, 0.0, -2.0), (0.5, 0.0, 1.5), (1.0, 0.3, -0.5)]
+    ex3, ey3 = lens.field_points(pts3, n_phi_samples=256)
+    rx3 = ry3 = 0
+    for s, r in zip(specs, rhos):
+        f = O.forward(s, r)
+        a, b = O.focal_plane_bruteforce(s, f["geom"], f["mon"], pts3)
+        rx3, ry3 = rx3 + a, ry3 + b
+    assert _rel(ex3, rx3) < 1e-4 and _rel(ey3, ry3) < 1e-4
 
 
 def test_topopt_on_a_zone_increases_focal_intensity():

@@ -476,3 +476,26 @@ def test_focal_plane_on_axis_equals_on_axis_transform():
     cp, cm = f["S"][:nl], np.conj(f["S"][nl:])
     assert np.allclose(ex[:, 0], cp + cm, rtol=1e-10, atol=1e-14)
     assert np.allclose(ey[:, 0], 1j * (cp - cm), rtol=1e-10, atol=1e-14)
+
+
+def test_field_off_the_focal_plane_matches_the_annulus_closed_form():
+    """The brute-force field at (0, 0, h) above the focal plane of a uniform
+    m = +1 annulus field (as in T8, E_r part) equals Re(U0) times the RS-I
+    closed form at distance zf + h, converging at second order in dr."""
+    hs = (-3.0, -1.0, 0.0, 2.5)
+    errs = []
+    for dr in (0.05, 0.025):
+        s = zone_tiny(r_lo=5.0, n_r=int(round(4 / dr)), dr=dr, pml_r_in=int(round(0.5 / dr)),
+                      pml_r_out=int(round(0.5 / dr)), n_phi=12, n_fold=40, wavelengths=(0.9,), focal=7.0)
+        g = O.Geometry(s)
+        U0 = 0.7 - 0.3j
+        mon = np.zeros((g.n_freq, 2, s.n_r, s.n_phi), complex)
+        mon[:, 0] = U0 * np.exp(1j * g.phi_n)[None, None, :]
+        _, _, zf = O.focal_weights(s, g)
+        ex, ey = O.focal_plane_bruteforce(s, g, mon, [(0.0, 0.0, h) for h in hs])
+        k = 2 * math.pi / 0.9
+        want = np.array([U0.real * _annulus_closed_form(zf + h, g.r0, g.r1, k) for h in hs])
+        wy = np.array([-U0.imag * _annulus_closed_form(zf + h, g.r0, g.r1, k) for h in hs])
+        errs.append(max(np.max(np.abs(ex[0] - want) / np.abs(want)), np.max(np.abs(ey[0] - wy) / np.abs(wy))))
+    assert errs[0] < 1e-2, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
