@@ -99,7 +99,7 @@ void launch_update_e(const StepParams &p, int n, cudaStream_t s);
 // two z-cells per thread (zda_pair.cu): even n_z, even pml_z, wedge zones
 bool pair_kernels_apply(const StepParams &p);
 void launch_update_h_pair(const StepParams &p, cudaStream_t s);
-void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s);   // no DFT: see launch_dft_sites
+void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s);   // writes the DFT history; see launch_dft_flush
 // Time-blocked running DFT of the split step (two z-cells per thread).
 constexpr int DFT_BLOCK = 32;
 #define ZDA_DFT_MAXQ 16

@@ -142,7 +142,7 @@ __device__ __forceinline__ void mb_arrive(uint32_t bar)
 }
 
 // Persistent, warp-specialised convolution.  Warp 0 (one lane) streams, per
-// tile and input group, the TMA window into one of two window stages; the
+// tile and input unit, the bulk-copied window into one of two stages; the
 // weight blocks are either loaded once per CTA (resident: every layer whose
 // weights fit beside the two windows) or streamed per tap through a ring
 // (the concatenating layers); warp 1 (one lane) issues the MMAs
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t raw = su32(smem), base = (raw + 1023u) & ~1023u;   // TMA destinations: 1024-aligned
+    const uint32_t raw = su32(smem), base = (raw + 1023u) & ~1023u;   // copy destinations: 1024-aligned
     // a unit = up to 4 planes (32 channels) of one input group; window stages hold one unit
     const int upl = p.cg / 8 < 4 ? p.cg / 8 : 4, uh = (p.cg / 8) / upl, nunits = p.ngroups * uh;
     const uint32_t win_bytes = (uint32_t)upl * p.plane;

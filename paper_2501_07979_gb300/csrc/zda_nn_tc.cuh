@@ -1,5 +1,5 @@
 // Inline-PTX helpers of the surrogate's tensor-core kernels (sm_103a):
-// mbarriers, TMA tensor and bulk copies, and the tcgen05 family (TMEM
+// mbarriers, bulk copies (cp.async.bulk), and the tcgen05 family (TMEM
 // allocation, MMA issue, commit, TMEM -> register loads).
 //
 // Operand layouts used with tcgen05.mma (no swizzle, "interleaved" canonical
@@ -49,16 +49,6 @@ __device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, int limit
 }
 
 // ---------------------------------------------------------------- copies
-// 2-D tiled TMA load (box from the tensor map) into shared memory, completing
-// on `bar` (transaction bytes).  x = innermost coordinate (elements).
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
 // Contiguous bulk copy (16-byte aligned addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
