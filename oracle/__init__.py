@@ -65,6 +65,9 @@ class _Problem(ctypes.Structure):
         ("mon_k", ctypes.c_int), ("mon_dft", ctypes.c_void_p),
         ("des_k0", ctypes.c_int), ("des_nk", ctypes.c_int), ("des_dft", ctypes.c_void_p),
         ("state", ctypes.c_void_p), ("nthreads", ctypes.c_int),
+        ("rpml_metric", ctypes.c_int),
+        ("bm_n", ctypes.c_void_p), ("cm_n", ctypes.c_void_p),
+        ("bm_h", ctypes.c_void_p), ("cm_h", ctypes.c_void_p),
     ]
 
 
@@ -82,7 +85,7 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
-N_STATE = 14   # E_r, E_phi, E_z, H_r, H_phi, H_z and 8 CPML auxiliaries
+N_STATE = 18   # E_r, E_phi, E_z, H_r, H_phi, H_z, 8 CPML and 4 metric auxiliaries
 
 
 # --------------------------------------------------------------------------
@@ -149,37 +152,66 @@ class Geometry:
 # --------------------------------------------------------------------------
 # CPML profiles (stretched-coordinate PML in r and z)
 # --------------------------------------------------------------------------
-def cpml_coefficients(spec, geom, R0: float = 1e-8, grade: int = 3):
+def cpml_coefficients(spec, geom, R0: float = 1e-8, grade: int = 3, metric: bool = False,
+                      outer_stretch: bool = True, metric_inner: bool = False, margin: float = 2.0):
     """Convolutional PML coefficients b, c at r nodes, r half nodes, z nodes and
     z half nodes (section "Differentiable FDTD": stretched-coordinate PMLs in
     (r, z)).  Reading: kappa = 1, sigma(x) = sigma_max x^grade with
     sigma_max = -(grade+1) ln(R0) / (2 d), alpha(x) = alpha_max (1 - x) with
     alpha_max = 0.05 * 2 pi f0, x = depth / d in [0, 1];
-    b = exp(-(sigma + alpha) dt), c = sigma / (sigma + alpha) (b - 1)."""
+    b = exp(-(sigma + alpha) dt), c = sigma / (sigma + alpha) (b - 1).
+
+    metric=True: inside the r-PML the metric factors use the stretched
+    radius (the same section: r' = r + i zeta_r / w appears in the equations
+    themselves).  (1/r~) d/dr~ (r~ F) = (1/s_r) dF/dr + F / r~, so only the
+    derivative part of (1/r) d/dr (r .) carries the CPML stretch, and the
+    metric parts are divided by r~.  Outer slab: r~ = r + Omega(r) /
+    (alpha_max - i w), Omega(r) = int sigma dr' from the slab's interior face,
+    with the same constant alpha_max in s_r so that dr~/dr = s_r exactly;
+    1/r~ = (1/r) / (1 + sigma_m / (alpha_max - i w)), sigma_m = Omega / r >= 0,
+    is one more recursive convolution: bm = exp(-(sigma_m + alpha) dt),
+    cm = sigma_m / (sigma_m + alpha) (bm - 1).  outer_stretch=False keeps
+    r~ = r there too (bm = cm = 0).
+
+    The regularisation (the same section warns that the r-PML must be
+    regularised against divergence): the inner slab's metric keeps the real
+    radius (bm = cm = 0).  There Omega < 0, so Im r~ < 0, and a field of
+    azimuthal order M with M / r >> k (the wedge's non-propagating orders
+    m + k n) gains at a rate ~ -sigma_m instead of decaying.
+    metric_inner=True builds that unregularised inner slab anyway
+    (alpha_s = max(alpha_max, margin max(-sigma_m)) in it keeps its own pole
+    stable) so that a test can show the growth."""
     s = spec
     dt = geom.dt
     a_max = 0.05 * 2.0 * math.pi * s.pulse_f0
 
-    def coeffs(pos, lo, hi, n_in, n_out, h):
+    def depth(pos, lo, hi, n_in, n_out, h):
+        """(x in [0, 1], sign: -1 inner PML, +1 outer PML, 0 interior, d)."""
         pos = np.asarray(pos, dtype=np.float64)
         x = np.zeros_like(pos)
+        sgn = np.zeros_like(pos)
         if n_in > 0:
             d = n_in * h
-            x = np.where(pos < lo + d, (lo + d - pos) / d, x)
+            inner = pos < lo + d
+            x = np.where(inner, (lo + d - pos) / d, x)
+            sgn = np.where(inner, -1.0, sgn)
         if n_out > 0:
             d = n_out * h
-            x = np.where(pos > hi - d, (pos - (hi - d)) / d, x)
-        x = np.clip(x, 0.0, 1.0)
-        d_in = max(n_in, 1) * h
-        d_out = max(n_out, 1) * h
-        d = np.where(pos < 0.5 * (lo + hi), d_in, d_out)
-        smax = -(grade + 1) * math.log(R0) / (2.0 * d)
-        sig = smax * x ** grade
-        alp = a_max * (1.0 - x)
+            outer = pos > hi - d
+            x = np.where(outer, (pos - (hi - d)) / d, x)
+            sgn = np.where(outer, 1.0, sgn)
+        d = np.where(sgn < 0, max(n_in, 1) * h, max(n_out, 1) * h)
+        return np.clip(x, 0.0, 1.0), sgn, d
+
+    def recursion(sig, alp):
         b = np.exp(-(sig + alp) * dt)
-        c = np.where(sig > 0, sig / np.maximum(sig + alp, 1e-300) * (b - 1.0), 0.0)
-        b = np.where(sig > 0, b, 0.0)
-        return b, c
+        c = np.where(sig != 0, sig / np.where(sig != 0, sig + alp, 1.0) * (b - 1.0), 0.0)
+        return np.where(sig != 0, b, 0.0), c
+
+    def coeffs(pos, lo, hi, n_in, n_out, h):
+        x, sgn, d = depth(pos, lo, hi, n_in, n_out, h)
+        smax = -(grade + 1) * math.log(R0) / (2.0 * d)
+        return recursion(smax * x ** grade, a_max * (1.0 - x))
 
     r_lo, r_hi = s.r_lo, s.r_lo + s.n_r * s.dr
     z_lo, z_hi = 0.0, s.n_z * s.dz
@@ -189,8 +221,35 @@ def cpml_coefficients(spec, geom, R0: float = 1e-8, grade: int = 3):
     zh = s.dz * (np.arange(s.n_z) + 0.5)
     bz_n, cz_n = coeffs(zn, z_lo, z_hi, s.pml_z, s.pml_z, s.dz)
     bz_h, cz_h = coeffs(zh, z_lo, z_hi, s.pml_z, s.pml_z, s.dz)
-    return dict(br_n=br_n, cr_n=cr_n, br_h=br_h, cr_h=cr_h,
-                bz_n=bz_n, cz_n=cz_n, bz_h=bz_h, cz_h=cz_h)
+    out = dict(br_n=br_n, cr_n=cr_n, br_h=br_h, cr_h=cr_h,
+               bz_n=bz_n, cz_n=cz_n, bz_h=bz_h, cz_h=cz_h)
+    if not metric:
+        return out
+
+    def stretch(pos):
+        x, sgn, d = depth(pos, r_lo, r_hi, s.pml_r_in, s.pml_r_out, s.dr)
+        smax = -(grade + 1) * math.log(R0) / (2.0 * d)
+        omega_int = sgn * smax * d * x ** (grade + 1) / (grade + 1)     # int sigma dr' from the face
+        pos = np.asarray(pos, dtype=np.float64)
+        sig_m = np.where(pos > 0, omega_int / np.where(pos > 0, pos, 1.0), 0.0)
+        return smax * x ** grade, sig_m, sgn
+
+    a_in = a_max
+    parts = {}
+    for key, pos in (("n", geom.r_n), ("h", geom.r_h)):
+        parts[key] = stretch(pos)
+        if metric_inner:
+            a_in = max(a_in, margin * max(0.0, float(-parts[key][1].min())))
+    for key, (sig, sig_m, sgn) in parts.items():
+        stretched = ((sgn > 0) & outer_stretch) | ((sgn < 0) & metric_inner)
+        alp = np.where(sgn < 0, a_in, a_max)
+        b, c = recursion(np.where(stretched, sig, 0.0), alp)
+        out["br_" + key] = np.where(stretched, b, out["br_" + key])
+        out["cr_" + key] = np.where(stretched, c, out["cr_" + key])
+        out["bm_" + key], out["cm_" + key] = recursion(np.where(stretched, sig_m, 0.0), alp)
+    out["metric"] = 1
+    out["alpha_s"] = (a_in, a_max)
+    return out
 
 
 def no_pml(spec):
@@ -395,7 +454,13 @@ def run(spec, geom, eps, n_steps=None, pml=None, src_pat=None, src_time=None, sr
     if state is not None:
         state = np.ascontiguousarray(state, dtype=np.complex128)
         assert state.shape == (N_STATE, s.n_r, s.n_phi, s.n_z)
-    pm = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in pml.items()}
+    metric = int(pml.get("metric", 0))
+    pm = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in pml.items()
+          if k not in ("metric", "alpha_s")}
+    if metric:
+        mt = {k: _ptr(pm[k]) for k in ("bm_n", "cm_n", "bm_h", "cm_h")}
+    else:
+        mt = dict(bm_n=None, cm_n=None, bm_h=None, cm_h=None)
     b = geom.bloch if bloch is None else bloch
     P = _Problem(
         nr=s.n_r, nphi=s.n_phi, nz=s.n_z, n_steps=n_steps,
@@ -409,7 +474,8 @@ def run(spec, geom, eps, n_steps=None, pml=None, src_pat=None, src_time=None, sr
         n_freq=nf, twiddle=_ptr(twiddle),
         mon_k=(mon_k if mon is not None else -1), mon_dft=_ptr(mon),
         des_k0=geom.des_k0, des_nk=(geom.des_nk if des is not None else 0), des_dft=_ptr(des),
-        state=_ptr(state), nthreads=int(nthreads), bor=int(geom.bor), m=int(s.m))
+        state=_ptr(state), nthreads=int(nthreads), bor=int(geom.bor), m=int(s.m),
+        rpml_metric=metric, **mt)
     rc = _lib().orc_run(ctypes.byref(P))
     if rc != 0:
         raise RuntimeError("oracle time loop failed: %d" % rc)

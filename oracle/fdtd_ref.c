@@ -22,8 +22,21 @@
  *    both neighbours and 1/r at the centre.  PEC walls close the domain at
  *    r_lo, r_hi, z = 0 and z = nz dz (tangential E = 0 there).
  *  - CPML: each r- or z-derivative term D gets an auxiliary psi with
- *    psi <- b psi + c D and is replaced by D + psi (kappa = 1).  The 1/r
- *    metric factors use the real radius.
+ *    psi <- b psi + c D and is replaced by D + psi (kappa = 1).  With
+ *    rpml_metric == 0 the 1/r metric factors use the real radius and the
+ *    whole (1/r) d/dr (r .) term is stretched.
+ *  - rpml_metric == 1: inside the r-PML (radii whose CPML b is non-zero)
+ *    the stretched radius r~ of the r-PML enters the metric factors
+ *    (section "Differentiable FDTD": the stretched coordinate appears
+ *    explicitly in the equations).  (1/r~) d/dr~ (r~ F) = (1/s_r) dF/dr +
+ *    F / r~, so the z-curls split into a stretched derivative
+ *    (F(i+1) - F(i)) / dr and a metric part X = (F(i+1) + F(i)) / 2 -+ dF/dphi;
+ *    every metric part (and the phi-derivatives of the r-curls) is divided
+ *    by r~ through 1/r~ = (1/r) (X + psi_m), psi_m <- bm psi_m + cm X, the
+ *    same recursive convolution as the CPML with sigma_m = Omega / r
+ *    (bm = cm = 0: r~ = r, only the derivative is stretched).  Outside the
+ *    r-PML the updates are those of rpml_metric == 0 (the same in exact
+ *    arithmetic there).
  *  - The source current J enters the E update as E += dt/eps (curl H - J)
  *    on the E_r and E_phi sites of one z-plane at t_{n+1/2}.
  *  - DFT: X(w) += E^{n+1} e^{i w t_{n+1}} dt after each E update.
@@ -65,14 +78,17 @@ typedef struct {
     double *mon_dft;          /* complex [n_freq][2][nr][nphi] (E_r, E_phi) */
     int des_k0, des_nk;       /* des_nk == 0: no design-volume DFT */
     double *des_dft;          /* complex [n_freq][3][des_nk][nr][nphi] */
-    double *state;            /* NULL, or complex [14][nr][nphi][nz] in/out */
+    double *state;            /* NULL, or complex [18][nr][nphi][nz] in/out */
     int nthreads;             /* 0: OpenMP default */
+    int rpml_metric;          /* 1: stretched radius in the metric factors */
+    const double *bm_n, *cm_n, *bm_h, *cm_h;   /* metric recursion, r nodes / half nodes */
 } orc_problem;
 
-#define NSTATE 14
+#define NSTATE 18
 enum { ER, EP, EZ, HR, HP, HZ,
        PS_HR_Z, PS_HP_Z, PS_HP_R, PS_HZ_R,     /* H-side CPML psi */
-       PS_ER_Z, PS_EP_Z, PS_EP_R, PS_EZ_R };   /* E-side CPML psi */
+       PS_ER_Z, PS_EP_Z, PS_EP_R, PS_EZ_R,     /* E-side CPML psi */
+       PS_HR_M, PS_HZ_M, PS_ER_M, PS_EZ_M };   /* metric psi (rpml_metric == 1) */
 
 int orc_state_count(void) { return NSTATE; }
 
@@ -126,6 +142,12 @@ int orc_run(const orc_problem *p)
                     if (r_n[i] > 0.0) {
                         cplx d_phi = p->bor ? I * p->m * AT(Ez, i, j, k) / r_n[i]
                                             : (ez_jp - AT(Ez, i, j, k)) / (r_n[i] * dphi);
+                        if (p->rpml_metric && p->br_n[i] != 0.0) {
+                            const cplx X = p->bor ? I * p->m * AT(Ez, i, j, k) : (ez_jp - AT(Ez, i, j, k)) / dphi;
+                            cplx *pm = &AT(f + PS_HR_M * ncell, i, j, k);
+                            *pm = p->bm_n[i] * *pm + p->cm_n[i] * X;
+                            d_phi = (X + *pm) / r_n[i];
+                        }
                         cplx d_z = (ep_kp - AT(Ep, i, j, k)) / dz;
                         cplx *ps = &AT(f + PS_HR_Z * ncell, i, j, k);
                         *ps = p->bz_h[k] * *ps + p->cz_h[k] * d_z;
@@ -142,13 +164,22 @@ int orc_run(const orc_problem *p)
                         AT(Hp, i, j, k) -= dt * ((d_z + *psz) - (d_r + *psr));
                     }
                     /* H_z at (r_{i+1/2}, phi_{j+1/2}, z_k) */
-                    {
+                    if (!(p->rpml_metric && p->br_h[i] != 0.0)) {
                         cplx d_r = (r_n[i + 1] * ep_ip - r_n[i] * AT(Ep, i, j, k)) / (r_h[i] * dr);
                         cplx d_phi = p->bor ? I * p->m * AT(Er, i, j, k) / r_h[i]
                                             : (er_jp - AT(Er, i, j, k)) / (r_h[i] * dphi);
                         cplx *ps = &AT(f + PS_HZ_R * ncell, i, j, k);
                         *ps = p->br_h[i] * *ps + p->cr_h[i] * d_r;
                         AT(Hz, i, j, k) -= dt * ((d_r + *ps) - d_phi);
+                    } else {
+                        const cplx d_r = (ep_ip - AT(Ep, i, j, k)) / dr;
+                        const cplx X = 0.5 * (ep_ip + AT(Ep, i, j, k))
+                                     - (p->bor ? I * p->m * AT(Er, i, j, k) : (er_jp - AT(Er, i, j, k)) / dphi);
+                        cplx *ps = &AT(f + PS_HZ_R * ncell, i, j, k);
+                        cplx *pm = &AT(f + PS_HZ_M * ncell, i, j, k);
+                        *ps = p->br_h[i] * *ps + p->cr_h[i] * d_r;
+                        *pm = p->bm_h[i] * *pm + p->cm_h[i] * X;
+                        AT(Hz, i, j, k) -= dt * ((d_r + *ps) + (X + *pm) / r_h[i]);
                     }
                 }
 
@@ -173,6 +204,12 @@ int orc_run(const orc_problem *p)
                     if (k > 0) {
                         cplx d_phi = p->bor ? I * p->m * AT(Hz, i, j, k) / r_h[i]
                                             : (AT(Hz, i, j, k) - hz_jm) / (r_h[i] * dphi);
+                        if (p->rpml_metric && p->br_h[i] != 0.0) {
+                            const cplx X = p->bor ? I * p->m * AT(Hz, i, j, k) : (AT(Hz, i, j, k) - hz_jm) / dphi;
+                            cplx *pm = &AT(f + PS_ER_M * ncell, i, j, k);
+                            *pm = p->bm_h[i] * *pm + p->cm_h[i] * X;
+                            d_phi = (X + *pm) / r_h[i];
+                        }
                         cplx d_z = (AT(Hp, i, j, k) - AT(Hp, i, j, k - 1)) / dz;
                         cplx *ps = &AT(f + PS_ER_Z * ncell, i, j, k);
                         *ps = p->bz_n[k] * *ps + p->cz_n[k] * d_z;
@@ -189,13 +226,22 @@ int orc_run(const orc_problem *p)
                         AT(Ep, i, j, k) += dt / AT(p->eps_p, i, j, k) * (((d_z + *psz) - (d_r + *psr)) - jp);
                     }
                     /* E_z at (r_i, phi_j, z_{k+1/2}); PEC at i = 0 */
-                    if (i > 0) {
+                    if (i > 0 && !(p->rpml_metric && p->br_n[i] != 0.0)) {
                         cplx d_r = (r_h[i] * AT(Hp, i, j, k) - r_h[i - 1] * AT(Hp, i - 1, j, k)) / (r_n[i] * dr);
                         cplx d_phi = p->bor ? I * p->m * AT(Hr, i, j, k) / r_n[i]
                                             : (AT(Hr, i, j, k) - hr_jm) / (r_n[i] * dphi);
                         cplx *ps = &AT(f + PS_EZ_R * ncell, i, j, k);
                         *ps = p->br_n[i] * *ps + p->cr_n[i] * d_r;
                         AT(Ez, i, j, k) += dt / AT(p->eps_z, i, j, k) * ((d_r + *ps) - d_phi);
+                    } else if (i > 0) {
+                        const cplx d_r = (AT(Hp, i, j, k) - AT(Hp, i - 1, j, k)) / dr;
+                        const cplx X = 0.5 * (AT(Hp, i, j, k) + AT(Hp, i - 1, j, k))
+                                     - (p->bor ? I * p->m * AT(Hr, i, j, k) : (AT(Hr, i, j, k) - hr_jm) / dphi);
+                        cplx *ps = &AT(f + PS_EZ_R * ncell, i, j, k);
+                        cplx *pm = &AT(f + PS_EZ_M * ncell, i, j, k);
+                        *ps = p->br_n[i] * *ps + p->cr_n[i] * d_r;
+                        *pm = p->bm_n[i] * *pm + p->cm_n[i] * X;
+                        AT(Ez, i, j, k) += dt / AT(p->eps_z, i, j, k) * ((d_r + *ps) + (X + *pm) / r_n[i]);
                     }
                 }
 
