@@ -219,6 +219,27 @@ long long zda_zone_launch_count(const zda_zone *zone);
 zda_status zda_zone_set_kernel(zda_zone *zone, int variant, int tile_phi, int i_ranges);
 zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi, int *i_ranges);
 
+/* Form of the radial PML ("Differentiable FDTD in cylindrical coordinates":
+ * the stretched coordinate r' = r + i zeta_r(r) / w appears explicitly in the
+ * equations, and the r-PML has to be regularised).
+ * form 0 (default): convolutional PML on every d/dr term, the whole
+ *   (1/r) d/dr (r .) of the z-curls stretched, real radius in every metric
+ *   factor.
+ * form 1: stretched coordinates.  Inside the r-PML the z-curls are
+ *   (1/s_r) dF/dr + X / r~ with the metric part X = (F(i+1) + F(i)) / 2 -+
+ *   dG/dphi, and the r-curls take (1/r~) dG/dphi; in the outer slab r~ = r + Omega / (alpha - i w),
+ *   Omega = int sigma dr' (alpha constant over the slab, so dr~/dr = s_r),
+ *   realised as one more recursive convolution per H_r, H_z, E_r, E_z site.
+ *   The inner slab keeps r~ = r (the regularisation: with the stretched inner
+ *   radius Im r~ < 0 and the wedge's non-propagating azimuthal orders grow).
+ *   Reflection of a cylindrical pulse at w0, against a radially larger
+ *   domain: 1.9e-3 (form 0) vs 5e-5 (form 1) at r = 10 lambda.
+ * Form 1 runs on the split step (variants 0 and 2); the fused step
+ * (variant 1) refuses it (ZDA_ERR_ARG either way round).  Takes effect at
+ * the next run; a zda_adjoint needs a zda_forward of the same form. */
+zda_status zda_zone_set_radial_pml(zda_zone *zone, int form);
+zda_status zda_zone_get_radial_pml(const zda_zone *zone, int *form);
+
 /* Time `steps` time steps of the zone's current step kernel (no source, no
  * DFT) on its current field state, with CUDA events on `stream`; ms_out
  * receives the elapsed milliseconds.  Overwrites the fields (a following

@@ -557,19 +557,22 @@ def intensity_grad(S):
 # --------------------------------------------------------------------------
 # forward and adjoint (hybrid time/frequency adjoint)
 # --------------------------------------------------------------------------
-def forward(spec, rho, nthreads=0, n_steps=None):
+def forward(spec, rho, nthreads=0, n_steps=None, pml_form=0):
     """Forward zone solve: rho -> rho~ -> eps -> time loop with the plane-wave
-    source -> monitor and design-volume DFTs -> focal phasors S -> I."""
+    source -> monitor and design-volume DFTs -> focal phasors S -> I.
+    pml_form 1: the stretched-coordinate r-PML (cpml_coefficients, metric)."""
     geom = Geometry(spec)
+    pml = cpml_coefficients(spec, geom, metric=bool(pml_form))
     rt = rho_tilde(spec, geom, np.asarray(rho, dtype=np.float64))
     eps = site_eps(spec, geom, rt)
     n = spec.n_steps if n_steps is None else n_steps
     t_half = geom.dt * (np.arange(n) + 0.5)
     src_t = pulse(spec, t_half)[:, None].astype(np.complex128)
-    mon, des, _ = run(spec, geom, eps, n_steps=n, src_pat=plane_wave_pattern(spec, geom),
+    mon, des, _ = run(spec, geom, eps, n_steps=n, pml=pml, src_pat=plane_wave_pattern(spec, geom),
                       src_time=src_t, twiddle=twiddles(geom, n), nthreads=nthreads)
     S = focal_phasors(spec, geom, mon)
-    return dict(geom=geom, rho_tilde=rt, eps=eps, mon=mon, des=des, S=S, I=intensity(S), n_steps=n)
+    return dict(geom=geom, rho_tilde=rt, eps=eps, mon=mon, des=des, S=S, I=intensity(S), n_steps=n,
+                pml=pml)
 
 
 def adjoint_pulse_matrix(spec, geom, n_steps):
@@ -632,7 +635,7 @@ def adjoint(spec, fwd, dI_dS, nthreads=0):
     b_p[:, 0, :] = 0.0                                 # E_phi on the PEC wall r_lo (or the axis)
     pat = np.stack([b_r, b_p], axis=1)                 # [q][2][nr][nphi]
     src_t = adjoint_pulse_matrix(s, geom, n)
-    _, des_a, _ = run(s, geom, fwd["eps"], n_steps=n, src_pat=pat, src_time=src_t, src_k=k,
+    _, des_a, _ = run(s, geom, fwd["eps"], n_steps=n, pml=fwd.get("pml"), src_pat=pat, src_time=src_t, src_k=k,
                       twiddle=twiddles(geom, n), mon_k=-1, nthreads=nthreads)
     nl = geom.n_lambda
     qbar = (np.arange(geom.n_freq) + nl) % geom.n_freq
@@ -652,11 +655,11 @@ def adjoint(spec, fwd, dI_dS, nthreads=0):
     return dict(grad_rho_tilde=g_rt, des_adj=des_a, site_grad=gsite)
 
 
-def gradient(spec, rho, nthreads=0, n_steps=None):
+def gradient(spec, rho, nthreads=0, n_steps=None, pml_form=0):
     """dI/drho for I = summed focal intensity: forward, adjoint, then the
     projection derivative and the transposed conic filter."""
     rho = np.asarray(rho, dtype=np.float64)
-    fwd = forward(spec, rho, nthreads=nthreads, n_steps=n_steps)
+    fwd = forward(spec, rho, nthreads=nthreads, n_steps=n_steps, pml_form=pml_form)
     fwd["rho"] = rho
     adj = adjoint(spec, fwd, intensity_grad(fwd["S"]), nthreads=nthreads)
     geom = fwd["geom"]

@@ -77,6 +77,8 @@ SIGNATURES = {
     "zda_zone_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_zone_set_kernel": (_i, [_vp, _i, _i, _i]),
     "zda_zone_get_kernel": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "zda_zone_set_radial_pml": (_i, [_vp, _i]),
+    "zda_zone_get_radial_pml": (_i, [_vp, ctypes.POINTER(_i)]),
     "zda_zone_set_wait_limit": (_i, [_vp, _i, _i]),
     "zda_zone_time_steps": (_i, [_vp, _i, _dp, _vp]),
     "zda_zone_set_timing": (_i, [_vp, _i]),

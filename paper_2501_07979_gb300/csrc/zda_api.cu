@@ -48,8 +48,8 @@ struct zda_ctx {
 namespace {
 
 struct Layout {           // byte offsets inside the workspace
-    size_t fields, psi_z, psi_r, fields2, psi_h2, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
-        norm, src_rad, dft_hist, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
+    size_t fields, psi_z, psi_r, psi_m, fields2, psi_h2, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
+        norm, src_rad, dft_hist, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bm_n, cm_n, bm_h, cm_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
         ph_h, pulse, twiddle, adj_time, Gr, Gp, emph_n, emph_h, wt, beta_r, beta_p, g_in, partial, S,
         umean, pt_row, qr, qw, qp, qwp, kk, status, total;
 };
@@ -76,6 +76,7 @@ struct zda_zone {
     int variant = 0, tile_phi = 2, i_ranges = 0;
     int wait_limit = 1 << 22, inject_timeout = 0;   // bounded mbarrier waits of the fused step
     bool pair_kernels = true;       // split step: two z-cells per thread where the grid allows
+    int rpml = 0;                   // r-PML form (zda_zone_set_radial_pml)
     int last_parity = 0;            // fused runs: which buffer holds the final fields
     // optional CUDA-event timing of every `time_every`-th H/E launch pair
     int time_every = 0;
@@ -126,24 +127,47 @@ static double layer_eps_at(const zda_zone_desc &d, int k)
 // sigma_max = -4 ln(1e-8) / (2 d), alpha = 0.05 (2 pi f0) (1 - x);
 // b = exp(-(sigma + alpha) dt), c = sigma / (sigma + alpha) (b - 1);
 // x = depth into the PML / its thickness.
+//
+// Stretched-radius form of the r-PML (metric != 0; section "Differentiable
+// FDTD": the stretched coordinate r~ enters the equations themselves): in
+// the outer slab r~ = r + Omega(r) / (alpha_max - i w) with
+// Omega = int sigma dr' = sigma_max d x^4 / 4, and s_r takes the same
+// constant alpha_max so that dr~/dr = s_r; 1/r~ = (1/r) / (1 + sigma_m /
+// (alpha_max - i w)), sigma_m = Omega / r, is the same recursion with
+// sigma_m (the `metric` tables).  The inner slab keeps the real radius (a
+// stretched inner radius has Im r~ < 0, under which the wedge's
+// non-propagating azimuthal orders grow) and its graded alpha.
 static void cpml_table(const zda_zone &z, double lo, double hi, int n_in, int n_out, double h,
-                       const std::vector<double> &pos, std::vector<float> &b, std::vector<float> &c)
+                       const std::vector<double> &pos, std::vector<float> &b, std::vector<float> &c,
+                       int stretched_outer = 0, std::vector<float> *bm = nullptr, std::vector<float> *cm = nullptr)
 {
     const double a_max = 0.05 * 2.0 * M_PI * z.f0;
     b.assign(pos.size(), 0.f);
     c.assign(pos.size(), 0.f);
+    if (bm) bm->assign(pos.size(), 0.f);
+    if (cm) cm->assign(pos.size(), 0.f);
+    auto recursion = [&](double sg, double al, float &bo, float &co) {
+        const double bb = std::exp(-(sg + al) * z.dt);
+        bo = (float)bb;
+        co = (float)(sg / (sg + al) * (bb - 1.0));
+    };
     for (size_t t = 0; t < pos.size(); ++t) {
         const double x0 = pos[t];
         double x = 0.0, thick = h;
+        bool outer = false;
         if (n_in > 0 && x0 < lo + n_in * h) { thick = n_in * h; x = (lo + thick - x0) / thick; }
-        if (n_out > 0 && x0 > hi - n_out * h) { thick = n_out * h; x = (x0 - (hi - thick)) / thick; }
+        if (n_out > 0 && x0 > hi - n_out * h) { thick = n_out * h; x = (x0 - (hi - thick)) / thick; outer = true; }
         x = std::min(std::max(x, 0.0), 1.0);
         if (x <= 0.0) continue;
         const double smax = -4.0 * std::log(1e-8) / (2.0 * thick);
-        const double sg = smax * x * x * x, al = a_max * (1.0 - x);
-        const double bb = std::exp(-(sg + al) * z.dt);
-        b[t] = (float)bb;
-        c[t] = (float)(sg / (sg + al) * (bb - 1.0));
+        const double sg = smax * x * x * x;
+        if (stretched_outer && outer) {
+            recursion(sg, a_max, b[t], c[t]);
+            const double sm = smax * thick * x * x * x * x / 4.0 / x0;
+            if (bm && cm) recursion(sm, a_max, (*bm)[t], (*cm)[t]);
+        } else {
+            recursion(sg, a_max * (1.0 - x), b[t], c[t]);
+        }
     }
 }
 
@@ -195,6 +219,7 @@ static void compute_layout(zda_zone &z)
     L.fields = take(6 * ncell * sizeof(float2));
     L.psi_z = take(4 * plane * 2 * d.pml_z * sizeof(float2));
     L.psi_r = take(4 * (size_t)(d.pml_r_in + d.pml_r_out) * np * nz * sizeof(float2));
+    L.psi_m = take(4 * (size_t)(d.pml_r_in + d.pml_r_out) * np * nz * sizeof(float2));   // zeroed with psi_r
     // second field buffer and H-side CPML set for the fused (ping-pong) step
     L.fields2 = take(6 * ncell * sizeof(float2));
     L.psi_h2 = take((2 * plane * 2 * d.pml_z + 2 * (size_t)(d.pml_r_in + d.pml_r_out) * np * nz) * sizeof(float2));
@@ -218,6 +243,10 @@ static void compute_layout(zda_zone &z)
     L.cr_n = take((nr + 1) * sizeof(float));
     L.br_h = take(nr * sizeof(float));
     L.cr_h = take(nr * sizeof(float));
+    L.bm_n = take((nr + 1) * sizeof(float));
+    L.cm_n = take((nr + 1) * sizeof(float));
+    L.bm_h = take(nr * sizeof(float));
+    L.cm_h = take(nr * sizeof(float));
     L.bz_n = take((nz + 1) * sizeof(float));
     L.cz_n = take((nz + 1) * sizeof(float));
     L.bz_h = take(nz * sizeof(float));
@@ -279,13 +308,17 @@ static zda_status upload(zda_zone &z)
         for (int k = 0; k <= nz; ++k) zn[k] = k * d.dz;
         for (int k = 0; k < nz; ++k) zh[k] = (k + 0.5) * d.dz;
         const double rhi = d.r_lo + nr * d.dr, zhi = nz * d.dz;
-        std::vector<float> b, c;
-        cpml_table(z, d.r_lo, rhi, d.pml_r_in, d.pml_r_out, d.dr, rn, b, c);
+        std::vector<float> b, c, bm, cm;
+        cpml_table(z, d.r_lo, rhi, d.pml_r_in, d.pml_r_out, d.dr, rn, b, c, z.rpml, &bm, &cm);
         CUDA_TRY(put(z.L.br_n, b.data(), b.size() * 4));
         CUDA_TRY(put(z.L.cr_n, c.data(), c.size() * 4));
-        cpml_table(z, d.r_lo, rhi, d.pml_r_in, d.pml_r_out, d.dr, rh, b, c);
+        CUDA_TRY(put(z.L.bm_n, bm.data(), bm.size() * 4));
+        CUDA_TRY(put(z.L.cm_n, cm.data(), cm.size() * 4));
+        cpml_table(z, d.r_lo, rhi, d.pml_r_in, d.pml_r_out, d.dr, rh, b, c, z.rpml, &bm, &cm);
         CUDA_TRY(put(z.L.br_h, b.data(), b.size() * 4));
         CUDA_TRY(put(z.L.cr_h, c.data(), c.size() * 4));
+        CUDA_TRY(put(z.L.bm_h, bm.data(), bm.size() * 4));
+        CUDA_TRY(put(z.L.cm_h, cm.data(), cm.size() * 4));
         cpml_table(z, 0.0, zhi, d.pml_z, d.pml_z, d.dz, zn, b, c);
         CUDA_TRY(put(z.L.bz_n, b.data(), b.size() * 4));
         CUDA_TRY(put(z.L.cz_n, c.data(), c.size() * 4));
@@ -509,6 +542,7 @@ static zda::StepParams step_params(zda_zone &z)
     p.nr = d.n_r; p.nphi = d.n_phi; p.nz = d.n_z;
     p.pr_in = d.pml_r_in; p.pr_out = d.pml_r_out; p.pz = d.pml_z;
     p.bor = d.n_fold == 0 ? 1 : 0;
+    p.rpml_metric = z.rpml;
     p.m = (float)d.m;
     p.dt = (float)z.dt;
     p.inv_dr = (float)(1.0 / d.dr); p.inv_dz = (float)(1.0 / d.dz); p.inv_dphi = (float)(1.0 / z.dphi);
@@ -522,6 +556,9 @@ static zda::StepParams step_params(zda_zone &z)
     const size_t nrs = (size_t)(d.pml_r_in + d.pml_r_out) * d.n_phi * d.n_z;
     float2 *R = P<float2>(z, z.L.psi_r);
     p.psi = Psi{Z, Z + nzs, R, R + nrs, Z + 2 * nzs, Z + 3 * nzs, R + 2 * nrs, R + 3 * nrs};
+    float2 *M = P<float2>(z, z.L.psi_m);
+    p.rm = Metric{P<float>(z, z.L.bm_n), P<float>(z, z.L.cm_n), P<float>(z, z.L.bm_h), P<float>(z, z.L.cm_h),
+                  M, M + nrs, M + 2 * nrs, M + 3 * nrs};
     p.t = Tables{P<float>(z, z.L.inv_r_n), P<float>(z, z.L.inv_r_h), P<float>(z, z.L.br_n),
                  P<float>(z, z.L.cr_n), P<float>(z, z.L.br_h), P<float>(z, z.L.cr_h), P<float>(z, z.L.bz_n),
                  P<float>(z, z.L.cz_n), P<float>(z, z.L.bz_h), P<float>(z, z.L.cz_h), P<float>(z, z.L.a_n),
@@ -574,7 +611,7 @@ static zda_status clear_state(zda_zone &z, cudaStream_t s)
 {
     CUDA_TRY(cudaMemsetAsync(P<int>(z, z.L.status) + 1, 0, sizeof(int), s));         // wait-timeout word
     CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields, 0, z.L.psi_r - z.L.fields, s));      // fields, psi_z
-    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.psi_r, 0, z.L.fields2 - z.L.psi_r, s));      // psi_r
+    CUDA_TRY(cudaMemsetAsync(z.ws + z.L.psi_r, 0, z.L.fields2 - z.L.psi_r, s));      // psi_r, psi_m
     if (z.variant == 1) {                                                             // fields2, psi_h2
         CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields2, 0, z.L.mon - z.L.fields2, s));
     }
@@ -1073,6 +1110,7 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
     z->pair_kernels = true;
     if (variant == 1) {
         if (z->d.n_fold == 0) return fail(ZDA_ERR_ARG, "the axis zone (continuous axisymmetry) uses the split step");
+        if (z->rpml) return fail(ZDA_ERR_ARG, "the fused step implements the real-radius r-PML only");
         if (tile_phi != 2 && tile_phi != 4) return fail(ZDA_ERR_ARG, "fused step: tile_phi must be 2 or 4");
         if (z->d.n_z > zda::fused_max_nz()) return fail(ZDA_ERR_ARG, "fused step supports n_z <= 256");
         if (z->d.n_z % 2) return fail(ZDA_ERR_ARG, "fused step needs an even n_z (16-byte bulk copies)");
@@ -1081,6 +1119,25 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
     z->tile_phi = tile_phi;
     z->i_ranges = i_ranges;
     z->have_forward = false;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_set_radial_pml(zda_zone *z, int form)
+{
+    if (!z || (form != 0 && form != 1)) return fail(ZDA_ERR_ARG, "r-PML form must be 0 or 1");
+    if (form == 1 && z->variant == 1) return fail(ZDA_ERR_ARG, "the fused step implements the real-radius r-PML only");
+    if (z->rpml != form) {
+        z->rpml = form;
+        z->tables_dirty = true;
+        z->have_forward = false;
+    }
+    return ZDA_OK;
+}
+
+zda_status zda_zone_get_radial_pml(const zda_zone *z, int *form)
+{
+    if (!z || !form) return fail(ZDA_ERR_ARG, "null argument");
+    *form = z->rpml;
     return ZDA_OK;
 }
 
@@ -1211,7 +1268,7 @@ static size_t lens_ws_total(const zda_lens &L) { return lens_ws_status(L) + 256;
 static std::vector<long long> zone_stamp(const zda_zone &z)
 {
     return {(long long)(uintptr_t)z.ws, z.variant, z.pair_kernels, z.tile_phi, z.i_ranges, z.d.n_steps, z.nq,
-            z.wait_limit, z.inject_timeout, (long long)z.lambda.size()};
+            z.wait_limit, z.inject_timeout, (long long)z.lambda.size(), z.rpml};
 }
 
 static bool stamps_match(const zda_lens &L, const std::vector<std::vector<long long>> &st)

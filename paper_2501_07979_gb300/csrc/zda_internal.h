@@ -3,6 +3,7 @@
 //   fields       E_r, E_phi, E_z, H_r, H_phi, H_z: [n_r][n_phi][n_z], z fastest
 //   z-CPML psi   [n_r][n_phi][2 pml_z]        (lower slab, then upper slab)
 //   r-CPML psi   [pml_r_in + pml_r_out][n_phi][n_z]
+//   metric psi   [pml_r_in + pml_r_out][n_phi][n_z]   (stretched-radius r-PML, H_r H_z E_r E_z)
 //   monitor DFT  [Q][2][n_r][n_phi]
 //   design DFT   [Q][3][n_r][n_phi][nk]      (nk design planes fastest)
 #pragma once
@@ -66,6 +67,11 @@ struct Tables {
 
 struct Fields { float2 *Er, *Ep, *Ez, *Hr, *Hp, *Hz; };
 struct Psi { float2 *hr_z, *hp_z, *hp_r, *hz_r, *er_z, *ep_z, *ep_r, *ez_r; };
+// Stretched-coordinate r-PML: 1/r~ recursion tables and metric auxiliaries.
+struct Metric {
+    const float *bm_n, *cm_n, *bm_h, *cm_h;    // at r nodes / half nodes (0: r~ = r)
+    float2 *hr, *hz, *er, *ez;                 // [pml_r_in + pml_r_out][n_phi][n_z]
+};
 
 enum { SRC_NONE = 0, SRC_PLANE_WAVE = 1, SRC_ADJOINT = 2 };
 
@@ -91,6 +97,11 @@ struct StepParams {
     float2 *mon;
     int des_k0, des_nk;                        // des_nk == 0: no design DFT
     float2 *des;
+    // r-PML form: 0 = CPML on the whole (1/r) d/dr (r .) term, real-radius
+    // metric; 1 = stretched coordinates: inside the r-PML only the derivative
+    // part is stretched and the metric parts are divided by r~ (rm tables)
+    int rpml_metric;
+    Metric rm;
 };
 
 // kernels (zda_kernels.cu)

@@ -11,6 +11,13 @@
 // slabs; the plane-wave / adjoint sources and the running DFTs are fused
 // into the E update.
 //
+// Stretched-coordinate r-PML (rpml_metric = 1): inside the r-PML the z-curls'
+// (1/r) d/dr (r F) = (F(i+1) - F(i))/dr + (F(i+1) + F(i))/(2 r) is split; only
+// the derivative carries the CPML stretch, and the metric part
+// X = (F(i+1) + F(i))/2 -+ dF/dphi (and the phi-derivative of the r-curls) is
+// divided by the stretched radius through 1/r~ = (1/r)(X + psi_m),
+// psi_m <- bm psi_m + cm X (bm = cm = 0 where r~ = r, the inner slab).
+//
 // Continuous axisymmetry (the axis zone, one phi cell): every (1/r) d/dphi
 // is i m / r times the local value.  On the axis (r_lo = 0) the table entry
 // 1/r_0 is 0, so H_r(0) keeps its value 0; E_z(0) and E_phi(0) are not
@@ -66,11 +73,20 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_h(const StepParams p
     const int kz = zslab(k, nz, p.pz);
     const int ir = rslab(i, p.nr, p.pr_in, p.pr_out);
     const float dt = p.dt;
+    const bool sr = p.rpml_metric && ir >= 0;          // stretched r-PML column (uniform per block)
+    const size_t rx = ((size_t)(ir >= 0 ? ir : 0) * nphi + j) * nz + k;
 
     // H_r(i, j+1/2, k+1/2): (1/r) dE_z/dphi - dE_phi/dz
     {
-        const float2 dph = p.bor ? c_scale(make_float2(-ez.y, ez.x), p.m * irn)
-                                 : c_scale(c_sub(ez_jp, ez), irn * p.inv_dphi);
+        float2 dph;
+        if (sr) {
+            const float2 X = p.bor ? c_scale(make_float2(-ez.y, ez.x), p.m) : c_scale(c_sub(ez_jp, ez), p.inv_dphi);
+            const float2 pm = c_add(c_scale(p.rm.hr[rx], __ldg(p.rm.bm_n + i)), c_scale(X, __ldg(p.rm.cm_n + i)));
+            p.rm.hr[rx] = pm;
+            dph = c_scale(c_add(X, pm), irn);
+        } else {
+            dph = p.bor ? c_scale(make_float2(-ez.y, ez.x), p.m * irn) : c_scale(c_sub(ez_jp, ez), irn * p.inv_dphi);
+        }
         float2 dz = c_scale(c_sub(ep_kp, ep), p.inv_dz);
         if (kz >= 0) {
             const size_t ix = ((size_t)i * nphi + j) * (2 * p.pz) + kz;
@@ -102,7 +118,18 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_h(const StepParams p
     }
     // H_z(i+1/2, j+1/2, k): (1/r) d(r E_phi)/dr - (1/r) dE_r/dphi
     //   (r_{i+1} E(i+1) - r_i E(i)) / (r_{i+1/2} dr) = (E(i+1)-E(i))/dr + (E(i+1)+E(i)) / (2 r_{i+1/2})
-    {
+    if (sr) {
+        float2 drr = c_scale(c_sub(ep_ip, ep), p.inv_dr);
+        const float2 ps = c_add(c_scale(p.psi.hz_r[rx], __ldg(p.t.br_h + i)), c_scale(drr, __ldg(p.t.cr_h + i)));
+        p.psi.hz_r[rx] = ps;
+        drr = c_add(drr, ps);
+        const float2 X = c_sub(c_scale(c_add(ep_ip, ep), 0.5f),
+                               p.bor ? c_scale(make_float2(-er.y, er.x), p.m) : c_scale(c_sub(er_jp, er), p.inv_dphi));
+        const float2 pm = c_add(c_scale(p.rm.hz[rx], __ldg(p.rm.bm_h + i)), c_scale(X, __ldg(p.rm.cm_h + i)));
+        p.rm.hz[rx] = pm;
+        const float2 h = p.f.Hz[c];
+        p.f.Hz[c] = c_sub(h, c_scale(c_add(drr, c_scale(c_add(X, pm), irh)), dt));
+    } else {
         float2 drr = c_add(c_scale(c_sub(ep_ip, ep), p.inv_dr), c_scale(c_add(ep_ip, ep), 0.5f * irh));
         const float2 dph = p.bor ? c_scale(make_float2(-er.y, er.x), p.m * irh)
                                  : c_scale(c_sub(er_jp, er), irh * p.inv_dphi);
@@ -150,6 +177,8 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_e(const StepParams p
     const int ir = rslab(i, nr, p.pr_in, p.pr_out);
     const float dt = p.dt;
     const size_t ij = (size_t)i * nphi + j;
+    const bool sr = p.rpml_metric && ir >= 0;          // stretched r-PML column (uniform per block)
+    const size_t rx = ((size_t)(ir >= 0 ? ir : 0) * nphi + j) * nz + k;
 
     float2 jr = zero, jp = zero;
     if (k == p.src_k) {
@@ -175,8 +204,15 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_e(const StepParams p
     float2 er = p.f.Er[c], ep = p.f.Ep[c], ez = p.f.Ez[c];
     // E_r(i+1/2, j, k): (1/r) dH_z/dphi - dH_phi/dz ; PEC at k = 0
     if (k > 0) {
-        const float2 dph = p.bor ? c_scale(make_float2(-hz.y, hz.x), p.m * irh)
-                                 : c_scale(c_sub(hz, hz_jm), irh * p.inv_dphi);
+        float2 dph;
+        if (sr) {
+            const float2 X = p.bor ? c_scale(make_float2(-hz.y, hz.x), p.m) : c_scale(c_sub(hz, hz_jm), p.inv_dphi);
+            const float2 pm = c_add(c_scale(p.rm.er[rx], __ldg(p.rm.bm_h + i)), c_scale(X, __ldg(p.rm.cm_h + i)));
+            p.rm.er[rx] = pm;
+            dph = c_scale(c_add(X, pm), irh);
+        } else {
+            dph = p.bor ? c_scale(make_float2(-hz.y, hz.x), p.m * irh) : c_scale(c_sub(hz, hz_jm), irh * p.inv_dphi);
+        }
         float2 dz = c_scale(c_sub(hp, hp_km), p.inv_dz);
         if (kz >= 0) {
             const size_t ix = ij * (2 * p.pz) + kz;
@@ -210,7 +246,19 @@ __global__ void __launch_bounds__(ZDA_BX * ZDA_BY) k_update_e(const StepParams p
     }
     // E_z(i, j, k+1/2): (1/r) d(r H_phi)/dr - (1/r) dH_r/dphi ; PEC at i = 0
     //   (r_{i+1/2} H(i+1/2) - r_{i-1/2} H(i-1/2)) / (r_i dr) = (H - H_im)/dr + (H + H_im) / (2 r_i)
-    if (i > 0) {
+    if (i > 0 && sr) {
+        float2 drr = c_scale(c_sub(hp, hp_im), p.inv_dr);
+        const float2 ps = c_add(c_scale(p.psi.ez_r[rx], __ldg(p.t.br_n + i)), c_scale(drr, __ldg(p.t.cr_n + i)));
+        p.psi.ez_r[rx] = ps;
+        drr = c_add(drr, ps);
+        const float2 X = c_sub(c_scale(c_add(hp, hp_im), 0.5f),
+                               p.bor ? c_scale(make_float2(-hr.y, hr.x), p.m) : c_scale(c_sub(hr, hr_jm), p.inv_dphi));
+        const float2 pm = c_add(c_scale(p.rm.ez[rx], __ldg(p.rm.bm_n + i)), c_scale(X, __ldg(p.rm.cm_n + i)));
+        p.rm.ez[rx] = pm;
+        const float ie = 1.0f / (__ldg(p.t.a_c + k) + __ldg(p.t.d_c + k) * __ldg(p.rb_z + ij));
+        ez = c_add(ez, c_scale(c_add(drr, c_scale(c_add(X, pm), irn)), dt * ie));
+        p.f.Ez[c] = ez;
+    } else if (i > 0) {
         float2 drr = c_add(c_scale(c_sub(hp, hp_im), p.inv_dr), c_scale(c_add(hp, hp_im), 0.5f * irn));
         const float2 dph = p.bor ? c_scale(make_float2(-hr.y, hr.x), p.m * irn)
                                  : c_scale(c_sub(hr, hr_jm), irn * p.inv_dphi);

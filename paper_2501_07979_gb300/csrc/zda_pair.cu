@@ -8,7 +8,12 @@
 // bandwidth with traffic equal to the algorithmic bytes).  The z-neighbour
 // outside the pair comes from one extra 8-byte load (an L1 hit).  Needs an
 // even n_z and an even z-PML width, so that a pair never straddles a CPML
-// slab boundary; otherwise the one-cell kernels run.
+// slab boundary; otherwise the one-cell kernels run.  Stretched-coordinate
+// r-PML columns (rpml_metric = 1, uniform per block since blockIdx.z = i)
+// take the split radial curl and the 1/r~ recursion of k_update_h / k_update_e;
+// that code is compiled only into the RM = true instances (the H kernel at
+// 3 blocks per SM, 80 registers), so the default form keeps its budget of
+// 64 registers at 4 blocks per SM without spilling.
 #include "zda_internal.h"
 
 namespace zda {
@@ -44,7 +49,8 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-__global__ void __launch_bounds__(PX * PY, 4) k_update_h_pair(const StepParams p)
+template <bool RM>
+__global__ void __launch_bounds__(PX * PY, RM ? 3 : 4) k_update_h_pair(const StepParams p)
 {
     const int kp = blockIdx.x * PX + threadIdx.x;
     const int j = blockIdx.y * PY + threadIdx.y;
@@ -94,6 +100,48 @@ __global__ void __launch_bounds__(PX * PY, 4) k_update_h_pair(const StepParams p
     if (ir >= 0) { ps_pr = ld4rw(p.psi.hp_r + rx); ps_zr = ld4rw(p.psi.hz_r + rx); }
     float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
     float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
+    const bool sr = RM && ir >= 0;
+    if (sr) {                                   // stretched-coordinate r-PML column
+        C2 pm_r = ld4rw(p.rm.hr + rx), pm_z = ld4rw(p.rm.hz + rx);
+        float2 *MR[2] = {&pm_r.a, &pm_r.b}, *MZ[2] = {&pm_z.a, &pm_z.b};
+        const float bmn = __ldg(p.rm.bm_n + i), cmn = __ldg(p.rm.cm_n + i);
+        const float bmh = __ldg(p.rm.bm_h + i), cmh = __ldg(p.rm.cm_h + i);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            {                                   // H_r
+                const float2 X = c_scale(c_sub(EZJ[u], EZ[u]), p.inv_dphi);
+                *MR[u] = c_add(c_scale(*MR[u], bmn), c_scale(X, cmn));
+                const float2 dph = c_scale(c_add(X, *MR[u]), irn);
+                float2 dz = c_scale(c_sub(EP[u + 1], EP[u]), p.inv_dz);
+                if (kz >= 0) {
+                    *PR[u] = c_add(c_scale(*PR[u], bzh[u]), c_scale(dz, czh[u]));
+                    dz = c_add(dz, *PR[u]);
+                }
+                *HR[u] = c_sub(*HR[u], c_scale(c_sub(dph, dz), dt));
+            }
+            {                                   // H_phi
+                float2 dz = c_scale(c_sub(ER[u + 1], ER[u]), p.inv_dz);
+                float2 drr = c_scale(c_sub(EZI[u], EZ[u]), p.inv_dr);
+                if (kz >= 0) {
+                    *PP[u] = c_add(c_scale(*PP[u], bzh[u]), c_scale(dz, czh[u]));
+                    dz = c_add(dz, *PP[u]);
+                }
+                *PPR[u] = c_add(c_scale(*PPR[u], brh), c_scale(drr, crh));
+                drr = c_add(drr, *PPR[u]);
+                *HP[u] = c_sub(*HP[u], c_scale(c_sub(dz, drr), dt));
+            }
+            {                                   // H_z: stretched derivative + metric part / r~
+                float2 drr = c_scale(c_sub(EPI[u], EP[u]), p.inv_dr);
+                *PZR[u] = c_add(c_scale(*PZR[u], brh), c_scale(drr, crh));
+                drr = c_add(drr, *PZR[u]);
+                const float2 X = c_sub(c_scale(c_add(EPI[u], EP[u]), 0.5f), c_scale(c_sub(ERJ[u], ER[u]), p.inv_dphi));
+                *MZ[u] = c_add(c_scale(*MZ[u], bmh), c_scale(X, cmh));
+                *HZ[u] = c_sub(*HZ[u], c_scale(c_add(drr, c_scale(c_add(X, *MZ[u]), irh)), dt));
+            }
+        }
+        st4(p.rm.hr + rx, pm_r);
+        st4(p.rm.hz + rx, pm_z);
+    } else {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         // H_r
@@ -131,6 +179,7 @@ __global__ void __launch_bounds__(PX * PY, 4) k_update_h_pair(const StepParams p
             *HZ[u] = c_sub(*HZ[u], c_scale(c_sub(drr, dph), dt));
         }
     }
+    }
     st4(p.f.Hr + c, hr);
     st4(p.f.Hp + c, hp);
     st4(p.f.Hz + c, hz);
@@ -138,6 +187,7 @@ __global__ void __launch_bounds__(PX * PY, 4) k_update_h_pair(const StepParams p
     if (ir >= 0) { st4(p.psi.hp_r + rx, ps_pr); st4(p.psi.hz_r + rx, ps_zr); }
 }
 
+template <bool RM>
 __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p, const int n)
 {
     const int kp = blockIdx.x * PX + threadIdx.x;
@@ -184,6 +234,16 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
     float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
     const float rbr = __ldg(p.rb_r + ij), rbp = __ldg(p.rb_p + ij), rbz = __ldg(p.rb_z + ij);
     const float brn = ir >= 0 ? __ldg(p.t.br_n + i) : 0.f, crn = ir >= 0 ? __ldg(p.t.cr_n + i) : 0.f;
+    const bool sr = RM && ir >= 0;                     // stretched-coordinate r-PML column
+    C2 pm_r = C2{zero, zero}, pm_z = C2{zero, zero};
+    float bmn = 0.f, cmn = 0.f, bmh = 0.f, cmh = 0.f;
+    if (sr) {
+        pm_r = ld4rw(p.rm.er + rx);
+        pm_z = ld4rw(p.rm.ez + rx);
+        bmn = __ldg(p.rm.bm_n + i); cmn = __ldg(p.rm.cm_n + i);
+        bmh = __ldg(p.rm.bm_h + i); cmh = __ldg(p.rm.cm_h + i);
+    }
+    float2 *MER[2] = {&pm_r.a, &pm_r.b}, *MEZ[2] = {&pm_z.a, &pm_z.b};
 
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -202,7 +262,14 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
         }
         const float bzn = kz >= 0 ? __ldg(p.t.bz_n + kk) : 0.f, czn = kz >= 0 ? __ldg(p.t.cz_n + kk) : 0.f;
         if (kk > 0) {                                       // E_r
-            const float2 dph = c_scale(c_sub(HZ[u], HZJ[u]), irh * p.inv_dphi);
+            float2 dph;
+            if (sr) {
+                const float2 X = c_scale(c_sub(HZ[u], HZJ[u]), p.inv_dphi);
+                *MER[u] = c_add(c_scale(*MER[u], bmh), c_scale(X, cmh));
+                dph = c_scale(c_add(X, *MER[u]), irh);
+            } else {
+                dph = c_scale(c_sub(HZ[u], HZJ[u]), irh * p.inv_dphi);
+            }
             float2 dz = c_scale(c_sub(HP[u + 1], HP[u]), p.inv_dz);
             if (kz >= 0) {
                 *PR[u] = c_add(c_scale(*PR[u], bzn), c_scale(dz, czn));
@@ -225,7 +292,15 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
             const float ie = rcp_approx(__ldg(p.t.a_n + kk) + __ldg(p.t.d_n + kk) * rbp);
             *EP[u] = c_add(*EP[u], c_scale(c_sub(c_sub(dz, drr), jp), dt * ie));
         }
-        if (i > 0) {                                        // E_z
+        if (i > 0 && sr) {                                  // E_z, stretched r-PML column
+            float2 drr = c_scale(c_sub(HP[u + 1], HPI[u]), p.inv_dr);
+            *PZR[u] = c_add(c_scale(*PZR[u], brn), c_scale(drr, crn));
+            drr = c_add(drr, *PZR[u]);
+            const float2 X = c_sub(c_scale(c_add(HP[u + 1], HPI[u]), 0.5f), c_scale(c_sub(HRk[u + 1], HRJ[u]), p.inv_dphi));
+            *MEZ[u] = c_add(c_scale(*MEZ[u], bmn), c_scale(X, cmn));
+            const float ie = rcp_approx(__ldg(p.t.a_c + kk) + __ldg(p.t.d_c + kk) * rbz);
+            *EZ[u] = c_add(*EZ[u], c_scale(c_add(drr, c_scale(c_add(X, *MEZ[u]), irn)), dt * ie));
+        } else if (i > 0) {                                 // E_z
             float2 drr = c_add(c_scale(c_sub(HP[u + 1], HPI[u]), p.inv_dr),
                                c_scale(c_add(HP[u + 1], HPI[u]), 0.5f * irn));
             const float2 dph = c_scale(c_sub(HRk[u + 1], HRJ[u]), irn * p.inv_dphi);
@@ -242,6 +317,7 @@ __global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p
     st4(p.f.Ez + c, ez);
     if (kz >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
     if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
+    if (sr) { st4(p.rm.er + rx, pm_r); st4(p.rm.ez + rx, pm_z); }
 
     // history slot of the time-blocked DFT (entries as in dft_site)
     if (p.dft_hist && (p.des || p.mon)) {
@@ -369,13 +445,15 @@ bool pair_kernels_apply(const StepParams &p) { return p.nz % 2 == 0 && p.pz % 2 
 void launch_update_h_pair(const StepParams &p, cudaStream_t s)
 {
     dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
-    k_update_h_pair<<<g, b, 0, s>>>(p);
+    if (p.rpml_metric) k_update_h_pair<true><<<g, b, 0, s>>>(p);
+    else k_update_h_pair<false><<<g, b, 0, s>>>(p);
 }
 
 void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s)
 {
     dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
-    k_update_e_pair<<<g, b, 0, s>>>(p, n);
+    if (p.rpml_metric) k_update_e_pair<true><<<g, b, 0, s>>>(p, n);
+    else k_update_e_pair<false><<<g, b, 0, s>>>(p, n);
 }
 
 }  // namespace zda

@@ -185,6 +185,16 @@ class Zone:
         """Time-step kernel: variant 1 fused (tile_phi 2 or 4), 0 split H/E."""
         check(_lib.lib().zda_zone_set_kernel(self.handle, int(variant), int(tile_phi), int(i_ranges)))
 
+    def set_radial_pml(self, form):
+        """r-PML form: 0 convolutional PML with the real radius (default),
+        1 stretched coordinates (split radial curl, stretched outer radius)."""
+        check(_lib.lib().zda_zone_set_radial_pml(self.handle, int(form)))
+
+    def radial_pml(self):
+        f = ctypes.c_int()
+        check(_lib.lib().zda_zone_get_radial_pml(self.handle, ctypes.byref(f)))
+        return f.value
+
     def time_steps(self, steps):
         """Milliseconds for `steps` steps of the current step kernel (no
         source, no DFT); overwrites the fields."""
