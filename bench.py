@@ -39,10 +39,13 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
-    ap.add_argument("--workload", default="zone", choices=["zone", "lwir", "surrogate"],
+    ap.add_argument("--workload", default="zone", choices=["zone", "lwir", "rgb", "poly", "surrogate"],
                     help="zone: forward + adjoint FDTD iteration of the wide zone (headline); "
                          "lwir: the same on zone 16 of the paper's LWIR lens at its lambda/50 grid; "
+                         "rgb / poly: zone 16 of the paper's visible lenses at lambda/36; "
                          "surrogate: U-Net inference, 128 x 128 patches, batch 256")
+    ap.add_argument("--radial-pml", type=int, default=0, choices=[0, 1],
+                    help="r-PML form: 0 real-radius CPML (default), 1 stretched coordinates")
     ap.add_argument("--batch", type=int, default=256, help="surrogate workload: samples per forward")
     ap.add_argument("--kernel", default="default", choices=["default", "split", "split1", "fused2", "fused4"],
                     help="time-step kernel (default: the library's choice for the zone)")
@@ -53,11 +56,23 @@ WORKLOAD = "zone"
 
 
 def workload(n_steps):
-    from zda_inputs import zone_cfg2, zone_lwir
-    return zone_lwir(16, n_steps) if WORKLOAD == "lwir" else zone_cfg2(n_steps=n_steps)
+    from zda_inputs import zone_cfg2, zone_lwir, zone_visible
+    if WORKLOAD == "lwir":
+        return zone_lwir(16, n_steps)
+    if WORKLOAD in ("rgb", "poly"):
+        return zone_visible(16, WORKLOAD, n_steps)
+    return zone_cfg2(n_steps=n_steps)
 
 
 def config(spec, n_steps):
+    if WORKLOAD in ("rgb", "poly"):
+        return {"workload": "%s: %dx%dx%d cells, TiO2 on SiO2, %d wavelengths, forward+adjoint TopOpt iteration"
+                            % (spec.label, spec.n_r, spec.n_phi, spec.n_z, len(spec.wavelengths)),
+                "n_steps_per_run": n_steps, "cells": spec.cells, "runs_per_step": 2,
+                "design_pixels": spec.n_r_design * spec.n_phi,
+                "l2": "no flush: the %.0f MB field state fits in the 129 MB L2, and the time loop keeps it "
+                      "there as the real workload does; the HBM roofline fraction is not meaningful for this "
+                      "zone" % (spec.cells * 48 / 1e6)}
     if WORKLOAD == "lwir":
         return {"workload": "LWIR zone 16 of the paper's lens: r=[375,400] lambda, n=11520, lambda/50 grid, "
                             "%dx%dx%d cells, Si n=3.42, 1 wavelength, forward+adjoint TopOpt iteration"
@@ -247,6 +262,8 @@ def run_ours(a):
     kern = {"split": (0, 2, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0)}.get(a.kernel)
     if kern is not None:
         zone.set_kernel(*kern)
+    if a.radial_pml:
+        zone.set_radial_pml(a.radial_pml)
     variant, tile_phi, i_ranges = zone.get_kernel()
     rho = torch.tensor(rho_for(spec, 2 + rank), dtype=torch.float32, device="cuda:%d" % local)
     rho_host = rho.cpu().pin_memory()
@@ -353,7 +370,7 @@ def run_ours(a):
                          "sampled_launches": n_timed, "other_kernels": others},
             "step_kernel": {"variant": {0: "split, two z-cells per thread", 1: "fused",
                                         2: "split, one z-cell per thread"}[variant], "tile_phi": tile_phi,
-                            "i_ranges": i_ranges},
+                            "i_ranges": i_ranges, "radial_pml": zone.radial_pml()},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "focal_intensity": I}
     if not a.no_cpu_baseline:

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 import oracle as O
-from zda_inputs import zone_lwir, zone_cfg1, zone_cfg2, zone_tiny, smoothed_rho, rho_for
+from zda_inputs import zone_lwir, zone_visible, zone_cfg1, zone_cfg2, zone_tiny, smoothed_rho, rho_for
 
 pytestmark = pytest.mark.gpu
 
@@ -73,6 +73,8 @@ RAGGED = {
     "no_inner_pml": zone_tiny(pml_r_in=0, n_steps=200),
     # a 1-lambda strip of the paper's LWIR zone 16: lambda/50 grid, silicon, 11 phi cells
     "lwir_strip": zone_lwir(16, 1500).replace(n_r=66, r_lo=395.0),
+    # a 1-lambda strip of the paper's RGB zone 16: lambda/36, TiO2 on SiO2, three wavelengths
+    "rgb_strip": zone_visible(16, "rgb", 900).replace(n_r=52, r_lo=395.0),
 }
 
 

@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["ZoneSpec", "zone_cfg1", "zone_cfg2", "zone_tiny", "smoothed_rho",
+__all__ = ["ZoneSpec", "zone_cfg1", "zone_cfg2", "zone_tiny", "zone_lwir", "zone_visible", "smoothed_rho",
            "rho_for", "lens_zones", "focal_from_na"]
 
 
@@ -126,6 +126,39 @@ def zone_lwir(ell: int = 16, n_steps: int = 4000) -> ZoneSpec:
         filter_radius=0.08, beta=8.0, eta=0.5, wavelengths=(1.0,),
         pulse_sigma=0.5, pulse_t0=2.0, focal=focal_from_na(400.0, 0.3),
         label="LWIR zone %d: 25 lambda, lambda/50, n = %d" % (ell, 720 * ell))
+
+
+def zone_visible(ell: int = 16, lens: str = "rgb", n_steps: int = 4000) -> ZoneSpec:
+    """Zone l (2..32) of the paper's visible lenses at their lambda/36 grid
+    (section "Millimeter-scale poly-achromatic metalenses in the visible"),
+    lambda = the longest design wavelength:
+    rgb:  25 lambda zones, fold n = 360 l, wavelengths 0.74 / 0.81 / 1.0,
+          NA 0.8 (f = 600 lambda for the 800-lambda radius);
+    poly: 47 lambda zones, fold n = 1440 l, six wavelengths 490..650 nm
+          relative to 650 nm, NA 0.3.
+    TiO2 (n = 2.4) one wavelength thick (658 nm) on fused silica (n = 1.46);
+    conic filter radius 0.056 lambda; phi cells so that r dphi <= lambda/36 at
+    the zone's outer radius.  A throughput workload: the z stack (0.64 lambda
+    of substrate under the layer, the monitor 0.5 lambda above it, 8-cell
+    CPMLs) is this build's choice, as for the LWIR zone."""
+    if lens == "rgb":
+        width, fold, lams, na = 25.0, 360 * ell, (0.74, 0.81, 1.0), 0.8
+    elif lens == "poly":
+        width, fold, lams, na = 47.0, 1440 * ell, tuple(round(w / 650.0, 4) for w in (490, 520, 540, 570, 610, 650)), 0.3
+    else:
+        raise ValueError("lens must be 'rgb' or 'poly'")
+    h = 1.0 / 36.0
+    n_phi = int(np.ceil(width * ell * 2 * np.pi / fold / h))
+    k_layer, k_top = 8 + 23, 8 + 23 + 36
+    return ZoneSpec(
+        r_lo=width * (ell - 1) - 8 * h, n_r=int(round(width * 36)) + 16, n_phi=n_phi, n_z=k_top + 18 + 8 + 7,
+        n_fold=fold, dr=h, dz=h, pml_r_in=8, pml_r_out=8, pml_z=8,
+        layer_k0=(0, k_layer, k_top), layer_eps=(1.46 ** 2, 1.0, 1.0),
+        design_k0=k_layer, design_k1=k_top, eps_lo=1.0, eps_hi=2.4 ** 2,
+        source_k=14, monitor_k=k_top + 18, courant=0.5, n_steps=n_steps,
+        filter_radius=0.056, beta=8.0, eta=0.5, wavelengths=lams,
+        pulse_sigma=0.4, pulse_t0=1.6, focal=focal_from_na(32 * width, na),
+        label="%s zone %d: %g lambda, lambda/36, n = %d" % (lens, ell, width, fold))
 
 
 def zone_tiny(**kw) -> ZoneSpec:
