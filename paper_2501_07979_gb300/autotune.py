@@ -3,8 +3,10 @@
 For each candidate (variant, phi rows per block, radius ranges) the zone's
 step kernel is timed on the GPU for a few steps (`Zone.time_steps`); the
 fastest is applied to the zone and remembered in a JSON cache keyed by the
-zone's shape (n_r, n_phi, n_z, PML widths), so zones of the same shape in a
-lens (and later runs) reuse it without timing again.
+zone's shape (n_r, n_phi, n_z, PML widths) and r-PML form, so zones of the
+same shape in a lens (and later runs) reuse it without timing again.
+Candidates the zone refuses (the fused step with the stretched r-PML) are
+skipped.
 """
 import json
 import os
@@ -31,7 +33,7 @@ def tune_zone(zone, steps=40, cache_path=None, use_cache=True):
     (choice, {choice: ms}) with choice = (variant, tile_phi, i_ranges)."""
     from ._lib import ZdaError
     path = cache_path or DEFAULT_CACHE
-    key = shape_key(zone.spec)
+    key = shape_key(zone.spec) + "_rpml%d" % zone.radial_pml()
     cache = {}
     if use_cache and os.path.exists(path):
         try:
