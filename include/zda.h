@@ -331,6 +331,22 @@ zda_status zda_lens_focal_plane(zda_lens *lens, const double *pts_dev, int n_pts
 zda_status zda_lens_field_points(zda_lens *lens, const double *pts_dev, int n_pts, int n_phi_samples,
                                  double *field_dev, void *stream);
 
+/* Estimate of what the lens-field transforms above neglect for one zone
+ * (host only, no device work).  They keep the azimuthal orders +-1 of the
+ * zone's near field; the wedge's other orders m + j n (j != 0) reach a point
+ * at distance rho from the axis through Bessel functions J_L(x) with
+ * abs(L) >= n - 2 and x <= k r_hi rho / z_f (first order in r rho / R),
+ * k = 2 pi n_top / lambda_min, r_hi the zone's outer radius, z_f the point's
+ * distance from the monitor plane (focal - monitor height above the design
+ * top, + h for (x, y, h) points).  *bound_host = max over the points of
+ * (x/2)^nu / Gamma(nu + 1) >= abs(J_nu(x)), nu = max(n - 2, 0): a bound on
+ * the neglected orders' kernel relative to the kept one's; 0 for continuous
+ * axisymmetry (nothing neglected); HUGE_VAL for a point at or below the
+ * monitor plane.  pts_host: n_pts points of `stride` doubles, stride 2
+ * (x, y) or 3 (x, y, h). */
+zda_status zda_zone_order_bound(const zda_zone_desc *desc, const double *lambda_host, int n_lambda,
+                                const double *pts_host, int n_pts, int stride, double *bound_host);
+
 /* Thread-local message of the last error ("" if none). */
 const char *zda_last_error(void);
 

@@ -95,6 +95,7 @@ SIGNATURES = {
     "zda_lens_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_lens_focal_plane": (_i, [_vp, _vp, _i, _i, _vp, _dp, _vp]),
     "zda_lens_field_points": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "zda_zone_order_bound": (_i, [_vp, _vp, _i, _vp, _i, _i, ctypes.POINTER(ctypes.c_double)]),
     "zda_last_error": (ctypes.c_char_p, []),
     "zda_focal_transform_nn": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp]),
     "zda_focal_transform_nn_transpose": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp]),

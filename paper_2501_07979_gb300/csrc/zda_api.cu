@@ -1527,6 +1527,41 @@ static zda_status lens_field(zda_lens *L, const double *pts_dev, int pstride, in
     return ZDA_OK;
 }
 
+zda_status zda_zone_order_bound(const zda_zone_desc *d, const double *lambda_host, int n_lambda,
+                                const double *pts_host, int n_pts, int stride, double *bound_host)
+{
+    if (!d || !lambda_host || n_lambda < 1 || !pts_host || n_pts < 1 || (stride != 2 && stride != 3) || !bound_host)
+        return fail(ZDA_ERR_ARG, "bad argument");
+    double lmin = lambda_host[0];
+    for (int l = 1; l < n_lambda; ++l) lmin = std::min(lmin, lambda_host[l]);
+    if (!(lmin > 0)) return fail(ZDA_ERR_ARG, "wavelengths must be positive");
+    if (d->n_fold == 0) {                       // continuous axisymmetry: no other orders
+        *bound_host = 0.0;
+        return ZDA_OK;
+    }
+    const double k = 2.0 * M_PI * std::sqrt(layer_eps_at(*d, d->monitor_k)) / lmin;
+    const double r_hi = d->r_lo + d->n_r * d->dr;
+    const double zf0 = d->focal - (d->monitor_k * d->dz - d->design_k1 * d->dz);
+    const double nu = std::max(d->n_fold - 2, 0);
+    double worst = 0.0;
+    for (int t = 0; t < n_pts; ++t) {
+        const double *q = pts_host + (size_t)t * stride;
+        const double zf = zf0 + (stride == 3 ? q[2] : 0.0);
+        if (!(zf > 0)) {
+            worst = HUGE_VAL;
+            break;
+        }
+        const double x = k * r_hi * std::hypot(q[0], q[1]) / zf;
+        double b;
+        if (nu == 0) b = 1.0;
+        else if (x <= 0) b = 0.0;
+        else b = std::exp(std::min(nu * std::log(0.5 * x) - std::lgamma(nu + 1.0), 700.0));
+        worst = std::max(worst, b);
+    }
+    *bound_host = worst;
+    return ZDA_OK;
+}
+
 zda_status zda_lens_focal_plane(zda_lens *L, const double *pts_dev, int n_pts, int n_phi_samples, double *field_dev,
                                 double *p_trans_host, void *stream)
 {

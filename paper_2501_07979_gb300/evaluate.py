@@ -76,7 +76,8 @@ def evaluate_lens(lens, lens_radius, focal, incident, n_top=1.0, n_rad=48, n_ang
         res.append({"lambda": float(lam[l]), "fwhm": w, "focal_intensity": float(I0),
                     "focusing_efficiency": p_disc / p_inc, "relative_efficiency": p_disc / p_trans[l],
                     "transmittance": p_trans[l] / p_inc,
-                    "strehl": float(I0 * lam[l] ** 2 * focal ** 2 / (p_trans[l] * area))})
+                    "strehl": float(I0 * lam[l] ** 2 * focal ** 2 / (p_trans[l] * area)),
+                    "order_bound": lens.order_bound(pts)})
     return res, xs, I_line
 
 

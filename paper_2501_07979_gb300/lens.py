@@ -11,8 +11,28 @@ The zone solver is pluggable (any object with forward(rho) -> S and
 adjoint(dI_dS) -> grad): `Zone` on a GPU, or any stand-in.
 """
 import ctypes
+import warnings
 
 import numpy as np
+
+ORDER_BOUND_TOL = 1e-3
+
+
+def order_bound(spec, pts):
+    """Bound on the azimuthal orders the lens-field transforms neglect for
+    one zone at points (x, y) or (x, y, h) (zda_zone_order_bound)."""
+    from . import _lib
+    from ._lib import check
+    from .zone import make_desc
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64))
+    stride = pts.shape[-1]
+    pts = pts.reshape(-1, stride)
+    lam = np.ascontiguousarray(np.asarray(spec.wavelengths, dtype=np.float64))
+    d = make_desc(spec)
+    out = ctypes.c_double()
+    check(_lib.lib().zda_zone_order_bound(ctypes.byref(d), lam.ctypes.data, lam.size, pts.ctypes.data,
+                                          pts.shape[0], stride, ctypes.byref(out)))
+    return out.value
 
 
 def zone_cost(spec):
@@ -160,7 +180,18 @@ class Lens:
         check(_lib.lib().zda_lens_focal_plane(self.handle, ctypes.c_void_p(pts.data_ptr()), int(n), int(n_phi_samples),
                                               ctypes.c_void_p(out.data_ptr()), pt, self._stream()))
         o = out.cpu().numpy()
+        self._check_orders(pts_xy)
         return o[0, ..., 0] + 1j * o[0, ..., 1], o[1, ..., 0] + 1j * o[1, ..., 1], np.array(pt[:])
+
+    def order_bound(self, pts):
+        """Largest zda_zone_order_bound over the lens's zones at these points."""
+        return max(order_bound(z.spec, pts) for z in self.zones)
+
+    def _check_orders(self, pts):
+        b = self.order_bound(pts)
+        if b > ORDER_BOUND_TOL:
+            warnings.warn("lens field: the neglected azimuthal orders may reach %.2g of the kept ones at these "
+                          "points (zones with small n far off axis)" % b, RuntimeWarning, stacklevel=3)
 
     def field_points(self, pts_xyh, n_phi_samples=128):
         """Field of the last forward at points (x, y, h), h = height above the
@@ -175,4 +206,5 @@ class Lens:
         check(_lib.lib().zda_lens_field_points(self.handle, ctypes.c_void_p(pts.data_ptr()), int(n),
                                                int(n_phi_samples), ctypes.c_void_p(out.data_ptr()), self._stream()))
         o = out.cpu().numpy()
+        self._check_orders(np.asarray(pts_xyh, dtype=np.float64).reshape(-1, 3))
         return o[0, ..., 0] + 1j * o[0, ..., 1], o[1, ..., 0] + 1j * o[1, ..., 1]
