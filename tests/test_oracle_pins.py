@@ -380,6 +380,29 @@ def test_paper_focal_lengths_and_pixel_count():
     assert abs(n / p["pixels"] - 1) < p["rel_tol"]
 
 
+def test_paper_dof_ratio_and_zone_tiling():
+    """The wedge zones of the paper's lenses: with r dphi <= the grid step at
+    each zone's outer radius (zone_lwir, zone_visible), the LWIR lens has
+    ~10x the design degrees of freedom of its continuously axisymmetric
+    twin (zone 1 continuous, zones 2..16 with n_phi pixels per radial pixel);
+    the visible lenses' 32 zones tile their printed diameters."""
+    from zda_inputs import zone_lwir, zone_visible
+    gold = json.load(open(os.path.join(GOLDEN, "paper_numbers.json")))
+    g = gold["dof_ratio"]
+    zones = [zone_lwir(l, 10) for l in range(2, g["zones"] + 1)]
+    nrd = zones[0].n_r_design
+    assert nrd * zones[0].dr == pytest.approx(g["zone_width_lambda"])
+    dof_ring = nrd + sum(z.n_r_design * z.n_phi for z in zones)      # zone 1: one pixel per radius
+    ratio = dof_ring / (g["zones"] * nrd)
+    assert abs(ratio / g["ratio"] - 1) < g["rel_tol"], ratio
+    v = gold["visible_zone_counts"]
+    for lens in ("rgb", "poly"):
+        z = zone_visible(v[lens]["zones"], lens, 10)
+        outer = z.r_lo + (z.n_r - z.pml_r_out) * z.dr
+        assert abs(2 * outer / v[lens]["diameter_lambda"] - 1) < v["rel_tol"], (lens, outer)
+        assert z.n_r_design * z.dr == pytest.approx(v[lens]["zone_width_lambda"], rel=1e-3)
+
+
 def test_cfg1_geometry():
     """The single-zone workload: r dphi and the Courant step of the smallest
     azimuthal spacing; the r_lo * dphi bound must be the binding one."""
