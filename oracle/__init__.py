@@ -744,17 +744,29 @@ def focal_plane_bruteforce(spec, geom, mon, pts):
 
 def transmitted_power(spec, geom, mon):
     """(n/2) |E_t|^2 over the monitor annulus of the whole circle per
-    wavelength (plane-wave estimate of the transmitted flux)."""
+    wavelength (plane-wave estimate of the transmitted flux, section
+    "Results and Discussion": relative focusing efficiency).
+
+    The physical +w field is E+ + E- with E+ = psi(+w) (order m = +1) and
+    E- = conj(psi(-w)) (order -1).  Over the n wedge copies the cross term
+    2 Re(E+ conj(E-)) turns by e^{2 i tau} per copy and sums to zero for
+    n >= 3 (and over the circle for continuous axisymmetry), so the
+    full-circle sum is n sum_wedge (|E+|^2 + |E-|^2); for n = 1, 2 every copy
+    carries the same cross term and it stays."""
     s = spec
     nl = geom.n_lambda
     layer = np.searchsorted(np.asarray(s.layer_k0), s.monitor_k, side="right") - 1
     n_top = math.sqrt(s.layer_eps[layer])
     copies = 1.0 if geom.bor else float(s.n_fold)
+    cross = (not geom.bor) and s.n_fold <= 2
     out = np.zeros(nl)
     for l in range(nl):
-        Er = mon[l, 0] + np.conj(mon[l + nl, 0])
-        Ep = mon[l, 1] + np.conj(mon[l + nl, 1])
-        pw = (np.abs(Er) ** 2 + np.abs(Ep) ** 2).sum(axis=1)
+        if cross:
+            Er = mon[l, 0] + np.conj(mon[l + nl, 0])
+            Ep = mon[l, 1] + np.conj(mon[l + nl, 1])
+            pw = (np.abs(Er) ** 2 + np.abs(Ep) ** 2).sum(axis=1)
+        else:
+            pw = (np.abs(mon[l]) ** 2 + np.abs(mon[l + nl]) ** 2).sum(axis=(0, 2))
         i0, i1 = geom.i_d0, geom.i_d1
         out[l] = 0.5 * n_top * np.sum(pw[i0:i1] * geom.r_h[i0:i1] * s.dr * geom.dphi) * copies
     return out

@@ -1503,7 +1503,8 @@ static zda_status lens_field(zda_lens *L, const double *pts_dev, int pstride, in
     for (zda_zone *Z : L->zones) {
         const zda_zone_desc &d = Z->d;
         zda::launch_phi_means(P<float2>(*Z, Z->L.mon), P<double2>(*Z, Z->L.emph_n), P<double2>(*Z, Z->L.emph_h),
-                              Z->nq, d.n_r, d.n_phi, P<double2>(*Z, Z->L.umean), P<double>(*Z, Z->L.pt_row), s);
+                              Z->nq, d.n_r, d.n_phi, (d.n_fold == 1 || d.n_fold == 2) ? 1 : 0,
+                              P<double2>(*Z, Z->L.umean), P<double>(*Z, Z->L.pt_row), s);
         const double zf = d.focal - (d.monitor_k * d.dz - d.design_k1 * d.dz);
         zda::launch_focal_plane(P<double2>(*Z, Z->L.umean), P<double>(*Z, Z->L.qr), P<double>(*Z, Z->L.qw),
                                 P<double>(*Z, Z->L.qp), P<double>(*Z, Z->L.qwp), d.n_r, nl, pts_dev, pstride, n_pts, zf,

@@ -151,8 +151,9 @@ void launch_cell_gradient(const float *site_grad, int nr, int nphi, int nk, int 
                           float *g_t, cudaStream_t s);
 void launch_fill_status_check(const float *x, size_t n, int *status, cudaStream_t s);
 void launch_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, int *status, cudaStream_t s);
+// cross != 0 (n_fold 1 or 2): the transmitted intensity keeps the +-1 cross term
 void launch_phi_means(const float2 *mon, const double2 *emph_n, const double2 *emph_h, int nq, int nr, int nphi,
-                      double2 *umean, double *pt_row, cudaStream_t s);
+                      int cross, double2 *umean, double *pt_row, cudaStream_t s);
 void launch_focal_plane(const double2 *umean, const double *rr, const double *wr, const double *rp, const double *wp,
                         int nr, int nl, const double *pts, int pstride, int npts, double zf, const double *kk, int ns,
                         double2 *ex, double2 *ey, cudaStream_t s);

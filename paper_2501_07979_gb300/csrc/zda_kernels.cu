@@ -718,8 +718,15 @@ void launch_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, 
 // phi_{j+1/2}; no phase in the axis zone), and the transmitted-power density
 // sum over the row of |E_r|^2 + |E_phi|^2 of the physical phasor at +w_l,
 // Psi(+w) + conj(Psi(-w)).
+// Per radius and frequency: the phi-means of the monitor DFT (times the
+// e^{-i m phi} phases) and, per wavelength, sum_j of the transmitted
+// intensity.  The physical +w field is E+ + E- (E+ = psi(+w), E- =
+// conj(psi(-w))); over the n wedge copies the cross term 2 Re(E+ conj(E-))
+// turns by e^{2 i tau} per copy and cancels for n >= 3 (and for continuous
+// axisymmetry), so only abs(E+)^2 + abs(E-)^2 is summed; with cross != 0
+// (n = 1, 2) abs(E+ + E-)^2.
 __global__ void k_phi_means(const float2 *__restrict__ mon, const double2 *__restrict__ emph_n,
-                            const double2 *__restrict__ emph_h, int nq, int nr, int nphi, double2 *umean,
+                            const double2 *__restrict__ emph_h, int nq, int nr, int nphi, int cross, double2 *umean,
                             double *pt_row)
 {
     const int i = blockIdx.x, q = blockIdx.y;
@@ -738,9 +745,15 @@ __global__ void k_phi_means(const float2 *__restrict__ mon, const double2 *__res
         if (q < nl) {                                   // physical phasor at +w_q
             const float2 *er2 = mon + (size_t)(q + nl) * 2 * plane + (size_t)i * nphi;
             const float2 *ep2 = er2 + plane;
-            const double xr = (double)a.x + er2[j].x, yr = (double)a.y - er2[j].y;
-            const double xp = (double)b.x + ep2[j].x, yp = (double)b.y - ep2[j].y;
-            pw += xr * xr + yr * yr + xp * xp + yp * yp;
+            if (cross) {
+                const double xr = (double)a.x + er2[j].x, yr = (double)a.y - er2[j].y;
+                const double xp = (double)b.x + ep2[j].x, yp = (double)b.y - ep2[j].y;
+                pw += xr * xr + yr * yr + xp * xp + yp * yp;
+            } else {
+                const double c0 = er2[j].x, c1 = er2[j].y, c2 = ep2[j].x, c3 = ep2[j].y;
+                pw += (double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x + (double)b.y * b.y +
+                      c0 * c0 + c1 * c1 + c2 * c2 + c3 * c3;
+            }
         }
     }
     const double2 tr = block_sum2(sr);
@@ -756,10 +769,10 @@ __global__ void k_phi_means(const float2 *__restrict__ mon, const double2 *__res
 }
 
 void launch_phi_means(const float2 *mon, const double2 *emph_n, const double2 *emph_h, int nq, int nr, int nphi,
-                      double2 *umean, double *pt_row, cudaStream_t s)
+                      int cross, double2 *umean, double *pt_row, cudaStream_t s)
 {
     dim3 g(nr, nq);
-    k_phi_means<<<g, 256, 0, s>>>(mon, emph_n, emph_h, nq, nr, nphi, umean, pt_row);
+    k_phi_means<<<g, 256, 0, s>>>(mon, emph_n, emph_h, nq, nr, nphi, cross, umean, pt_row);
 }
 
 // Focal-plane field of one zone at points P = (x, y, z_f) above the monitor
