@@ -82,6 +82,21 @@ def test_invalid_arguments_return_status_not_crash(libpath):
     assert L.zda_last_error()
     assert L.zda_zone_query(None, None) == _lib.ERR_ARG
     assert L.zda_zone_launch_count(None) == -1
+    form = ctypes.c_int()
+    assert L.zda_zone_set_radial_pml(None, 1) == _lib.ERR_ARG
+    assert L.zda_zone_get_radial_pml(None, ctypes.byref(form)) == _lib.ERR_ARG
+    # the order bound is host-only: bad stride, no points, non-positive wavelengths
+    from paper_2501_07979_gb300.zone import make_desc
+    from zda_inputs import zone_tiny
+    d = make_desc(zone_tiny())
+    lam = (ctypes.c_double * 1)(1.0)
+    pts = (ctypes.c_double * 3)(0.5, 0.0, 0.0)
+    b = ctypes.c_double()
+    assert L.zda_zone_order_bound(ctypes.byref(d), lam, 1, pts, 1, 4, ctypes.byref(b)) == _lib.ERR_ARG
+    assert L.zda_zone_order_bound(ctypes.byref(d), lam, 1, pts, 0, 2, ctypes.byref(b)) == _lib.ERR_ARG
+    assert L.zda_zone_order_bound(ctypes.byref(d), (ctypes.c_double * 1)(0.0), 1, pts, 1, 2,
+                                  ctypes.byref(b)) == _lib.ERR_ARG
+    assert L.zda_zone_order_bound(ctypes.byref(d), lam, 1, pts, 1, 3, ctypes.byref(b)) == 0 and b.value > 0
 
 
 def test_surrogate_descriptor_checks_and_sizes_need_no_gpu(libpath):
