@@ -190,17 +190,20 @@ def dft_entries(spec):
     return plane * (spec.design_k1 - spec.design_k0 + 1) * 3 + plane * 2
 
 
-def algorithmic_bytes_e(spec, nq, with_dft=True, history=False):
+def algorithmic_bytes_e(spec, nq, with_dft=True, history=False, rpml=0):
     """Bytes the E-update launch must move per time step: read E and H (6 complex
     FP32 components), write E (3), the CPML auxiliaries in the slabs (read +
     write); with_dft: also the design-volume DFT (3 components x nq
     frequencies, read + write) and the monitor DFT (2 x nq); history: the
-    time-blocked DFT's history write of E at the DFT sites (8 B each)."""
+    time-blocked DFT's history write of E at the DFT sites (8 B each); rpml 1
+    (stretched r-PML): the E_r, E_z metric auxiliaries of the r-slabs."""
     cells = spec.cells
     plane = spec.n_r * spec.n_phi
     b = cells * 9 * 8
     b += 2 * spec.pml_z * plane * 2 * 16                          # E_r, E_phi z-psi
     b += (spec.pml_r_in + spec.pml_r_out) * spec.n_phi * spec.n_z * 2 * 16   # E_phi, E_z r-psi
+    if rpml:
+        b += (spec.pml_r_in + spec.pml_r_out) * spec.n_phi * spec.n_z * 2 * 16   # E_r, E_z metric psi
     if with_dft:
         b += plane * (spec.design_k1 - spec.design_k0 + 1) * 3 * nq * 16
         b += plane * 2 * nq * 16
@@ -234,11 +237,15 @@ def algorithmic_bytes_dft_flush(spec, nq, block=32):
     return dft_entries(spec) * (block * 8 + nq * 16)
 
 
-def algorithmic_bytes_h(spec):
+def algorithmic_bytes_h(spec, rpml=0):
+    """H update: read E and H, write H (72 B per cell), the z- and r-slab CPML
+    auxiliaries (read + write); rpml 1: the H_r, H_z metric auxiliaries."""
     plane = spec.n_r * spec.n_phi
     b = spec.cells * 9 * 8
     b += 2 * spec.pml_z * plane * 2 * 16
     b += (spec.pml_r_in + spec.pml_r_out) * spec.n_phi * spec.n_z * 2 * 16
+    if rpml:
+        b += (spec.pml_r_in + spec.pml_r_out) * spec.n_phi * spec.n_z * 2 * 16
     return b
 
 
@@ -332,6 +339,7 @@ def run_ours(a):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     # the library's sampled launches of one time step (see Zone.timing)
     avg = [m / max(n_timed, 1) for m in ms3]
+    rpml = zone.radial_pml()
     pair = variant == 0 and spec.n_z % 2 == 0 and spec.pml_z % 2 == 0
     if variant == 1:
         kernels = [("k_stream_step", algorithmic_bytes_stream(spec), avg[0]),
@@ -339,11 +347,12 @@ def run_ours(a):
     elif pair:
         # the DFT history is written by the E update; the flush (every 32 steps)
         # is timed on its own below
-        kernels = [("k_update_h_pair", algorithmic_bytes_h(spec), avg[0]),
-                   ("k_update_e_pair", algorithmic_bytes_e(spec, nq, with_dft=False, history=True), avg[1])]
+        kernels = [("k_update_h_pair", algorithmic_bytes_h(spec, rpml), avg[0]),
+                   ("k_update_e_pair", algorithmic_bytes_e(spec, nq, with_dft=False, history=True, rpml=rpml),
+                    avg[1])]
     else:
-        kernels = [("k_update_h", algorithmic_bytes_h(spec), avg[0]),
-                   ("k_update_e", algorithmic_bytes_e(spec, nq), avg[1])]
+        kernels = [("k_update_h", algorithmic_bytes_h(spec, rpml), avg[0]),
+                   ("k_update_e", algorithmic_bytes_e(spec, nq, rpml=rpml), avg[1])]
     per_step = {nm: t for nm, _, t in kernels}
     if pair:
         kernels.append(("k_dft_flush", algorithmic_bytes_dft_flush(spec, nq), avg[2]))
@@ -357,7 +366,7 @@ def run_ours(a):
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get(main_name)
+            traffic = None if rpml else json.load(open(tp)).get(main_name)   # captured on the default form
         except ValueError:
             traffic = None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
