@@ -8,7 +8,7 @@
  * annulus (2 transverse components x signed frequencies x re/im channels),
  * i.e. the near field that the focal transform of "Results and Discussion"
  * integrates.  The paper has no learned component: the plain FDTD solve of
- * zda.h stays the reference and the judge of the surrogate's error.
+ * zda.h stays the reference and the measure of the surrogate's error.
  *
  * Precision: bfloat16 weights, activations and activation gradients; FP32
  * accumulation in tensor memory (tcgen05.mma kind::f16); FP32 biases, head

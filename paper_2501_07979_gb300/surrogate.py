@@ -6,7 +6,7 @@ design annulus, the near field that the on-axis focal transform integrates.
 It is trained on the GPU by the library's own tensor-core kernels on data
 the FDTD solver generates, and serves only as a warm start: the zone's
 topology optimisation is then refined with the adjoint FDTD, which also
-judges the surrogate's error.
+measures the surrogate's error.
 
 This module only marshals arguments; every step runs in libzda.
 """

@@ -13,7 +13,7 @@ tensors between calls):
    I_s(rho) = 2 sum_q |S_q|^2, S = focal transform of the predicted monitor
    DFT (zda_focal_transform_nn), gradient through the transposed focal
    transform, the network's backward pass and the transposed filter chain.
-4. The FDTD (zda_iteration) then refines rho and judges the result; the
+4. The FDTD (zda_iteration) then refines rho and checks the result; the
    surrogate's field error against the FDTD is reported on held-out samples.
 """
 import ctypes
