@@ -2,7 +2,9 @@
 zones (assigned longest-processing-time-first), solve them with the FP64
 oracle, and all-reduce the focal phasors; the result must equal the
 single-process sum, and each rank's adjoint gradients must equal the
-single-process ones."""
+single-process ones.  Failure detection: a rank whose zone solve fails
+leaves before the all-reduce, and the other rank's collective ends with an
+error instead of hanging."""
 import os
 import socket
 
@@ -102,3 +104,60 @@ def test_two_gloo_ranks_match_single_process():
             seen[z] = g
             assert np.allclose(g, g_ref[z], rtol=1e-10, atol=1e-14)
     assert sorted(seen) == list(range(len(specs)))
+
+
+class _FailingSolver(OracleSolver):
+    """A zone whose solve fails on this rank (an exception on the host)."""
+
+    def forward(self, rho):
+        raise RuntimeError("zone solve failed")
+
+
+def _worker_failing(rank, world, port, out):
+    """Rank 1 fails in its zone solve and exits without joining the phasor
+    all-reduce; rank 0 must get an error from the collective (peer gone, or
+    the process group's short timeout), not hang."""
+    import datetime
+    import time
+    import torch.distributed as dist
+    from paper_2501_07979_gb300.lens import ShardedLens, assign_zones
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    specs = _specs()
+    owner = assign_zones(specs, world)
+    cls = _FailingSolver if rank == 1 else OracleSolver
+    lens = ShardedLens(specs, {z: cls(specs[z]) for z in range(len(specs)) if owner[z] == rank})
+    t0 = time.time()
+    try:
+        lens.forward(_rhos(specs))
+        out.put((rank, "ok", time.time() - t0))
+    except Exception as e:                     # noqa: BLE001  (the failure is the point)
+        out.put((rank, "error: %s" % type(e).__name__, time.time() - t0))
+        if rank == 1:
+            out.close()
+            out.join_thread()                  # flush the report, then leave without cleanup
+            os._exit(3)
+    try:
+        dist.destroy_process_group()
+    except Exception:                          # noqa: BLE001
+        pass
+
+
+@pytest.mark.skipif(not __import__("torch").distributed.is_available(), reason="no torch.distributed")
+def test_a_failed_rank_ends_the_others_collective_with_an_error():
+    pytest.importorskip("paper_2501_07979_gb300.lens")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_failing, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict((r, (msg, dt)) for r, msg, dt in (q.get(timeout=120) for _ in procs))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1][0].startswith("error")                      # the failing rank saw its own failure
+    assert res[0][0].startswith("error"), res[0]              # the survivor: an error, not a hang
+    assert res[0][1] < 60                                     # within the group's timeout plus slack
+    assert procs[1].exitcode == 3
+    assert procs[0].exitcode == 0
