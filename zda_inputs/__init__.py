@@ -73,6 +73,20 @@ class ZoneSpec:
     def replace(self, **kw) -> "ZoneSpec":
         return dataclasses.replace(self, **kw)
 
+    def to_json(self) -> str:
+        """The spec as a JSON object (tuples as lists)."""
+        import json
+        return json.dumps(dataclasses.asdict(self), sort_keys=True)
+
+    @classmethod
+    def from_json(cls, text: str) -> "ZoneSpec":
+        import json
+        d = json.loads(text)
+        for f in dataclasses.fields(cls):
+            if isinstance(d.get(f.name), list):
+                d[f.name] = tuple(d[f.name])
+        return cls(**d)
+
 
 def zone_cfg1() -> ZoneSpec:
     """Single annular zone forward solve: r in [10, 12.4] (48 cells incl. 8-cell
