@@ -46,8 +46,13 @@ def beta_schedule(it, beta0=1.0, beta_max=32.0, every=20, factor=2.0):
 
 
 class TopOpt:
-    def __init__(self, value_and_grad, rhos, lr=0.02, set_beta=None, schedule=beta_schedule, log_path=None):
+    def __init__(self, value_and_grad, rhos, lr=0.02, set_beta=None, schedule=beta_schedule, log_path=None,
+                 metrics=None):
+        """metrics(it, rhos) -> dict: extra quantities for the iteration's log
+        record (e.g. intensity per wavelength, focusing efficiency, Strehl
+        ratio, Gcell-upd/s), evaluated after the step."""
         self.f = value_and_grad
+        self.metrics = metrics
         self.rhos = [np.asarray(r, dtype=np.float64).copy() for r in rhos]
         self.opt = Adam([r.shape for r in self.rhos], lr=lr)
         self.set_beta = set_beta
@@ -66,6 +71,8 @@ class TopOpt:
         self.rhos = self.opt.step(self.rhos, grads)
         rec = {"iter": self.it, "objective": float(val), "beta": beta, "seconds": time.perf_counter() - t0,
                "grey": float(np.mean([np.mean(4 * r * (1 - r)) for r in self.rhos]))}
+        if self.metrics is not None:
+            rec.update(self.metrics(self.it, self.rhos))
         self.history.append(rec)
         if self.log_path:
             with open(self.log_path, "a") as fh:

@@ -46,3 +46,20 @@ def test_beta_continuation_schedule():
                  schedule=lambda it: beta_schedule(it, every=2))
     opt.run(5)
     assert seen == [1.0, 1.0, 2.0, 2.0, 4.0]
+
+
+def test_metrics_callback_lands_in_the_log(tmp_path):
+    target = np.full((3, 3), 0.7)
+    seen = []
+
+    def metrics(it, rhos):
+        seen.append(it)
+        return {"I_per_lambda": [float(np.mean(rhos[0])), 1.0], "fe": 0.5}
+
+    opt = TopOpt(_quadratic(target), [np.full((3, 3), 0.2)], lr=0.05, schedule=None,
+                 log_path=str(tmp_path / "m.jsonl"), metrics=metrics)
+    opt.run(3)
+    lines = [json.loads(l) for l in open(tmp_path / "m.jsonl")]
+    assert seen == [0, 1, 2]
+    assert all("fe" in l and len(l["I_per_lambda"]) == 2 for l in lines)
+    assert lines[-1]["I_per_lambda"][0] > lines[0]["I_per_lambda"][0] - 1e-12     # rho moves up to 0.7
