@@ -319,7 +319,9 @@ long long zda_lens_launch_count(const zda_lens *lens);   /* graph launches (or d
  * azimuthal orders +-1 (its phi-averaged near field), integrated with
  * n_phi_samples (>= 8) azimuthal samples, summed over zones.  p_trans_host
  * (n_lambda doubles, may be NULL): (n/2) |E_t|^2 over all monitor annuli
- * (all azimuthal orders), the transmitted power.  Synchronises `stream`. */
+ * and the whole circle (all azimuthal orders of the wedge; the cross term of
+ * the orders +1 and -1 cancels over the n wedge copies for n >= 3 and is
+ * kept for n = 1, 2), the transmitted power.  Synchronises `stream`. */
 zda_status zda_lens_focal_plane(zda_lens *lens, const double *pts_dev, int n_pts, int n_phi_samples,
                                 double *field_dev, double *p_trans_host, void *stream);
 
