@@ -19,6 +19,7 @@
 #include "zda.h"
 #include "zda_internal.h"
 #include "zda_step.h"
+#include "zda_tile.h"
 
 using cd = std::complex<double>;
 
@@ -51,7 +52,7 @@ struct Layout {           // byte offsets inside the workspace
     size_t fields, psi_z, psi_r, psi_m, fields2, psi_h2, mon, des_f, des_a, rho_in, rho_bar, rho_t, rb, site_grad, g_t, g_rho,
         norm, src_rad, dft_hist, inv_r_n, inv_r_h, br_n, cr_n, br_h, cr_h, bm_n, cm_n, bm_h, cm_h, bz_n, cz_n, bz_h, cz_h, a_n, d_n, a_c, d_c, ph_n,
         ph_h, pulse, twiddle, adj_time, Gr, Gp, emph_n, emph_h, wt, beta_r, beta_p, g_in, partial, S,
-        umean, pt_row, qr, qw, qp, qwp, kk, status, total;
+        umean, pt_row, qr, qw, qp, qwp, kk, energy, energy_part, status, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -73,11 +74,17 @@ struct zda_zone {
     bool adjoint_ok = false;        // the broadband adjoint pulse matrix was invertible
     long long launches = 0;
     // time-step kernel: 0 = split H/E launches (default), 1 = fused single launch
+    // streaming along r (bulk-copy ring), 3 = fused single launch on TMA-staged
+    // tiles (tile_phi rows x 32 z-cells, streaming over i_ranges radius ranges)
     int variant = 0, tile_phi = 2, i_ranges = 0;
+    zda::TileMaps tmaps[2];         // tensor maps of the two field buffers (variant 3)
+    const char *tmaps_ws = nullptr; // the workspace and tile shape they were encoded for
+    int tmaps_tj = 0;
     int wait_limit = 1 << 22, inject_timeout = 0;   // bounded mbarrier waits of the fused step
     bool pair_kernels = true;       // split step: two z-cells per thread where the grid allows
     int rpml = 0;                   // r-PML form (zda_zone_set_radial_pml)
     int last_parity = 0;            // fused runs: which buffer holds the final fields
+    int probe_every = 0, probe_n = 0;   // decay probe of forward runs: sampling period, samples of the last run
     // optional CUDA-event timing of every `time_every`-th H/E launch pair
     int time_every = 0;
     std::vector<cudaEvent_t> ev;    // ring of 4 events per sample: launches 1 | 2 | 3 of a step
@@ -277,6 +284,8 @@ static void compute_layout(zda_zone &z)
     L.qp = take(nr * sizeof(double));
     L.qwp = take(nr * sizeof(double));
     L.kk = take(Q * sizeof(double));
+    L.energy = take(2 * T * sizeof(double));            // decay probe: W, Wdot per sample
+    L.energy_part = take(2 * nr * sizeof(double));
     L.status = take(sizeof(int) * 4);
     L.total = off;
 }
@@ -516,7 +525,8 @@ static zda_status derive(zda_zone &z)
     } else {
         z.di_max = z.dj_max = 0;
     }
-    if (d.n_z > zda::fused_max_nz() || bor) z.variant = 0;
+    if (z.variant == 1 && (d.n_z > zda::fused_max_nz() || bor)) z.variant = 0;
+    if (z.variant == 3 && (bor || d.n_z % 2 || d.pml_z % 2)) z.variant = 0;
     compute_layout(z);
     z.tables_dirty = true;
     z.have_forward = false;
@@ -612,7 +622,7 @@ static zda_status clear_state(zda_zone &z, cudaStream_t s)
     CUDA_TRY(cudaMemsetAsync(P<int>(z, z.L.status) + 1, 0, sizeof(int), s));         // wait-timeout word
     CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields, 0, z.L.psi_r - z.L.fields, s));      // fields, psi_z
     CUDA_TRY(cudaMemsetAsync(z.ws + z.L.psi_r, 0, z.L.fields2 - z.L.psi_r, s));      // psi_r, psi_m
-    if (z.variant == 1) {                                                             // fields2, psi_h2
+    if (z.variant == 1 || z.variant == 3) {                                           // fields2, psi_h2
         CUDA_TRY(cudaMemsetAsync(z.ws + z.L.fields2, 0, z.L.mon - z.L.fields2, s));
     }
     return ZDA_OK;
@@ -677,9 +687,129 @@ static zda::FusedParams fused_params(zda_zone &z, const zda::StepParams &p, int 
     return f;
 }
 
+// decay probe (forward runs): after step n with (n + 1) % every == 0, the field
+// energy of the state and of its one-step difference into sample n / every
+static bool probe_due(const zda_zone &z, const zda::StepParams &p, int n)
+{
+    return z.probe_every > 0 && p.src_mode == zda::SRC_PLANE_WAVE && (n + 1) % z.probe_every == 0;
+}
+
+static zda::Fields fields_at(zda_zone &z, size_t off)
+{
+    const size_t ncell = (size_t)z.d.n_r * z.d.n_phi * z.d.n_z;
+    float2 *F = P<float2>(z, off);
+    return zda::Fields{F, F + ncell, F + 2 * ncell, F + 3 * ncell, F + 4 * ncell, F + 5 * ncell};
+}
+
+static void probe_sample(zda_zone &z, const zda::StepParams &p, int n, size_t cur_off, size_t prev_off,
+                         cudaStream_t s)
+{
+    double *e = P<double>(z, z.L.energy);
+    const int slot = n / z.probe_every;
+    zda::launch_field_energy(p, fields_at(z, cur_off), fields_at(z, prev_off), z.d.r_lo, z.d.dr, z.dphi * z.d.dz,
+                             P<double>(z, z.L.energy_part), e + 2 * slot, e + 2 * slot + 1, s);
+    z.launches += 2;
+}
+
+static zda::TileParams tile_params(zda_zone &z, const zda::StepParams &p, int parity)
+{
+    using namespace zda;
+    const zda_zone_desc &d = z.d;
+    const size_t ncell = (size_t)d.n_r * d.n_phi * d.n_z;
+    float2 *dst = parity ? P<float2>(z, z.L.fields) : P<float2>(z, z.L.fields2);
+    const size_t nzs = (size_t)d.n_r * d.n_phi * 2 * d.pml_z;
+    const size_t nrs = (size_t)(d.pml_r_in + d.pml_r_out) * d.n_phi * d.n_z;
+    float2 *H1 = P<float2>(z, z.L.psi_h2);
+    float2 *s0[4] = {p.psi.hr_z, p.psi.hp_z, p.psi.hp_r, p.psi.hz_r};
+    float2 *s1[4] = {H1, H1 + nzs, H1 + 2 * nzs, H1 + 2 * nzs + nrs};
+    float2 **rd = parity ? s1 : s0, **wr = parity ? s0 : s1;
+    TileParams t{};
+    t.p = p;
+    for (int c = 0; c < 3; ++c) {
+        t.oE[c] = dst + c * ncell;
+        t.oH[c] = dst + (3 + c) * ncell;
+    }
+    for (int c = 0; c < 4; ++c) {
+        t.psH_in[c] = rd[c];
+        t.psH_out[c] = wr[c];
+    }
+    t.err = P<int>(z, z.L.status) + 1;
+    t.wait_limit = z.wait_limit;
+    return t;
+}
+
+// tensor maps of both field buffers for the tile step (encoded on the host;
+// re-encoded when the workspace or the tile shape changes)
+static zda_status tile_maps(zda_zone &z)
+{
+    if (z.tmaps_ws == z.ws && z.tmaps_tj == z.tile_phi) return ZDA_OK;
+    const zda_zone_desc &d = z.d;
+    const size_t ncell = (size_t)d.n_r * d.n_phi * d.n_z;
+    for (int b = 0; b < 2; ++b) {
+        float2 *F = b ? P<float2>(z, z.L.fields2) : P<float2>(z, z.L.fields);
+        float2 *E[3] = {F, F + ncell, F + 2 * ncell}, *H[3] = {F + 3 * ncell, F + 4 * ncell, F + 5 * ncell};
+        const char *why = "";
+        if (!zda::encode_tile_maps(&z.tmaps[b], E, H, d.n_r, d.n_phi, d.n_z, z.tile_phi, &why))
+            return fail(ZDA_ERR_CUDA, std::string("tile step: ") + why);
+    }
+    z.tmaps_ws = z.ws;
+    z.tmaps_tj = z.tile_phi;
+    return ZDA_OK;
+}
+
+static int tile_rchunks(const zda_zone &z)
+{
+    if (z.i_ranges > 0) return std::min(z.i_ranges, z.d.n_r);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return zda::tile_auto_rchunks(z.tile_phi, z.d.n_r, z.d.n_phi, z.d.n_z, sms);
+}
+
 static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
 {
     const int R = (int)z.ev_pending.size();
+    if (z.variant == 3) {
+        zda_status st = tile_maps(z);
+        if (st) return st;
+        const bool dft = p.des || p.mon;
+        p.dft_ne = zda::dft_entries(p);
+        const zda::TileParams tp[2] = {tile_params(z, p, 0), tile_params(z, p, 1)};
+        const int nrc = tile_rchunks(z);
+        const bool adj = p.src_mode == zda::SRC_ADJOINT;
+        // timed samples: [tile step] between events 0 and 1, [DFT flush] between 2 and 3
+        for (int n = 0; n < z.d.n_steps; ++n) {
+            const bool timed = z.time_every > 0 && R > 0 && (n % z.time_every) == z.time_every - 1;
+            int slot = 0;
+            if (adj) zda::launch_adjoint_source_rad(p, n, s);
+            if (timed) {
+                slot = z.ev_next;
+                z.ev_next = (z.ev_next + 1) % R;
+                timing_drain_slot(z, slot);
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot], s));
+            }
+            cudaError_t e = zda::launch_tile_step(z.tmaps[n & 1], tp[n & 1], n, z.tile_phi, nrc, s);
+            if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("tile step: ") + cudaGetErrorString(e));
+            if (probe_due(z, p, n))
+                probe_sample(z, p, n, (n & 1) ? z.L.fields : z.L.fields2, (n & 1) ? z.L.fields2 : z.L.fields, s);
+            if (timed) {
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 1], s));
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 2], s));
+            }
+            if (dft && zda::dft_flush_due(p, n, z.d.n_steps)) {
+                zda::launch_dft_flush(p, n, s);
+                ++z.launches;
+            }
+            if (timed) {
+                CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 3], s));
+                z.ev_pending[slot] = 1;
+            }
+        }
+        z.last_parity = z.d.n_steps & 1;
+        z.launches += (long long)z.d.n_steps * (adj ? 2 : 1);
+        CUDA_TRY(cudaGetLastError());
+        return ZDA_OK;
+    }
     if (z.variant == 1) {
         zda::FusedParams f[2] = {fused_params(z, p, 0), fused_params(z, p, 1)};
         // timed samples: [stream kernel] between events 0 and 1, [DFT kernel] between 1 and 2
@@ -697,6 +827,8 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
             }
             e = zda::launch_fused_stream(fp, n, s);
             if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("fused step: ") + cudaGetErrorString(e));
+            if (probe_due(z, p, n))
+                probe_sample(z, p, n, (n & 1) ? z.L.fields : z.L.fields2, (n & 1) ? z.L.fields2 : z.L.fields, s);
             if (timed) {
                 CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 1], s));
                 CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 2], s));
@@ -727,11 +859,16 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
             timing_drain_slot(z, slot);
             CUDA_TRY(cudaEventRecord(z.ev[4 * slot], s));
         }
+        if (probe_due(z, p, n))                       // the state before this step, for the difference
+            CUDA_TRY(cudaMemcpyAsync(z.ws + z.L.fields2, z.ws + z.L.fields,
+                                     6 * (size_t)z.d.n_r * z.d.n_phi * z.d.n_z * sizeof(float2),
+                                     cudaMemcpyDeviceToDevice, s));
         if (pair) zda::launch_update_h_pair(p, s);
         else zda::launch_update_h(p, s);
         if (timed) CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 1], s));
         if (pair) zda::launch_update_e_pair(p, n, s);
         else zda::launch_update_e(p, n, s);
+        if (probe_due(z, p, n)) probe_sample(z, p, n, z.L.fields, z.L.fields2, s);
         if (timed) CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 2], s));
         if (dft && zda::dft_flush_due(p, n, z.d.n_steps)) {
             zda::launch_dft_flush(p, n, s);
@@ -808,6 +945,7 @@ static zda_status forward_enqueue(zda_zone &z, const float *rho, cudaStream_t s)
     p.des = P<float2>(z, z.L.des_f);
     st = time_loop(z, p, s);
     if (st) return st;
+    z.probe_n = z.probe_every > 0 ? z.d.n_steps / z.probe_every : 0;
     return focal_enqueue(z, P<float2>(z, z.L.mon), s);
 }
 
@@ -990,7 +1128,7 @@ zda_status zda_adjoint(zda_zone *z, const double *dI, float *grad_rho, void *str
     CUDA_TRY(cudaMemcpyAsync(z->ws + z->L.g_in, dI, z->nq * sizeof(double2), cudaMemcpyHostToDevice, s));
     st = adjoint_enqueue(*z, grad_rho, s);
     if (st) return st;
-    if (z->variant == 1) return check_wait_status(*z, s);
+    if (z->variant == 1 || z->variant == 3) return check_wait_status(*z, s);
     return ZDA_OK;
 }
 
@@ -1068,7 +1206,7 @@ zda_status zda_copy_fields(zda_zone *z, float *out, void *stream)
     if (st) return st;
     if (!out) return fail(ZDA_ERR_ARG, "null pointer");
     const size_t n = 6 * (size_t)z->d.n_r * z->d.n_phi * z->d.n_z * sizeof(float2);
-    const size_t off = (z->variant == 1 && z->last_parity) ? z->L.fields2 : z->L.fields;
+    const size_t off = ((z->variant == 1 || z->variant == 3) && z->last_parity) ? z->L.fields2 : z->L.fields;
     CUDA_TRY(cudaMemcpyAsync(out, z->ws + off, n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return ZDA_OK;
 }
@@ -1098,7 +1236,19 @@ long long zda_zone_launch_count(const zda_zone *z) { return z ? z->launches : -1
 
 zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ranges)
 {
-    if (!z || variant < 0 || variant > 2 || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
+    if (!z || variant < 0 || variant > 3 || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
+    if (variant == 3) {                      // fused step on TMA-staged tiles streaming along r
+        if (z->d.n_fold == 0) return fail(ZDA_ERR_ARG, "the axis zone (continuous axisymmetry) uses the split step");
+        if (z->rpml) return fail(ZDA_ERR_ARG, "the tile step implements the real-radius r-PML only");
+        if (z->d.n_z % 2 || z->d.pml_z % 2) return fail(ZDA_ERR_ARG, "the tile step needs even n_z and pml_z");
+        if (!zda::tile_shape_ok(tile_phi)) return fail(ZDA_ERR_ARG, "tile step: tile_phi must be 4, 8 or 16");
+        z->pair_kernels = true;
+        z->variant = 3;
+        z->tile_phi = tile_phi;
+        z->i_ranges = i_ranges;
+        z->have_forward = false;
+        return ZDA_OK;
+    }
     if (variant == 2) {                      // split step, one z-cell per thread
         z->variant = 0;
         z->pair_kernels = false;
@@ -1125,7 +1275,8 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
 zda_status zda_zone_set_radial_pml(zda_zone *z, int form)
 {
     if (!z || (form != 0 && form != 1)) return fail(ZDA_ERR_ARG, "r-PML form must be 0 or 1");
-    if (form == 1 && z->variant == 1) return fail(ZDA_ERR_ARG, "the fused step implements the real-radius r-PML only");
+    if (form == 1 && (z->variant == 1 || z->variant == 3))
+        return fail(ZDA_ERR_ARG, "the fused steps implement the real-radius r-PML only");
     if (z->rpml != form) {
         z->rpml = form;
         z->tables_dirty = true;
@@ -1189,7 +1340,7 @@ zda_status zda_zone_get_kernel(const zda_zone *z, int *variant, int *tile_phi, i
     if (!z || !variant || !tile_phi || !i_ranges) return fail(ZDA_ERR_ARG, "null argument");
     *variant = (z->variant == 0 && !z->pair_kernels) ? 2 : z->variant;
     *tile_phi = z->tile_phi;
-    *i_ranges = z->variant == 1 ? auto_i_ranges(*z) : 0;
+    *i_ranges = z->variant == 1 ? auto_i_ranges(*z) : (z->variant == 3 ? tile_rchunks(*z) : 0);
     return ZDA_OK;
 }
 
@@ -1207,6 +1358,30 @@ zda_status zda_zone_set_timing(zda_zone *z, int every)
     z->ev_pending.assign(R, 0);
     z->ev_next = 0;
     z->time_every = every;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_set_energy_probe(zda_zone *z, int every)
+{
+    if (!z || every < 0) return fail(ZDA_ERR_ARG, "bad argument");
+    z->probe_every = every;
+    z->probe_n = 0;
+    return ZDA_OK;
+}
+
+zda_status zda_zone_energy_trace(zda_zone *z, double *w_host, double *wdot_host, int max_samples, int *n_samples)
+{
+    if (!z || !w_host || !wdot_host || !n_samples || max_samples < 0) return fail(ZDA_ERR_ARG, "null argument");
+    if (!z->ws) return fail(ZDA_ERR_STATE, "no workspace bound");
+    CUDA_TRY(cudaSetDevice(z->ctx->device));
+    const int n = std::min(z->probe_n, max_samples);
+    std::vector<double> buf(2 * (size_t)std::max(n, 1));
+    if (n > 0) CUDA_TRY(cudaMemcpy(buf.data(), z->ws + z->L.energy, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) {
+        w_host[i] = buf[2 * i];
+        wdot_host[i] = buf[2 * i + 1];
+    }
+    *n_samples = n;
     return ZDA_OK;
 }
 
@@ -1267,7 +1442,7 @@ static size_t lens_ws_total(const zda_lens &L) { return lens_ws_status(L) + 256;
 
 static std::vector<long long> zone_stamp(const zda_zone &z)
 {
-    return {(long long)(uintptr_t)z.ws, z.variant, z.pair_kernels, z.tile_phi, z.i_ranges, z.d.n_steps, z.nq,
+    return {(long long)(uintptr_t)z.ws, z.variant, z.pair_kernels, z.tile_phi, z.i_ranges, z.probe_every, z.d.n_steps, z.nq,
             z.wait_limit, z.inject_timeout, (long long)z.lambda.size(), z.rpml};
 }
 
@@ -1435,7 +1610,7 @@ zda_status zda_lens_forward(zda_lens *L, const float *const *rho, double *focal_
     CUDA_TRY(cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     for (zda_zone *Z : L->zones) {
-        if (Z->variant == 1) {
+        if (Z->variant == 1 || Z->variant == 3) {
             st = check_wait_status(*Z, s);
             if (st) return st;
         }
@@ -1481,7 +1656,7 @@ zda_status zda_lens_adjoint(zda_lens *L, const double *dI, float *const *grad_rh
     }
     CUDA_TRY(cudaStreamSynchronize(s));
     for (zda_zone *Z : L->zones)
-        if (Z->variant == 1) {
+        if (Z->variant == 1 || Z->variant == 3) {
             st = check_wait_status(*Z, s);
             if (st) return st;
         }

@@ -1,0 +1,653 @@
+// Fused leap-frog step on TMA-staged (r, phi, z) tiles (sm_103a).
+//
+// One launch advances (E^n, H^{n-1/2}) to (E^{n+1}, H^{n+1/2}) (Eqs. 3-4)
+// with the CPML auxiliaries, the sheet source and the history writes of the
+// time-blocked running DFT, reading one field buffer and writing the other
+// (ping-pong).  DRAM traffic per cell and step: one read and one write of
+// the six components (96 B) against 144 B for the split H / E launches,
+// which read the six components twice.
+//
+// Each CTA owns a tile of TI radii x TJ phi rows x 32 z-cells.  Its E update
+// needs H^{n+1/2} on the tile and on its low faces (i0-1, j0-1, k0-1); those
+// are recomputed here instead of being read from the neighbouring tiles
+// (which write them in the same launch).  So one thread issues the TMA
+// tensor copies (cp.async.bulk.tensor, one box per component) of
+//   E^n       radii i0-1 .. i0+TI, rows j0-1 .. j0+TJ, z k0-2 .. k0+33
+//   H^{n-1/2} radii i0-1 .. i0+TI-1, rows j0-1 .. j0+TJ-1, z k0-2 .. k0+31
+// into shared memory ([radius][row][z], z fastest; outside the grid the
+// copy fills zeros, which are the PEC values there), completing on one
+// mbarrier.  Tiles at the wedge's phi edges also fetch the wrapped row
+// (phi row n_phi-1 for j0-1, row 0 for n_phi) into a staging slab and copy
+// it, times the Bloch phase e^{-+i m tau}, into place.  Then
+//   phase H: every (radius, row, z-pair) of the H box: H^{n+1/2} in place
+//            in shared memory; tile sites also stored to the output buffer
+//            with their H-side CPML auxiliaries (which are ping-ponged too:
+//            halo sites read the old set, which their owner does not write);
+//   phase E: every tile site: E^{n+1} from the shared H and E boxes, E-side
+//            CPML in place (each site only by its owner), source, DFT
+//            history, stored to the output buffer.
+// Threads walk the sites of a phase with consecutive z-pairs on consecutive
+// lanes (16-byte shared loads, coalesced 16-byte global stores).  The wait
+// for the copies is bounded: on expiry the error word is set, the kernel
+// finishes without the data and waits (bounded) for its copies before
+// exiting.  Same scheme and arithmetic as the split step (zda_pair.cu);
+// results agree to FP32 rounding.
+#include <cudaTypedefs.h>
+#include <algorithm>
+#include "zda_tile.h"
+
+namespace zda {
+namespace {
+
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void t_mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void t_mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// one poll; the thread may sleep in it up to 20 us (woken early when the phase completes)
+__device__ __forceinline__ bool t_mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(20000)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t t_now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait: at most `limit` polls and at most one second; false (and the
+// error word set) if the phase never completed
+__device__ __forceinline__ bool t_mbar_wait(uint32_t bar, uint32_t parity, int limit, int *err)
+{
+    const uint64_t t0 = t_now_ns();
+    for (int it = 0; it < limit; ++it) {
+        if (t_mbar_try(bar, parity)) return true;
+        if ((it & 15) == 15 && t_now_ns() - t0 > 1000000000ull) break;
+    }
+    atomicOr(err, 1);
+    return false;
+}
+
+// 3-D tensor copy global -> this CTA's shared memory, completing on `bar`
+__device__ __forceinline__ void tma3(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+struct C2 { float2 a, b; };                       // the z-pair (k, k+1)
+
+__device__ __forceinline__ C2 lds4(const float2 *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return C2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ C2 ldg4(const float2 *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return C2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st4(float2 *p, C2 c)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(c.a.x, c.a.y, c.b.x, c.b.y);
+}
+__device__ __forceinline__ C2 cmul2(float2 s, C2 c) { return C2{c_mul(s, c.a), c_mul(s, c.b)}; }
+__device__ __forceinline__ float2 f_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f_axpy(float s, float2 x, float2 y)      // y + s x
+{
+    return make_float2(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y));
+}
+__device__ __forceinline__ float t_rcp(float x)          // hardware reciprocal, as in the split E update
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int TJ>
+struct SG {                                                   // geometry of the radius-streamed tile step
+    static constexpr int KP = TILE_KZ / 2;                    // z-pairs of a tile
+    static constexpr int EZ = TILE_KZ + 4, HZ = TILE_KZ + 2;  // z extents of the slabs (from k0-2)
+    static constexpr int EJ = TJ + 2, HJ = TJ + 1;            // rows of the E slab (j0-1 .. j0+TJ), H slab
+    static constexpr int al(int x) { return (x + 15) & ~15; } // 128-byte aligned regions (float2 units)
+    static constexpr int ES = al(EJ * EZ), HS = al(HJ * HZ), RW = al(EZ > HZ ? EZ : HZ);
+    // one load group: E slab of radius r+1, H slab of radius r (3 components each), and the
+    // wrapped rows of edge tiles: E low, E high, H low (3 components each)
+    static constexpr int E_OFF = 0, H_OFF = 3 * ES, WEL = H_OFF + 3 * HS, WEH = WEL + 3 * RW, WHL = WEH + 3 * RW;
+    static constexpr int GROUP = WHL + 3 * RW;
+    static constexpr int NSLOT = 4;
+    // threads: E items (row, pair 1..KP) | H items (row, pair 1..KP) | H z-halo items (row, pair 0)
+    static constexpr int NE = TJ * KP, NH = HJ * KP, NHALO = HJ;
+    static constexpr int NT = (NE + NH + NHALO + 31) / 32 * 32;
+};
+
+template <int TJ, int MINB>
+__global__ void __launch_bounds__(SG<TJ>::NT, MINB)
+    k_tile_step(const __grid_constant__ TileMaps m, const TileParams tp, const int n, const int i_range)
+{
+    using G = SG<TJ>;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT];
+    __shared__ int abort_s;                                   // the error word was already set at entry
+    const uint32_t raw_s = s_addr(smem_raw);
+    const uint32_t base_s = (raw_s + 127u) & ~127u;
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + (base_s - raw_s));
+
+    const StepParams &p = tp.p;
+    const int nr = p.nr, nphi = p.nphi, nz = p.nz;
+    const int nzc = (nz + TILE_KZ - 1) / TILE_KZ;
+    const int k0 = (blockIdx.x % nzc) * TILE_KZ;
+    const int j0 = (blockIdx.x / nzc) * TJ;
+    const int ib = blockIdx.y * i_range, ie = min(nr, ib + i_range);
+    const int r0 = ib > 0 ? ib - 1 : 0;                       // radius ib-1: H recomputed, nothing stored
+    const int tid = threadIdx.x;
+    const bool wlo = j0 == 0;                                 // row j0-1 is the wrapped row n_phi-1
+    const int s_hi = nphi - j0 + 1;                           // slab row of phi row n_phi (the wrapped row 0)
+    const bool whi = s_hi <= TJ + 1;
+    const int x = 2 * (k0 - 2);
+
+    // load group g(r) = {E^n(r+1), H^{n-1/2}(r)}, r = r0-1 .. ie-1, in slot (r - r0 + 1) % NSLOT
+    auto slot_of = [&](int r) { return (r - r0 + 1) % G::NSLOT; };
+    auto parity_of = [&](int r) { return (uint32_t)(((r - r0 + 1) / G::NSLOT) & 1); };
+    auto issue = [&](int r) {
+        const int sl = slot_of(r);
+        const uint32_t g = base_s + (uint32_t)(sl * G::GROUP) * 8u;
+        const uint32_t bar = s_addr(&bar_mem[sl]);
+        uint32_t bytes = 3u * (G::EZ * G::EJ + G::HZ * G::HJ) * 8u;
+        if (wlo) bytes += 3u * (G::EZ + G::HZ) * 8u;
+        if (whi) bytes += 3u * G::EZ * 8u;
+        t_mbar_expect_tx(bar, bytes);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            tma3(g + (G::E_OFF + c * G::ES) * 8u, &m.e[c], x, j0 - 1, r + 1, bar);
+            tma3(g + (G::H_OFF + c * G::HS) * 8u, &m.h[c], x, j0 - 1, r, bar);
+            if (wlo) {
+                tma3(g + (G::WEL + c * G::RW) * 8u, &m.ew[c], x, nphi - 1, r + 1, bar);
+                tma3(g + (G::WHL + c * G::RW) * 8u, &m.hw[c], x, nphi - 1, r, bar);
+            }
+            if (whi) tma3(g + (G::WEH + c * G::RW) * 8u, &m.ew[c], x, 0, r + 1, bar);
+        }
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
+        // an earlier launch of this run gave up waiting: do nothing (the host reports the error)
+        abort_s = *(volatile int *)tp.err;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (abort_s) return;
+    // groups g(r0-1), g(r0), g(r0+1) now; g(r+2) after iteration r, into the slot of g(r-2)
+    if (tid == 0)
+        for (int r = r0 - 1; r < ie && r <= r0 + 1; ++r) issue(r);
+    int last_issued = min(ie - 1, r0 + 1);
+    // every thread observes the first group's completion (its E slab is read at iteration r0)
+    bool failed = !t_mbar_wait(s_addr(&bar_mem[slot_of(r0 - 1)]), parity_of(r0 - 1), tp.wait_limit, tp.err);
+
+    const float2 zero = make_float2(0.f, 0.f);
+    const float dt = p.dt;
+    const int sj = nz, si = nphi * nz;                        // element strides (a zone's field < 2^31 cells)
+
+    if (tid < G::NE) {
+        // ================= E items: E^{n+1}(r-1) at iteration r, row se, pair pe (fixed)
+        const int se = tid / G::KP + 1, pe = tid % G::KP + 1;
+        const int je = j0 - 1 + se, ke = k0 - 2 + 2 * pe;
+        const bool e_valid = je < nphi && ke < nz;
+        const int kze = (ke < p.pz) ? ke : ((ke >= nz - p.pz) ? ke - (nz - 2 * p.pz) : -1);
+        float bzn[2] = {0.f, 0.f}, czn[2] = {0.f, 0.f}, an[2] = {1.f, 1.f}, dn[2] = {0.f, 0.f},
+              ac[2] = {1.f, 1.f}, dc[2] = {0.f, 0.f};
+        float2 src_pn = zero, src_ph = zero;
+        int src_u = -1;                                       // which cell of the pair carries the source
+        if (e_valid) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (kze >= 0) { bzn[u] = __ldg(p.t.bz_n + ke + u); czn[u] = __ldg(p.t.cz_n + ke + u); }
+                an[u] = __ldg(p.t.a_n + ke + u); dn[u] = __ldg(p.t.d_n + ke + u);
+                ac[u] = __ldg(p.t.a_c + ke + u); dc[u] = __ldg(p.t.d_c + ke + u);
+            }
+            if (p.src_mode != SRC_NONE && (ke == p.src_k || ke + 1 == p.src_k)) {
+                src_u = p.src_k - ke;
+                src_pn = p.t.ph_n[je];
+                src_ph = p.t.ph_h[je];
+            }
+        }
+        const float src_amp = p.src_mode == SRC_PLANE_WAVE ? __ldg(p.t.pulse + n) * p.src_scale : 0.f;
+        const int he_own = G::H_OFF + se * G::HZ + 2 * pe, he_jm = G::H_OFF + (se - 1) * G::HZ + 2 * pe;
+        const int ee_own = G::E_OFF + se * G::EZ + 2 * pe;
+        const size_t plane = (size_t)nr * nphi, ndes = p.des ? plane * p.des_nk : 0;
+        float2 *hs = (p.dft_hist && (p.des || p.mon)) ? p.dft_hist + (size_t)(n % DFT_BLOCK) * p.dft_ne : nullptr;
+        const int dk0 = ke - p.des_k0;
+        const bool e_hist = hs && e_valid &&
+                            ((p.des && dk0 + 1 >= 0 && dk0 < p.des_nk) || (p.mon && (ke == p.mon_k || ke + 1 == p.mon_k)));
+        // per-radius values of the next E radius, loaded one iteration ahead
+        auto rb_load = [&](int i, float &a, float &b, float &c) {
+            if (e_valid && i >= 0 && i < nr) {
+                const int ij = i * nphi + je;
+                a = __ldg(p.rb_r + ij); b = __ldg(p.rb_p + ij); c = __ldg(p.rb_z + ij);
+            }
+        };
+        float rbr = 0.f, rbp = 0.f, rbz = 0.f, nrbr = 0.f, nrbp = 0.f, nrbz = 0.f;
+        float4 tab = make_float4(0.f, 0.f, 0.f, 0.f), ntab = tab;   // 1/r_i, 1/r_{i+1/2}, CPML b, c at r_i
+        auto tab_load = [&](int i, float4 &t) {
+            if (i >= 0 && i < nr)
+                t = make_float4(__ldg(p.t.inv_r_n + i), __ldg(p.t.inv_r_h + i), __ldg(p.t.br_n + i), __ldg(p.t.cr_n + i));
+        };
+        rb_load(ib, nrbr, nrbp, nrbz);
+        tab_load(ib, ntab);
+        for (int r = r0; r <= ie; ++r) {
+            const int i = r - 1;                              // radius of this iteration's E update
+            rbr = nrbr; rbp = nrbp; rbz = nrbz;
+            tab = ntab;
+            rb_load(i + 1, nrbr, nrbp, nrbz);
+            tab_load(i + 1, ntab);
+            if (r < ie && !failed) failed = !t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err);
+            if (i >= ib && e_valid && !failed) {
+                const float2 *gq = sm + slot_of(i) * G::GROUP;     // H^{n+1/2}(i)
+                const float2 *gp = sm + slot_of(i - 1) * G::GROUP; // E^n(i), H^{n+1/2}(i-1)
+                const C2 hr = lds4(gq + he_own), hp = lds4(gq + he_own + G::HS), hz = lds4(gq + he_own + 2 * G::HS);
+                const C2 hz_jm = lds4(gq + he_jm + 2 * G::HS), hr_jm = lds4(gq + he_jm);
+                const float2 hp_km = gq[he_own + G::HS - 1], hr_km = gq[he_own - 1];
+                const C2 hz_im = lds4(gp + he_own + 2 * G::HS), hp_im = lds4(gp + he_own + G::HS);
+                C2 er = lds4(gp + ee_own), ep = lds4(gp + ee_own + G::ES), ez = lds4(gp + ee_own + 2 * G::ES);
+                const float irn = tab.x, irh = tab.y;
+                const int ir = (i < p.pr_in) ? i : ((i >= nr - p.pr_out) ? i - (nr - p.pr_in - p.pr_out) : -1);
+                const int ij = i * nphi + je;
+                const int zx = ij * (2 * p.pz) + (kze >= 0 ? kze : 0);
+                const int rx = ((ir >= 0 ? ir : 0) * nphi + je) * nz + ke;
+                const float2 HPk[3] = {hp_km, hp.a, hp.b}, HRk[3] = {hr_km, hr.a, hr.b};
+                const float2 HZk[2] = {hz.a, hz.b}, HZJ[2] = {hz_jm.a, hz_jm.b}, HRJ[2] = {hr_jm.a, hr_jm.b};
+                const float2 HZI[2] = {hz_im.a, hz_im.b}, HPI[2] = {hp_im.a, hp_im.b};
+                float2 *ER[2] = {&er.a, &er.b}, *EP[2] = {&ep.a, &ep.b}, *EZ[2] = {&ez.a, &ez.b};
+                C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
+                if (kze >= 0) { ps_r = ldg4(p.psi.er_z + zx); ps_p = ldg4(p.psi.ep_z + zx); }
+                float brn = 0.f, crn = 0.f;
+                if (ir >= 0) {
+                    ps_pr = ldg4(p.psi.ep_r + rx); ps_zr = ldg4(p.psi.ez_r + rx);
+                    brn = tab.z; crn = tab.w;
+                }
+                float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
+                float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
+                const bool fast = kze < 0 && ir < 0 && src_u < 0 && ke > 0 && i > 0;
+                if (fast) {
+                    // interior: coefficient form (no CPML, no source, not on a PEC face)
+                    const float cph_h = irh * p.inv_dphi, cph_n = irn * p.inv_dphi, cm = 0.5f * irn;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const float cr = dt * t_rcp(an[u] + dn[u] * rbr), cp = dt * t_rcp(an[u] + dn[u] * rbp);
+                        const float cz = dt * t_rcp(ac[u] + dc[u] * rbz);
+                        float2 t = f_sub(HZk[u], HZJ[u]);     // E_r: (1/r) dH_z/dphi - dH_phi/dz
+                        float2 a = make_float2(cph_h * t.x, cph_h * t.y);
+                        a = f_axpy(-p.inv_dz, f_sub(HPk[u + 1], HPk[u]), a);
+                        *ER[u] = f_axpy(cr, a, *ER[u]);
+                        t = f_sub(HRk[u + 1], HRk[u]);        // E_phi: dH_r/dz - dH_z/dr
+                        a = make_float2(p.inv_dz * t.x, p.inv_dz * t.y);
+                        a = f_axpy(-p.inv_dr, f_sub(HZk[u], HZI[u]), a);
+                        *EP[u] = f_axpy(cp, a, *EP[u]);
+                        t = f_sub(HPk[u + 1], HPI[u]);        // E_z: (1/r) d(r H_phi)/dr - (1/r) dH_r/dphi
+                        a = make_float2(p.inv_dr * t.x, p.inv_dr * t.y);
+                        a = f_axpy(cm, f_add(HPk[u + 1], HPI[u]), a);
+                        a = f_axpy(-cph_n, f_sub(HRk[u + 1], HRJ[u]), a);
+                        *EZ[u] = f_axpy(cz, a, *EZ[u]);
+                    }
+                } else {
+                float2 sr = zero, sp = zero;                  // source of this radius
+                if (src_u >= 0) {
+                    if (p.src_mode == SRC_PLANE_WAVE) {
+                        sr = c_scale(src_pn, src_amp);
+                        sp = make_float2(-src_ph.y * src_amp, src_ph.x * src_amp);
+                    } else {
+                        sr = c_mul(src_pn, p.src_rad[i]);
+                        sp = c_mul(src_ph, p.src_rad[nr + i]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int kk = ke + u;
+                    const float2 jr = (u == src_u) ? sr : zero, jp = (u == src_u) ? sp : zero;
+                    if (kk > 0) {                             // E_r
+                        const float2 dph = c_scale(c_sub(HZk[u], HZJ[u]), irh * p.inv_dphi);
+                        float2 dz = c_scale(c_sub(HPk[u + 1], HPk[u]), p.inv_dz);
+                        if (kze >= 0) {
+                            *PR[u] = c_add(c_scale(*PR[u], bzn[u]), c_scale(dz, czn[u]));
+                            dz = c_add(dz, *PR[u]);
+                        }
+                        const float iee = t_rcp(an[u] + dn[u] * rbr);
+                        *ER[u] = c_add(*ER[u], c_scale(c_sub(c_sub(dph, dz), jr), dt * iee));
+                    }
+                    if (i > 0 && kk > 0) {                    // E_phi
+                        float2 dz = c_scale(c_sub(HRk[u + 1], HRk[u]), p.inv_dz);
+                        float2 drr = c_scale(c_sub(HZk[u], HZI[u]), p.inv_dr);
+                        if (kze >= 0) {
+                            *PP[u] = c_add(c_scale(*PP[u], bzn[u]), c_scale(dz, czn[u]));
+                            dz = c_add(dz, *PP[u]);
+                        }
+                        if (ir >= 0) {
+                            *PPR[u] = c_add(c_scale(*PPR[u], brn), c_scale(drr, crn));
+                            drr = c_add(drr, *PPR[u]);
+                        }
+                        const float iee = t_rcp(an[u] + dn[u] * rbp);
+                        *EP[u] = c_add(*EP[u], c_scale(c_sub(c_sub(dz, drr), jp), dt * iee));
+                    }
+                    if (i > 0) {                              // E_z
+                        float2 drr = c_add(c_scale(c_sub(HPk[u + 1], HPI[u]), p.inv_dr),
+                                           c_scale(c_add(HPk[u + 1], HPI[u]), 0.5f * irn));
+                        const float2 dph = c_scale(c_sub(HRk[u + 1], HRJ[u]), irn * p.inv_dphi);
+                        if (ir >= 0) {
+                            *PZR[u] = c_add(c_scale(*PZR[u], brn), c_scale(drr, crn));
+                            drr = c_add(drr, *PZR[u]);
+                        }
+                        const float iee = t_rcp(ac[u] + dc[u] * rbz);
+                        *EZ[u] = c_add(*EZ[u], c_scale(c_sub(drr, dph), dt * iee));
+                    }
+                }
+                }
+                const int c = i * si + je * sj + ke;
+                st4(tp.oE[0] + c, er);
+                st4(tp.oE[1] + c, ep);
+                st4(tp.oE[2] + c, ez);
+                if (kze >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
+                if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
+                if (e_hist) {                                 // history slot of the time-blocked DFT
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int dk = dk0 + u;
+                        if (p.des && dk >= 0 && dk < p.des_nk) {
+                            const size_t e = (size_t)ij * p.des_nk + dk;
+                            hs[e] = *ER[u];
+                            hs[ndes + e] = *EP[u];
+                            hs[2 * ndes + e] = *EZ[u];
+                        }
+                        if (p.mon && ke + u == p.mon_k) {
+                            hs[3 * ndes + ij] = *ER[u];
+                            hs[3 * ndes + plane + ij] = *EP[u];
+                        }
+                    }
+                }
+            }
+            // H(r) published; group g(r-2) free; a wait that gave up anywhere ends the loop for all
+            if (__syncthreads_or(failed)) { failed = true; break; }
+            if (tid == 0 && r + 2 < ie) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(r + 2);
+                last_issued = r + 2;
+            }
+        }
+    } else {
+        // ================= H items: H^{n+1/2}(r) at iteration r, row sh, pair ph (fixed)
+        const int th = tid - G::NE;
+        const bool h_on = th < G::NH + G::NHALO;
+        const int sh = th < G::NH ? th / G::KP : th - G::NH;
+        const int ph = th < G::NH ? th % G::KP + 1 : 0;       // pair 0: the z-halo below the tile
+        const int jh = j0 - 1 + sh, kh = k0 - 2 + 2 * ph;
+        const bool h_valid = h_on && jh < nphi && kh >= 0 && kh < nz;
+        const bool h_own = sh > 0 && ph > 0;
+        const bool h_wlo = wlo && sh == 0, h_whi = whi && sh + 1 == s_hi;
+        const int jhw = jh < 0 ? jh + nphi : jh;
+        const int kzh = (kh < p.pz) ? kh : ((kh >= nz - p.pz) ? kh - (nz - 2 * p.pz) : -1);
+        float bzh[2] = {0.f, 0.f}, czh[2] = {0.f, 0.f};
+        if (h_valid && kzh >= 0) {
+            bzh[0] = __ldg(p.t.bz_h + kh); bzh[1] = __ldg(p.t.bz_h + kh + 1);
+            czh[0] = __ldg(p.t.cz_h + kh); czh[1] = __ldg(p.t.cz_h + kh + 1);
+        }
+        // shared offsets within a group: own row (slab or wrapped-row staging), row + 1
+        const int e_own = h_wlo ? G::WEL + 2 * ph : G::E_OFF + sh * G::EZ + 2 * ph;
+        const int e_cs = h_wlo ? G::RW : G::ES;               // component stride of that region
+        const int e_up = h_whi ? G::WEH + 2 * ph : G::E_OFF + (sh + 1) * G::EZ + 2 * ph;
+        const int e_ucs = h_whi ? G::RW : G::ES;
+        const int h_rd = h_wlo ? G::WHL + 2 * ph : G::H_OFF + sh * G::HZ + 2 * ph;
+        const int h_rcs = h_wlo ? G::RW : G::HS;
+        const int h_wr = G::H_OFF + sh * G::HZ + 2 * ph;      // H^{n+1/2} always into the slab
+        float4 tab = make_float4(0.f, 0.f, 0.f, 0.f), ntab = tab;   // 1/r_r, 1/r_{r+1/2}, CPML b, c at r_{r+1/2}
+        auto tab_load = [&](int r, float4 &t) {
+            if (r >= 0 && r < nr)
+                t = make_float4(__ldg(p.t.inv_r_n + r), __ldg(p.t.inv_r_h + r), __ldg(p.t.br_h + r), __ldg(p.t.cr_h + r));
+        };
+        tab_load(r0, ntab);
+        for (int r = r0; r <= ie; ++r) {
+            tab = ntab;
+            tab_load(r + 1, ntab);
+            if (r < ie && !failed) failed = !t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err);
+            if (r < ie && h_valid && !failed) {
+                const float2 *gp = sm + slot_of(r - 1) * G::GROUP;  // E^n(r)
+                float2 *gc = sm + slot_of(r) * G::GROUP;            // E^n(r+1), H(r)
+                const float irn = tab.x, irh = tab.y;
+                const int ir = (r < p.pr_in) ? r : ((r >= nr - p.pr_out) ? r - (nr - p.pr_in - p.pr_out) : -1);
+                const C2 er = lds4(gp + e_own), ep = lds4(gp + e_own + e_cs), ez = lds4(gp + e_own + 2 * e_cs);
+                const float2 ep_k2 = gp[e_own + e_cs + 2], er_k2 = gp[e_own + 2];
+                const C2 ez_jp = lds4(gp + e_up + 2 * e_ucs), er_jp = lds4(gp + e_up);
+                const C2 ez_ip = lds4(gc + e_own + 2 * e_cs), ep_ip = lds4(gc + e_own + e_cs);
+                C2 hr = lds4(gc + h_rd), hp = lds4(gc + h_rd + h_rcs), hz = lds4(gc + h_rd + 2 * h_rcs);
+                float2 EP[3] = {ep.a, ep.b, ep_k2}, ER[3] = {er.a, er.b, er_k2};
+                float2 EZ[2] = {ez.a, ez.b}, EZJ[2] = {ez_jp.a, ez_jp.b}, ERJ[2] = {er_jp.a, er_jp.b};
+                float2 EZI[2] = {ez_ip.a, ez_ip.b}, EPI[2] = {ep_ip.a, ep_ip.b};
+                if (h_wlo) {                                  // row n_phi-1 seen from the wedge's low side
+#pragma unroll
+                    for (int u = 0; u < 3; ++u) { EP[u] = c_mul(p.bloch_inv, EP[u]); ER[u] = c_mul(p.bloch_inv, ER[u]); }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        EZ[u] = c_mul(p.bloch_inv, EZ[u]); EZI[u] = c_mul(p.bloch_inv, EZI[u]);
+                        EPI[u] = c_mul(p.bloch_inv, EPI[u]);
+                    }
+                    hr = cmul2(p.bloch_inv, hr); hp = cmul2(p.bloch_inv, hp); hz = cmul2(p.bloch_inv, hz);
+                }
+                if (h_whi) {                                  // row 0 seen from the wedge's high side
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) { EZJ[u] = c_mul(p.bloch, EZJ[u]); ERJ[u] = c_mul(p.bloch, ERJ[u]); }
+                }
+                const int zx = (r * nphi + jhw) * (2 * p.pz) + (kzh >= 0 ? kzh : 0);
+                const int rx = ((ir >= 0 ? ir : 0) * nphi + jhw) * nz + kh;
+                C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
+                if (kzh >= 0) {
+                    ps_r = ldg4(tp.psH_in[0] + zx);
+                    ps_p = ldg4(tp.psH_in[1] + zx);
+                    if (h_wlo) { ps_r = cmul2(p.bloch_inv, ps_r); ps_p = cmul2(p.bloch_inv, ps_p); }
+                }
+                float brh = 0.f, crh = 0.f;
+                if (ir >= 0) {
+                    brh = tab.z; crh = tab.w;
+                    ps_pr = ldg4(tp.psH_in[2] + rx);
+                    ps_zr = ldg4(tp.psH_in[3] + rx);
+                    if (h_wlo) { ps_pr = cmul2(p.bloch_inv, ps_pr); ps_zr = cmul2(p.bloch_inv, ps_zr); }
+                }
+                float2 *HR[2] = {&hr.a, &hr.b}, *HP[2] = {&hp.a, &hp.b}, *HZ[2] = {&hz.a, &hz.b};
+                float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
+                float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
+                if (kzh < 0 && ir < 0) {
+                    // interior: coefficient form (no CPML)
+                    const float k_phn = dt * irn * p.inv_dphi, k_z = dt * p.inv_dz, k_r = dt * p.inv_dr;
+                    const float k_m = 0.5f * dt * irh, k_phh = dt * irh * p.inv_dphi;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        *HR[u] = f_axpy(-k_phn, f_sub(EZJ[u], EZ[u]), *HR[u]);
+                        *HR[u] = f_axpy(k_z, f_sub(EP[u + 1], EP[u]), *HR[u]);
+                        *HP[u] = f_axpy(-k_z, f_sub(ER[u + 1], ER[u]), *HP[u]);
+                        *HP[u] = f_axpy(k_r, f_sub(EZI[u], EZ[u]), *HP[u]);
+                        *HZ[u] = f_axpy(-k_r, f_sub(EPI[u], EP[u]), *HZ[u]);
+                        *HZ[u] = f_axpy(-k_m, f_add(EPI[u], EP[u]), *HZ[u]);
+                        *HZ[u] = f_axpy(k_phh, f_sub(ERJ[u], ER[u]), *HZ[u]);
+                    }
+                } else {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    {                                         // H_r
+                        const float2 dph = c_scale(c_sub(EZJ[u], EZ[u]), irn * p.inv_dphi);
+                        float2 dz = c_scale(c_sub(EP[u + 1], EP[u]), p.inv_dz);
+                        if (kzh >= 0) {
+                            *PR[u] = c_add(c_scale(*PR[u], bzh[u]), c_scale(dz, czh[u]));
+                            dz = c_add(dz, *PR[u]);
+                        }
+                        *HR[u] = c_sub(*HR[u], c_scale(c_sub(dph, dz), dt));
+                    }
+                    {                                         // H_phi
+                        float2 dz = c_scale(c_sub(ER[u + 1], ER[u]), p.inv_dz);
+                        float2 drr = c_scale(c_sub(EZI[u], EZ[u]), p.inv_dr);
+                        if (kzh >= 0) {
+                            *PP[u] = c_add(c_scale(*PP[u], bzh[u]), c_scale(dz, czh[u]));
+                            dz = c_add(dz, *PP[u]);
+                        }
+                        if (ir >= 0) {
+                            *PPR[u] = c_add(c_scale(*PPR[u], brh), c_scale(drr, crh));
+                            drr = c_add(drr, *PPR[u]);
+                        }
+                        *HP[u] = c_sub(*HP[u], c_scale(c_sub(dz, drr), dt));
+                    }
+                    {                                         // H_z
+                        float2 drr = c_add(c_scale(c_sub(EPI[u], EP[u]), p.inv_dr),
+                                           c_scale(c_add(EPI[u], EP[u]), 0.5f * irh));
+                        const float2 dph = c_scale(c_sub(ERJ[u], ER[u]), irh * p.inv_dphi);
+                        if (ir >= 0) {
+                            *PZR[u] = c_add(c_scale(*PZR[u], brh), c_scale(drr, crh));
+                            drr = c_add(drr, *PZR[u]);
+                        }
+                        *HZ[u] = c_sub(*HZ[u], c_scale(c_sub(drr, dph), dt));
+                    }
+                }
+                }
+                st4(gc + h_wr, hr);
+                st4(gc + h_wr + G::HS, hp);
+                st4(gc + h_wr + 2 * G::HS, hz);
+                if (h_own && r >= ib) {
+                    const int c = r * si + jh * sj + kh;
+                    st4(tp.oH[0] + c, hr);
+                    st4(tp.oH[1] + c, hp);
+                    st4(tp.oH[2] + c, hz);
+                    if (kzh >= 0) { st4(tp.psH_out[0] + zx, ps_r); st4(tp.psH_out[1] + zx, ps_p); }
+                    if (ir >= 0) { st4(tp.psH_out[2] + rx, ps_pr); st4(tp.psH_out[3] + rx, ps_zr); }
+                }
+            }
+            if (__syncthreads_or(failed)) { failed = true; break; }   // matches the E warps' barrier
+        }
+    }
+    if (failed && tid == 0)                                   // copies still in flight
+        for (int r = max(r0 - 1, last_issued - 3); r <= last_issued; ++r)
+            t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+template <int TJ, int MINB>
+cudaError_t launch_shape(const TileMaps &m, const TileParams &tp, int n, int n_rchunks, cudaStream_t s)
+{
+    using G = SG<TJ>;
+    const size_t bytes = (size_t)G::NSLOT * G::GROUP * sizeof(float2) + 128;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static unsigned attr_done = 0;                            // per device (bit), set once
+    if (dev < 32 && !(attr_done & (1u << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_step<TJ, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_done |= 1u << dev;
+    }
+    const int nzc = (tp.p.nz + TILE_KZ - 1) / TILE_KZ, njt = (tp.p.nphi + TJ - 1) / TJ;
+    const int nrc = std::max(1, std::min(n_rchunks, tp.p.nr));
+    const int i_range = (tp.p.nr + nrc - 1) / nrc;
+    dim3 g((unsigned)(nzc * njt), (unsigned)((tp.p.nr + i_range - 1) / i_range));
+    k_tile_step<TJ, MINB><<<g, G::NT, bytes, s>>>(m, tp, n, i_range);
+    return cudaGetLastError();
+}
+
+template <int TJ>
+size_t shape_bytes() { return (size_t)SG<TJ>::NSLOT * SG<TJ>::GROUP * sizeof(float2) + 128; }
+
+}  // namespace
+
+bool tile_shape_ok(int tj) { return tj == 4 || tj == 8 || tj == 16; }
+
+size_t tile_smem_bytes(int tj)
+{
+    if (tj == 4) return shape_bytes<4>();
+    if (tj == 8) return shape_bytes<8>();
+    if (tj == 16) return shape_bytes<16>();
+    return 0;
+}
+
+int tile_blocks_per_sm(int tj)
+{
+    const size_t b = tile_smem_bytes(tj);
+    return b ? (int)std::min<size_t>(8, (227 * 1024) / (b + 1024)) : 0;
+}
+
+int tile_auto_rchunks(int tj, int nr, int nphi, int nz, int sms)
+{
+    const int per_wave = sms * std::max(1, tile_blocks_per_sm(tj));
+    const int tiles = ((nz + TILE_KZ - 1) / TILE_KZ) * ((nphi + tj - 1) / tj);
+    // about four waves of thread blocks (radius chunks streamed in parallel), at least 8 radii per chunk
+    int c = std::max(1, (4 * per_wave + tiles - 1) / std::max(tiles, 1));
+    return std::max(1, std::min(c, nr / 8));
+}
+
+bool encode_tile_maps(TileMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
+                      const char **why)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        *why = "the driver's cuTensorMapEncodeTiled is not available";
+        return false;
+    }
+    // FP32 view: x = 2 k (+1 for the imaginary part), y = phi row, z = radius
+    const cuuint64_t dims[3] = {2ull * (cuuint64_t)nz, (cuuint64_t)nphi, (cuuint64_t)nr};
+    const cuuint64_t strides[2] = {(cuuint64_t)nz * 8ull, (cuuint64_t)nphi * (cuuint64_t)nz * 8ull};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const cuuint32_t be[3] = {2u * (TILE_KZ + 4), (cuuint32_t)(tj + 2), 1u};
+    const cuuint32_t bew[3] = {2u * (TILE_KZ + 4), 1u, 1u};
+    const cuuint32_t bh[3] = {2u * (TILE_KZ + 2), (cuuint32_t)(tj + 1), 1u};
+    const cuuint32_t bhw[3] = {2u * (TILE_KZ + 2), 1u, 1u};
+    auto one = [&](CUtensorMap *t, void *base, const cuuint32_t *box) {
+        return enc(t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    for (int c = 0; c < 3; ++c) {
+        if (!one(&m->e[c], E[c], be) || !one(&m->ew[c], E[c], bew) || !one(&m->h[c], H[c], bh) ||
+            !one(&m->hw[c], H[c], bhw)) {
+            *why = "cuTensorMapEncodeTiled refused the field layout";
+            return false;
+        }
+    }
+    return true;
+}
+
+cudaError_t launch_tile_step(const TileMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s)
+{
+    if (tj == 4) return launch_shape<4, 3>(m, tp, n, n_rchunks, s);
+    if (tj == 8) return launch_shape<8, 2>(m, tp, n, n_rchunks, s);
+    if (tj == 16) return launch_shape<16, 1>(m, tp, n, n_rchunks, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace zda

@@ -1,0 +1,37 @@
+// Fused leap-frog step on TMA-staged (r, phi, z) tiles (zda_tile.cu).
+#pragma once
+#include <cuda.h>
+#include "zda_internal.h"
+
+namespace zda {
+
+// Tensor maps of one field buffer ([n_r][n_phi][n_z] complex FP32 per
+// component, seen as FP32 with dims (2 n_z, n_phi, n_r)): the E slab and H
+// slab of a tile at one radius, and the one-row boxes that fetch the
+// phi-wrapped halo rows.
+struct TileMaps {
+    CUtensorMap e[3], ew[3], h[3], hw[3];
+};
+
+struct TileParams {
+    StepParams p;                 // tables, E-side CPML (updated in place), density, source, DFT history
+    float2 *oE[3], *oH[3];        // destination buffer: E^{n+1}, H^{n+1/2}
+    const float2 *psH_in[4];      // H-side CPML auxiliaries at n-1/2: hr_z, hp_z, hp_r, hz_r
+    float2 *psH_out[4];           // ... at n+1/2 (the other set)
+    int *err;                     // error word: a bounded wait gave up
+    int wait_limit;               // polls of the tile's mbarrier before giving up
+};
+
+// tile shapes compiled: tj in {4, 8, 16} phi rows, 32 z-cells; each thread block streams
+// over a range of radii (n_rchunks ranges per tile column)
+bool tile_shape_ok(int tj);
+constexpr int TILE_KZ = 32;
+size_t tile_smem_bytes(int tj);
+int tile_blocks_per_sm(int tj);
+int tile_auto_rchunks(int tj, int nr, int nphi, int nz, int sms);
+// false if the driver's tensor-map encoder is unavailable or refuses the layout
+bool encode_tile_maps(TileMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
+                      const char **why);
+cudaError_t launch_tile_step(const TileMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s);
+
+}  // namespace zda

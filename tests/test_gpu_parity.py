@@ -24,13 +24,16 @@ GRAD_TOL = 1e-3
 
 
 KERNELS = {"split": (0, 2, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0),
-           "fused2_ir3": (1, 2, 3)}
+           "fused2_ir3": (1, 2, 3), "tile8": (3, 8, 0), "tile4": (3, 4, 0), "tile16": (3, 16, 0),
+           "tile8_r5": (3, 8, 5)}
 
 
 def _zone(spec, kernel=None):
     from paper_2501_07979_gb300 import Zone
     if kernel is not None and KERNELS[kernel][0] == 1 and (spec.n_z % 2 or spec.n_fold == 0):
         pytest.skip("the fused step needs an even n_z and an annular zone")
+    if kernel is not None and KERNELS[kernel][0] == 3 and (spec.n_z % 2 or spec.pml_z % 2 or spec.n_fold == 0):
+        pytest.skip("the tile step needs even n_z and pml_z and an annular zone")
     z = Zone(spec, device=0)
     if kernel is not None:
         z.set_kernel(*KERNELS[kernel])
@@ -66,6 +69,12 @@ RAGGED = {
                         wavelengths=(0.85, 1.0, 1.2), filter_radius=0.2, beta=3.0, pulse_sigma=0.4,
                         pulse_t0=1.6),
     "ragged_even": zone_tiny(n_r=27, n_phi=7, n_z=46, pml_r_in=3, pml_r_out=5, pml_z=5, n_steps=250,
+                             layer_k0=(0, 15, 19), design_k0=15, design_k1=19, source_k=8, monitor_k=26,
+                             wavelengths=(0.85, 1.0, 1.2), filter_radius=0.2, beta=3.0, pulse_sigma=0.4,
+                             pulse_t0=1.6),
+    # several tiles of the tile step in every direction, each with a ragged tail (13 phi rows, 46
+    # z-cells, 27 radii), odd r-PML widths
+    "ragged_tile": zone_tiny(n_r=27, n_phi=13, n_z=46, pml_r_in=3, pml_r_out=5, pml_z=6, n_steps=250,
                              layer_k0=(0, 15, 19), design_k0=15, design_k1=19, source_k=8, monitor_k=26,
                              wavelengths=(0.85, 1.0, 1.2), filter_radius=0.2, beta=3.0, pulse_sigma=0.4,
                              pulse_t0=1.6),
@@ -189,10 +198,11 @@ GRAD_SPECS = {
     "tiny2": zone_tiny(n_steps=700, filter_radius=0.25, beta=4.0, wavelengths=(0.9, 1.1),
                        pulse_sigma=0.4, pulse_t0=1.6),
     "ragged3": RAGGED["ragged_even"].replace(n_steps=500),
+    "ragged_tile3": RAGGED["ragged_tile"].replace(n_steps=500),
 }
 
 
-@pytest.mark.parametrize("kernel", ["split", "split1", "fused2", "fused4"])
+@pytest.mark.parametrize("kernel", ["split", "split1", "fused2", "fused4", "tile8", "tile4", "tile8_r5"])
 @pytest.mark.parametrize("name", list(GRAD_SPECS))
 def test_gradient_matches_oracle(name, kernel):
     spec = GRAD_SPECS[name]
