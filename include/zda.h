@@ -269,6 +269,25 @@ zda_status zda_zone_set_wait_limit(zda_zone *zone, int polls, int inject_timeout
 zda_status zda_zone_set_timing(zda_zone *zone, int every);
 zda_status zda_zone_timing(zda_zone *zone, double *ms3_host, long long *count_host);
 
+/* Decay probe of forward runs (section "Differentiable FDTD in cylindrical
+ * coordinates": the gradient is assembled from the running DFTs of one
+ * forward and one adjoint run, which is exact once the time-domain fields
+ * have died out by the last step).  With every > 0, each zda_forward (or
+ * zda_iteration, or lens forward) records after steps every, 2 every, ...
+ *   W    = sum over E sites of eps |E|^2 V + sum over H sites of |H|^2 V,
+ *   Wdot = the same sum over the one-step differences (E^{n+1} - E^n and
+ *          H^{n+1/2} - H^{n-1/2}),
+ * V = r dr dphi dz at the site's radius (E_r, H_phi, H_z at r_{i+1/2}; E_phi,
+ * E_z, H_r at r_i), FP64 sums.  Wdot is the decay measure: a source whose
+ * time integral is not zero leaves a static charge field that never decays
+ * but does not oscillate.  every = 0 (default) turns the probe off.  The
+ * split step copies the state before each sampled step into the fused
+ * step's second field buffer.  zda_zone_energy_trace copies the samples of
+ * the last forward run (n_steps / every of them, at most max_samples) to
+ * host arrays and writes their number (synchronous). */
+zda_status zda_zone_set_energy_probe(zda_zone *zone, int every);
+zda_status zda_zone_energy_trace(zda_zone *zone, double *w_host, double *wdot_host, int max_samples, int *n_samples);
+
 /* Density filter + projection without any device allocation (the paper has
  * no counterpart: this exists for callers that cannot call cudaMalloc, e.g.
  * a program whose device memory belongs to another framework's pool, or a

@@ -483,6 +483,77 @@ def run(spec, geom, eps, n_steps=None, pml=None, src_pat=None, src_time=None, sr
 
 
 # --------------------------------------------------------------------------
+# decay rule: the time-domain fields must have died out by the end of the run
+# --------------------------------------------------------------------------
+def field_energy(spec, geom, eps, state):
+    """Electromagnetic energy of a field state, sum over the Yee sites of
+    eps_s abs(E_s)^2 V_s + abs(H_s)^2 V_s, V = r dr dphi dz with r at the
+    site's radius (E_r, H_phi, H_z at r_{i+1/2}; E_phi, E_z, H_r at r_i).
+    Section "Differentiable FDTD": the frequency-domain adjoint (all
+    frequencies from one forward and one adjoint run) equals the gradient of
+    the running-DFT objective only once the fields have decayed; this is the
+    quantity whose decay is measured (the PML auxiliaries are not fields and
+    are left out)."""
+    s = spec
+    vol_h = (geom.r_h * s.dr * geom.dphi * s.dz)[:, None, None]
+    vol_n = (geom.r_n[:s.n_r] * s.dr * geom.dphi * s.dz)[:, None, None]
+    er, ep, ez = eps
+    a2 = lambda x: np.abs(x) ** 2
+    w = np.sum(er * a2(state[0]) * vol_h) + np.sum(ep * a2(state[1]) * vol_n) + np.sum(ez * a2(state[2]) * vol_n)
+    w += np.sum(a2(state[3]) * vol_n) + np.sum(a2(state[4]) * vol_h) + np.sum(a2(state[5]) * vol_h)
+    return float(w)
+
+
+def energy_trace(spec, rho, n_steps, every, nthreads=0, pml_form=0):
+    """Field energy of the forward run (plane-wave source) after steps
+    every, 2 every, ...: W of the state and Wdot of its one-step difference
+    (E^{n+1} - E^n, H^{n+1/2} - H^{n-1/2}).  The run is cut into chunks that
+    carry the full state (fields and PML auxiliaries), so the trace is that of
+    one uninterrupted run.  Returns (steps, W, Wdot).
+
+    Wdot is the decay measure.  The sheet source's pulse has a nonzero time
+    integral, so the run leaves a static charge whose field never decays; a
+    static field has no one-step difference and no component at the DFT
+    frequencies +-w, while every oscillating field does."""
+    geom = Geometry(spec)
+    pml = cpml_coefficients(spec, geom, metric=bool(pml_form))
+    rt = rho_tilde(spec, geom, np.asarray(rho, dtype=np.float64))
+    eps = site_eps(spec, geom, rt)
+    state = np.zeros((N_STATE, spec.n_r, spec.n_phi, spec.n_z), np.complex128)
+    pat = plane_wave_pattern(spec, geom)
+
+    def advance(n0, n1):
+        t_half = geom.dt * (np.arange(n0, n1) + 0.5)
+        src_t = pulse(spec, t_half)[:, None].astype(np.complex128)
+        run(spec, geom, eps, n_steps=n1 - n0, pml=pml, src_pat=pat, src_time=src_t, state=state,
+            nthreads=nthreads)
+
+    steps, ws, wds = [], [], []
+    n0 = 0
+    while n0 + every <= n_steps:
+        n1 = n0 + every
+        if n1 - 1 > n0:
+            advance(n0, n1 - 1)
+        prev = state[:6].copy()
+        advance(n1 - 1, n1)
+        steps.append(n1)
+        ws.append(field_energy(spec, geom, eps, state))
+        wds.append(field_energy(spec, geom, eps, state[:6] - prev))
+        n0 = n1
+    return np.array(steps), np.array(ws), np.array(wds)
+
+
+def decay_steps(steps, wdot, tol=1e-8):
+    """The decay rule: the first sampled step after the peak of Wdot at which
+    Wdot is at most tol times that peak (None if the trace never gets there)."""
+    steps = np.asarray(steps)
+    w = np.asarray(wdot)
+    k = int(np.argmax(w))
+    below = np.nonzero(w[k:] <= tol * w[k])[0]
+    return int(steps[k + below[0]]) if below.size else None
+
+
+# --------------------------------------------------------------------------
 # a6/a7: near-to-far focal transform and objective
 # --------------------------------------------------------------------------
 def focal_weights(spec, geom):

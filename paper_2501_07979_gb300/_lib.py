@@ -83,6 +83,8 @@ SIGNATURES = {
     "zda_zone_time_steps": (_i, [_vp, _i, _dp, _vp]),
     "zda_zone_set_timing": (_i, [_vp, _i]),
     "zda_zone_timing": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "zda_zone_set_energy_probe": (_i, [_vp, _i]),
+    "zda_zone_energy_trace": (_i, [_vp, _dp, _dp, _i, ctypes.POINTER(_i)]),
     "zda_filter_project_noalloc": (_i, [ctypes.POINTER(ZoneDesc), _vp, _vp, _vp]),
     "zda_lens_create": (_i, [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "zda_lens_destroy": (None, [_vp]),

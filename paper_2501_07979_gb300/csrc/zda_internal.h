@@ -149,6 +149,9 @@ void launch_site_gradient(const float2 *des_f, const float2 *des_a, const float 
                           int nk, double r_lo, double dr, double vol_scale, float *site_grad, cudaStream_t s);
 void launch_cell_gradient(const float *site_grad, int nr, int nphi, int nk, int i_d0, int nrd, float deps,
                           float *g_t, cudaStream_t s);
+// decay probe: field energy of the state cur and of cur - prev
+void launch_field_energy(const StepParams &p, const Fields &cur, const Fields &prev, double r_lo, double dr,
+                         double vol_dphi_dz, double *partial, double *w_out, double *wdot_out, cudaStream_t s);
 void launch_fill_status_check(const float *x, size_t n, int *status, cudaStream_t s);
 void launch_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, int *status, cudaStream_t s);
 // cross != 0 (n_fold 1 or 2): the transmitted intensity keeps the +-1 cross term

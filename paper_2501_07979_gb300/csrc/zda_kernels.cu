@@ -439,6 +439,84 @@ __global__ void k_rho_bar(const float *__restrict__ rho_t, int nr, int nphi, int
     rb_z[ix] = 0.25f * (cmm + cm0 + c0m + c00);
 }
 
+// Field energy of the current state and of its one-step difference (decay
+// probe): per radius i (one block), sum over the sites of eps |E|^2 V and
+// |H|^2 V, V = r dr dphi dz with r the site's radius (E_r, H_phi, H_z at
+// r_{i+1/2}; E_phi, E_z, H_r at r_i), for cur and for cur - prev; FP64
+// block sums into partial[2 i], partial[2 i + 1].
+__global__ void k_field_energy(const StepParams p, const Fields fc, const Fields fp, double r_lo, double dr,
+                               double vol_dphi_dz, double *partial)
+{
+    const float2 *cur[6] = {fc.Er, fc.Ep, fc.Ez, fc.Hr, fc.Hp, fc.Hz};
+    const float2 *prev[6] = {fp.Er, fp.Ep, fp.Ez, fp.Hr, fp.Hp, fp.Hz};
+    const int i = blockIdx.x;
+    const int nphi = p.nphi, nz = p.nz;
+    const size_t base = (size_t)i * nphi * nz;
+    const double rn = r_lo + i * dr, rh = r_lo + (i + 0.5) * dr;
+    double w = 0.0, wd = 0.0;
+    for (int t = threadIdx.x; t < nphi * nz; t += blockDim.x) {
+        const int j = t / nz, k = t % nz;
+        const size_t c = base + t, ij = (size_t)i * nphi + j;
+        const float er = p.t.a_n[k] + p.t.d_n[k] * p.rb_r[ij];
+        const float ep = p.t.a_n[k] + p.t.d_n[k] * p.rb_p[ij];
+        const float ez = p.t.a_c[k] + p.t.d_c[k] * p.rb_z[ij];
+        const double wgt[6] = {er * rh, ep * rn, ez * rn, rn, rh, rh};
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const float2 a = cur[f][c], b = prev[f][c];
+            const float dx = a.x - b.x, dy = a.y - b.y;
+            w += wgt[f] * ((double)a.x * a.x + (double)a.y * a.y);
+            wd += wgt[f] * ((double)dx * dx + (double)dy * dy);
+        }
+    }
+    __shared__ double sw[256], sd[256];
+    sw[threadIdx.x] = w;
+    sd[threadIdx.x] = wd;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sw[threadIdx.x] += sw[threadIdx.x + o];
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * i] = sw[0] * dr * vol_dphi_dz;
+        partial[2 * i + 1] = sd[0] * dr * vol_dphi_dz;
+    }
+}
+
+__global__ void k_field_energy_sum(const double *partial, int nr, double *w_out, double *wdot_out)
+{
+    __shared__ double sw[256], sd[256];
+    double w = 0.0, wd = 0.0;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        w += partial[2 * i];
+        wd += partial[2 * i + 1];
+    }
+    sw[threadIdx.x] = w;
+    sd[threadIdx.x] = wd;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sw[threadIdx.x] += sw[threadIdx.x + o];
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *w_out = sw[0];
+        *wdot_out = sd[0];
+    }
+}
+
+void launch_field_energy(const StepParams &p, const Fields &cur, const Fields &prev, double r_lo, double dr,
+                         double vol_dphi_dz, double *partial, double *w_out, double *wdot_out, cudaStream_t s)
+{
+    k_field_energy<<<p.nr, 256, 0, s>>>(p, cur, prev, r_lo, dr, vol_dphi_dz, partial);
+    k_field_energy_sum<<<1, 256, 0, s>>>(partial, p.nr, w_out, wdot_out);
+}
+
 void launch_rho_bar(const float *rho_t, int nr, int nphi, int i_d0, int i_d1, float *rb_r, float *rb_p,
                     float *rb_z, cudaStream_t s)
 {

@@ -227,6 +227,24 @@ class Zone:
         check(_lib.lib().zda_zone_timing(self.handle, ms, ctypes.byref(n)))
         return list(ms), n.value
 
+    def set_energy_probe(self, every):
+        """Record the field energy W and the energy of the one-step difference
+        Wdot after every `every`-th step of each forward run (0: off)."""
+        check(_lib.lib().zda_zone_set_energy_probe(self.handle, int(every)))
+        self._probe_every = int(every)
+
+    def energy_trace(self, max_samples=1 << 20):
+        """(steps, W, Wdot) of the last forward run's decay probe."""
+        n = ctypes.c_int()
+        m = int(min(max_samples, max(1, self.spec.n_steps)))
+        w = (ctypes.c_double * m)()
+        wd = (ctypes.c_double * m)()
+        check(_lib.lib().zda_zone_energy_trace(self.handle, w, wd, m, ctypes.byref(n)))
+        k = n.value
+        every = self._probe_every if getattr(self, "_probe_every", 0) else 1
+        steps = every * (np.arange(k) + 1)
+        return steps, np.array(w[:k]), np.array(wd[:k])
+
     @property
     def launches(self):
         return int(_lib.lib().zda_zone_launch_count(self.handle))

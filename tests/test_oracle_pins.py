@@ -363,6 +363,57 @@ def test_T7_adjoint_gradient_matches_central_differences():
     assert _directional_error(_fd_spec()) < 1e-3
 
 
+# ---------------------------------------------------------------- decay rule, high contrast
+def _hc_spec(n_steps):
+    # TiO2 (eps 5.76) design layer on SiO2 (eps 2.1): the high-contrast stack of
+    # the single-zone and wide-zone workloads, which supports guided modes
+    return zone_tiny(n_steps=n_steps, courant=0.9, filter_radius=0.25, beta=4.0,
+                     wavelengths=(0.9, 1.1), pulse_sigma=0.4, pulse_t0=1.6, eps_hi=5.76)
+
+
+def test_field_energy_closed_form():
+    """W of E_r = 1 everywhere (eps 1): sum of r_{i+1/2} dr dphi dz over the
+    wedge = tau (r_hi^2 - r_lo^2) / 2 * n_z dz (the midpoint rule is exact)."""
+    s = zone_tiny()
+    g = O.Geometry(s)
+    st = np.zeros((O.N_STATE, s.n_r, s.n_phi, s.n_z), complex)
+    st[0] = 1.0
+    ones = np.ones((s.n_r, s.n_phi, s.n_z))
+    r1 = s.r_lo + s.n_r * s.dr
+    want = g.tau * (r1 ** 2 - s.r_lo ** 2) / 2 * s.n_z * s.dz
+    assert abs(O.field_energy(s, g, (ones, ones, ones), st) / want - 1) < 1e-12
+    st[0] = 0.0
+    st[4] = 2.0                                  # H_phi at r_{i+1/2}: 4 x the same sum
+    assert abs(O.field_energy(s, g, (ones, ones, ones), st) / (4 * want) - 1) < 1e-12
+
+
+def test_decay_rule_on_high_contrast_zone():
+    """The decay measure Wdot (energy of the one-step difference) falls below
+    1e-8 of its peak within the run, while W keeps the static field of the
+    source's nonzero time integral (a plateau above 1e-3 of its peak)."""
+    s = _hc_spec(10000)
+    rho = smoothed_rho(s.n_r_design, s.n_phi, 7, mode="minmax")
+    st, w, wd = O.energy_trace(s, rho, 10000, 250)
+    T = O.decay_steps(st, wd)
+    assert T is not None and 2000 < T < 10000, T
+    assert w[-1] / w.max() > 1e-3                # static field: no decay of W
+    assert O.decay_steps(st, w) is None
+    assert np.all(wd[st >= T] <= 2e-8 * wd.max())
+
+
+def test_T7_high_contrast_gradient_matches_central_differences():
+    """FD check of the adjoint on the high-contrast (TiO2 on SiO2) stack, run
+    for the decay rule's T (Wdot <= 1e-8 of its peak): per pixel <= 2e-3 of
+    max abs(g), directional <= 1e-3 (measured 4e-4 and 2e-5)."""
+    probe = _hc_spec(12000)
+    rho = smoothed_rho(probe.n_r_design, probe.n_phi, 7, mode="minmax")
+    st, _, wd = O.energy_trace(probe, rho, 12000, 250)
+    s = probe.replace(n_steps=O.decay_steps(st, wd))
+    errs = _fd_errors(s, _FD_PIXELS)
+    assert errs.max() < 2e-3, errs
+    assert _directional_error(s) < 1e-3
+
+
 def test_T7_pin_detects_continuous_omega(monkeypatch):
     """Planted mistake: using w instead of wt = (2/dt) sin(w dt/2) in the
     adjoint (a ~0.5 % scaling at this dt) must break the directional check."""
