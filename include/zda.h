@@ -58,6 +58,7 @@ typedef enum {
 
 #define ZDA_MAX_LAYERS 8
 #define ZDA_MAX_FREQ 16      /* signed frequencies = 2 x wavelengths */
+#define ZDA_MAX_FILTER_TAPS 65536   /* conic-filter taps per pixel, (2 di + 1)(2 dj + 1) */
 
 typedef struct zda_ctx zda_ctx;
 typedef struct zda_zone zda_zone;
@@ -80,6 +81,10 @@ typedef struct zda_lens zda_lens;
  * E_r/E_phi plane source_k, the monitor on plane monitor_k (both above the
  * z-PML).  dt = courant / sqrt(1/dr^2 + 1/(r_lo dphi)^2 + 1/dz^2).
  * filter_radius <= 0 disables the conic filter, beta <= 0 the projection.
+ * The filter spans di = min(floor(R / dr), n_r_design - 1) radial and
+ * dj = floor(R / (r_c dphi)) azimuthal neighbours (r_c: the first design
+ * row's radius); a radius with (2 di + 1)(2 dj + 1) > ZDA_MAX_FILTER_TAPS is
+ * refused (ZDA_ERR_ARG).
  * focal is the focal distance above the top of the design layer. */
 typedef struct {
     double r_lo, dr, dz;
@@ -297,10 +302,13 @@ zda_status zda_zone_energy_trace(zda_zone *zone, double *w_host, double *wdot_ho
  * rho_tilde_dev the output (device, current device), stream a cudaStream_t.
  * Scratch (the filter's per-row weight sums) is a fixed 64 KiB device array
  * inside the library: n_r_design is limited to 16384 rows (ZDA_ERR_ARG
- * beyond).  The first call on each device looks up that array's device
- * address (with that device current); make that first call before any
- * stream capture.  All calls on a device share the array: calls whose
- * kernels overlap on the GPU race.  Allocates nothing. */
+ * beyond).  Accepts what zda_zone_create accepts (wedge zones and the axis
+ * zone), including its bound of ZDA_MAX_FILTER_TAPS filter taps per pixel.
+ * The first call on each device looks up that array's device address (with
+ * that device current) and keeps it; make that first call before any stream
+ * capture, and do not use this call on a device after cudaDeviceReset in the
+ * same process.  All calls on a device share the array: calls whose kernels
+ * overlap on the GPU race.  Allocates nothing. */
 zda_status zda_filter_project_noalloc(const zda_zone_desc *desc, const float *rho_dev, float *rho_tilde_dev,
                                       void *stream);
 

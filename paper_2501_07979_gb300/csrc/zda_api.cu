@@ -519,9 +519,16 @@ static zda_status derive(zda_zone &z)
     z.nrd = z.i_d1 - z.i_d0;
     z.nk = d.design_k1 - d.design_k0 + 1;
     if (d.filter_radius > 0) {
-        z.di_max = (int)std::floor(d.filter_radius / d.dr);
+        // taps past the design rows are dropped, so di_max never needs to exceed n_r_design - 1;
+        // the tap count is capped (a radius of many cells would make the filter kernel run for ages)
         const double rc0 = d.r_lo + (z.i_d0 + 0.5) * d.dr;
-        z.dj_max = (int)std::floor(d.filter_radius / (rc0 * z.dphi));
+        const double di = std::floor(d.filter_radius / d.dr), dj = std::floor(d.filter_radius / (rc0 * z.dphi));
+        const double taps = (2 * std::min(di, (double)(z.nrd - 1)) + 1) * (2 * dj + 1);
+        if (!(taps <= ZDA_MAX_FILTER_TAPS))
+            return fail(ZDA_ERR_ARG, "filter_radius spans " + std::to_string(taps) + " taps per pixel (limit " +
+                                         std::to_string(ZDA_MAX_FILTER_TAPS) + ")");
+        z.di_max = (int)std::min(di, (double)(z.nrd - 1));
+        z.dj_max = (int)dj;
     } else {
         z.di_max = z.dj_max = 0;
     }

@@ -12,12 +12,16 @@
 // compiled into the library.
 //
 // That array (ZDA_NOALLOC_MAX_ROWS floats, 64 KiB) exists on every GPU that
-// loads the library, for the lifetime of the process.  All calls on a device
+// loads the library, for the lifetime of the process.  Its device address is
+// looked up once per device and kept: after a cudaDeviceReset the module may
+// be loaded again at another address, so this entry point must not be used
+// on a device after cudaDeviceReset in the same process.  All calls on a device
 // share it: every call rewrites the rows it reads before reading them (nothing
 // needs to start at zero), and two calls whose kernels overlap on the GPU
 // (e.g. on different streams without ordering) race on it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -103,13 +107,31 @@ extern "C" zda_status zda_filter_project_noalloc(const zda_zone_desc *d, const f
                                                  float *rho_tilde_dev, void *stream)
 {
     if (!d || !rho_dev || !rho_tilde_dev) return na_fail(ZDA_ERR_ARG, "null argument");
-    if (d->n_fold < 1 || d->n_phi < 1 || d->dr <= 0 || d->r_lo <= 0)
-        return na_fail(ZDA_ERR_ARG, "annular zone needs n_fold >= 1, n_phi >= 1, dr > 0, r_lo > 0");
+    // the checks of zda_zone_create that concern the filter: wedge zones and
+    // the axis zone (continuous axisymmetry: n_fold = 0, one phi cell)
+    const bool bor = d->n_fold == 0;
+    if (d->n_fold < 0 || d->n_phi < 1 || d->n_r < 2 || d->dr <= 0)
+        return na_fail(ZDA_ERR_ARG, "zone needs n_r >= 2, n_phi >= 1, n_fold >= 0, dr > 0");
+    if (bor && (d->n_phi != 1 || d->r_lo < 0))
+        return na_fail(ZDA_ERR_ARG, "continuous axisymmetry (n_fold = 0) needs n_phi = 1 and r_lo >= 0");
+    if (!bor && d->r_lo <= 0) return na_fail(ZDA_ERR_ARG, "a wedge zone (n_fold > 0) needs r_lo > 0");
+    if (d->pml_r_in < 0 || d->pml_r_out < 0 || d->pml_r_in + d->pml_r_out >= d->n_r)
+        return na_fail(ZDA_ERR_ARG, "PML widths do not fit the grid");
     const int nrd = d->n_r - d->pml_r_in - d->pml_r_out;
-    if (nrd < 1) return na_fail(ZDA_ERR_ARG, "no design rows");
     if (nrd > ZDA_NOALLOC_MAX_ROWS)
         return na_fail(ZDA_ERR_ARG, "n_r_design = " + std::to_string(nrd) + " exceeds the no-allocation limit of " +
                                         std::to_string(ZDA_NOALLOC_MAX_ROWS) + " rows");
+    const double dphi = 2.0 * M_PI / (bor ? 1 : d->n_fold) / d->n_phi;
+    const double rc0 = d->r_lo + (d->pml_r_in + 0.5) * d->dr;
+    double di = 0, dj = 0;
+    if (d->filter_radius > 0) {                  // the same tap bound as zda_zone_create
+        di = std::min(std::floor(d->filter_radius / d->dr), (double)(nrd - 1));
+        dj = std::floor(d->filter_radius / (rc0 * dphi));
+        const double taps = (2 * di + 1) * (2 * dj + 1);
+        if (!(taps <= ZDA_MAX_FILTER_TAPS))
+            return na_fail(ZDA_ERR_ARG, "filter_radius spans " + std::to_string(taps) + " taps per pixel (limit " +
+                                            std::to_string(ZDA_MAX_FILTER_TAPS) + ")");
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(ZDA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -128,21 +150,17 @@ extern "C" zda_status zda_filter_project_noalloc(const zda_zone_desc *d, const f
         norm = g_norm_ptr[dev];
     }
     NaParams p{};
-    const double dphi = 2.0 * M_PI / d->n_fold / d->n_phi;
     p.nrd = nrd;
     p.nphi = d->n_phi;
     p.dr = (float)d->dr;
     p.dphi = (float)dphi;
     p.R = (float)d->filter_radius;
-    p.r_c0 = (float)(d->r_lo + (d->pml_r_in + 0.5) * d->dr);
+    p.r_c0 = (float)rc0;
     p.beta = (float)d->beta;
     p.eta = (float)d->eta;
     p.filter_on = d->filter_radius > 0 ? 1 : 0;
-    if (p.filter_on) {
-        const double rc0 = d->r_lo + (d->pml_r_in + 0.5) * d->dr;
-        p.di_max = (int)std::floor(d->filter_radius / d->dr);
-        p.dj_max = (int)std::floor(d->filter_radius / (rc0 * dphi));
-    }
+    p.di_max = (int)di;
+    p.dj_max = (int)dj;
     cudaStream_t s = (cudaStream_t)stream;
     if (p.filter_on) k_na_norm<<<(nrd + 127) / 128, 128, 0, s>>>(p, norm);
     dim3 g((p.nphi + 127) / 128, nrd);

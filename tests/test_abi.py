@@ -126,3 +126,26 @@ def test_surrogate_descriptor_checks_and_sizes_need_no_gpu(libpath):
     # unbound: calls that need the workspace report a state error
     assert L.zda_nn_adam(h, 1e-3, 0.9, 0.999, 1e-8, None) == _lib.ERR_STATE
     L.zda_nn_destroy(h)
+
+
+def test_filter_radius_beyond_the_tap_limit_is_refused(libpath):
+    """A conic-filter radius spanning more than ZDA_MAX_FILTER_TAPS taps per
+    pixel is refused by zone creation and by the allocation-free filter call
+    (host-side checks, before any device work)."""
+    from paper_2501_07979_gb300 import _lib
+    from paper_2501_07979_gb300.zone import make_desc
+    from zda_inputs import zone_tiny
+    L = _lib.load(libpath)
+    big = zone_tiny(filter_radius=150.0)          # 31 x 2803 taps: the radial span is clipped to the design rows
+    ok = zone_tiny(filter_radius=0.25)
+    ctx = ctypes.create_string_buffer(64)         # zone creation only stores the context pointer
+    h = ctypes.c_void_p()
+    assert L.zda_zone_create(ctx, ctypes.byref(make_desc(big)), ctypes.byref(h)) == _lib.ERR_ARG
+    assert b"taps" in L.zda_last_error()
+    assert L.zda_zone_create(ctx, ctypes.byref(make_desc(ok)), ctypes.byref(h)) == _lib.OK
+    L.zda_zone_destroy(h)
+    x = ctypes.c_void_p(16)                       # never dereferenced: the call fails first
+    assert L.zda_filter_project_noalloc(ctypes.byref(make_desc(big)), x, x, None) == _lib.ERR_ARG
+    assert b"taps" in L.zda_last_error()
+    neg = zone_tiny(pml_r_in=-2)
+    assert L.zda_filter_project_noalloc(ctypes.byref(make_desc(neg)), x, x, None) == _lib.ERR_ARG

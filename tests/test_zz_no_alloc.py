@@ -21,13 +21,15 @@ pytestmark = pytest.mark.gpu
 TOL = 5e-6       # same as the filter/projection parity tests
 
 
-@pytest.mark.parametrize("which", ["wide", "ragged"])
+@pytest.mark.parametrize("which", ["wide", "ragged", "axis"])
 def test_noalloc_filter_project_matches_workspace_entry_point(which):
     from paper_2501_07979_gb300 import Zone, _lib, make_desc
     if which == "wide":
         spec = zone_cfg2(n_steps=10)
-    else:
+    elif which == "ragged":
         spec = zone_tiny(n_r=27, n_phi=7, pml_r_in=3, pml_r_out=5, filter_radius=0.2, beta=3.0, n_steps=10)
+    else:                                                        # continuous axisymmetry, axis inside
+        spec = zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0, filter_radius=0.25, beta=4.0, n_steps=10)
     desc = make_desc(spec)
     L = _lib.lib()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
