@@ -67,13 +67,18 @@ class ShardedLens:
         self.group = group
 
     def _allreduce(self, x):
+        """Sum of the ranks' phasors (2 x n_freq float64).  NCCL reduces device
+        tensors only: under it the buffer goes to this rank's current CUDA
+        device; gloo reduces it on the host."""
         import torch
         import torch.distributed as dist
         if not dist.is_available() or not dist.is_initialized():
             return x
         t = torch.from_numpy(np.ascontiguousarray(np.stack([x.real, x.imag], 1)))
+        if dist.get_backend(self.group) == "nccl":
+            t = t.to("cuda:%d" % torch.cuda.current_device())
         dist.all_reduce(t, group=self.group)
-        a = t.numpy()
+        a = t.cpu().numpy()
         return a[:, 0] + 1j * a[:, 1]
 
     def forward(self, rhos):

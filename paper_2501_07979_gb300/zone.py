@@ -66,6 +66,24 @@ def context(device=0):
     return _CTX[device]
 
 
+def zone_info(spec, device=0):
+    """The derived quantities of a zone description (dt, dphi, tau, n_freq,
+    n_r_design, design_nk, workspace_bytes, cells) from zda_zone_query,
+    without binding a workspace (nothing is allocated on the device)."""
+    ctx = context(device)
+    L = _lib.lib()
+    h = ctypes.c_void_p()
+    check(L.zda_zone_create(ctx.handle, ctypes.byref(make_desc(spec)), ctypes.byref(h)))
+    try:
+        lam = (ctypes.c_double * len(spec.wavelengths))(*[float(x) for x in spec.wavelengths])
+        check(L.zda_set_wavelengths(h, lam, len(spec.wavelengths)))
+        info = _lib.ZoneInfo()
+        check(L.zda_zone_query(h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in _lib.ZoneInfo._fields_}
+    finally:
+        L.zda_zone_destroy(h)
+
+
 class Zone:
     """One annular zone's n-fold wedge on one GPU (see include/zda.h)."""
 

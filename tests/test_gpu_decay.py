@@ -1,0 +1,61 @@
+"""Decay rule on the GPU: the library's field-energy probe against the
+oracle, and the adjoint gradient of the high-contrast zones against central
+differences of the GPU forward.
+
+The hybrid time/frequency adjoint ("Differentiable FDTD in cylindrical
+coordinates") is the gradient of the running-DFT objective once the fields
+have died out by the last step.  The decay measure is Wdot, the energy of
+the one-step difference of the fields (the source's nonzero time integral
+leaves a static charge field, which does not oscillate and never decays)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from zda_inputs import zone_tiny, smoothed_rho
+
+pytestmark = pytest.mark.gpu
+
+
+def _hc(n_steps):
+    return zone_tiny(n_steps=n_steps, courant=0.9, filter_radius=0.25, beta=4.0, wavelengths=(0.9, 1.1),
+                     pulse_sigma=0.4, pulse_t0=1.6, eps_hi=5.76)
+
+
+@pytest.mark.parametrize("kernel", [(0, 2, 0), (3, 4, 0), (1, 2, 0)])
+def test_energy_probe_matches_oracle(kernel):
+    from paper_2501_07979_gb300 import Zone
+    spec = _hc(6000)
+    rho = smoothed_rho(spec.n_r_design, spec.n_phi, 7, mode="minmax")
+    st, w, wd = O.energy_trace(spec, rho, 6000, 250)
+    z = Zone(spec, device=0)
+    z.set_kernel(*kernel)
+    z.set_energy_probe(250)
+    z.forward(torch.tensor(rho, dtype=torch.float32, device="cuda:0"))
+    s2, w2, wd2 = z.energy_trace()
+    assert np.array_equal(s2, st)
+    assert np.abs(w2 / w - 1).max() < 1e-4
+    m = wd > 1e-6 * wd.max()                       # FP32 one-step differences below that are rounding
+    assert np.abs(wd2[m] / wd[m] - 1).max() < 1e-3
+    assert O.decay_steps(s2, wd2) == O.decay_steps(st, wd)
+
+
+def test_high_contrast_gradient_at_decay_against_gpu_central_differences():
+    """TiO2-on-SiO2 zone run for the decay rule's T: the GPU adjoint against
+    central differences of the GPU forward along the gradient and along a
+    seeded random direction (FP32 forward: directional steps, whose signal is
+    far above the single-precision noise of I)."""
+    from paper_2501_07979_gb300 import Zone
+    probe = _hc(12000)
+    rho = smoothed_rho(probe.n_r_design, probe.n_phi, 7, mode="minmax")
+    st, _, wd = O.energy_trace(probe, rho, 12000, 250)
+    spec = probe.replace(n_steps=O.decay_steps(st, wd))
+    z = Zone(spec, device=0)
+    r = torch.tensor(rho, dtype=torch.float32, device="cuda:0")
+    I, g = z.iteration(r)
+    u = torch.tensor(np.random.default_rng(3).standard_normal(rho.shape), dtype=torch.float32, device="cuda:0")
+    for d in (g / g.norm(), u / u.norm()):
+        h = 0.01                                   # O(h^2) truncation 1e-4 (FP64 oracle, same zone)
+        fd = (2 * np.sum(np.abs(z.forward(r + h * d)) ** 2) - 2 * np.sum(np.abs(z.forward(r - h * d)) ** 2)) / (2 * h)
+        want = float((g * d).sum().item())
+        assert abs(fd / want - 1) < 1e-3, (fd, want)
