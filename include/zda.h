@@ -215,12 +215,17 @@ long long zda_zone_launch_count(const zda_zone *zone);
 /* Time-step kernel of the zone.  variant 0 (default): two launches per step
  * (H update, E update), in place, two z-cells per thread with 16-byte loads
  * when n_z and pml_z are even (wedge zones), else one z-cell per thread;
- * variant 2: the same with one z-cell per thread always.  variant 1 (annular
- * zones, n_z <= 256):
- * one fused launch per step (E and H updated together, ping-pong field
- * buffers, streaming along r; tile_phi in {2, 4} phi rows per thread block,
- * i_ranges radius ranges per phi tile, 0 = as many as fit in one wave).
- * Both compute the same scheme; results agree to FP32 rounding. */
+ * tile_phi in {4, 8, 16, 32} is the thread block's phi rows (256 threads;
+ * other values: 16).  variant 2: the same with one z-cell per thread always.
+ * variant 1 (annular zones, n_z <= 256): one fused launch per step (E and H
+ * updated together, ping-pong field buffers, streaming along r; tile_phi in
+ * {2, 4} phi rows per thread block, i_ranges radius ranges per phi tile,
+ * 0 = as many as fit in one wave).  variant 3 (annular zones, even n_z and
+ * pml_z, real-radius r-PML): one fused launch per step on tiles of tile_phi
+ * in {4, 8, 16} phi rows x 32 z-cells staged into shared memory by TMA tensor
+ * copies, each thread block streaming over one of i_ranges radius ranges
+ * (0 = about four waves of blocks).  All compute the same scheme; results
+ * agree to FP32 rounding. */
 zda_status zda_zone_set_kernel(zda_zone *zone, int variant, int tile_phi, int i_ranges);
 zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi, int *i_ranges);
 
@@ -239,8 +244,8 @@ zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi
  *   radius Im r~ < 0 and the wedge's non-propagating azimuthal orders grow).
  *   Reflection of a cylindrical pulse at w0, against a radially larger
  *   domain: 1.9e-3 (form 0) vs 5e-5 (form 1) at r = 10 lambda.
- * Form 1 runs on the split step (variants 0 and 2); the fused step
- * (variant 1) refuses it (ZDA_ERR_ARG either way round).  Takes effect at
+ * Form 1 runs on the split step (variants 0 and 2); the fused steps
+ * (variants 1 and 3) refuse it (ZDA_ERR_ARG either way round).  Takes effect at
  * the next run; a zda_adjoint needs a zda_forward of the same form. */
 zda_status zda_zone_set_radial_pml(zda_zone *zone, int form);
 zda_status zda_zone_get_radial_pml(const zda_zone *zone, int *form);

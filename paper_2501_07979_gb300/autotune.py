@@ -5,8 +5,10 @@ step kernel is timed on the GPU for a few steps (`Zone.time_steps`); the
 fastest is applied to the zone and remembered in a JSON cache keyed by the
 zone's shape (n_r, n_phi, n_z, PML widths) and r-PML form, so zones of the
 same shape in a lens (and later runs) reuse it without timing again.
-Candidates the zone refuses (the fused step with the stretched r-PML) are
-skipped.
+Candidates the zone refuses (the fused steps with the stretched r-PML) are
+skipped.  The candidates are the split step's thread-block shapes (4 to 32
+phi rows), the one-cell split step, the streaming fused step and the
+TMA-tiled fused step's tile rows and radius ranges.
 """
 import json
 import os
@@ -20,12 +22,23 @@ def shape_key(spec):
 
 
 def candidates(spec):
-    cands = [(0, 2, 0), (2, 2, 0)]
+    """(variant, tile_phi, i_ranges) choices for the zone: the split step's
+    thread-block shape (phi rows x z-pairs, 256 threads), the one-cell split
+    step, the streaming fused step, and the TMA-tiled fused step's tile rows
+    and radius ranges."""
+    cands = [(2, 2, 0)]
+    pair = spec.n_z % 2 == 0 and spec.pml_z % 2 == 0 and spec.n_fold > 0
+    if pair:
+        cands += [(0, rows, 0) for rows in (4, 8, 16, 32) if rows <= 2 * max(spec.n_phi, 2)]
+    else:
+        cands.append((0, 16, 0))
     if spec.n_fold > 0 and spec.n_z % 2 == 0 and spec.n_z <= 256:
-        for tj in (2, 4):
-            for ir in (0, 2, 4):
-                cands.append((1, tj, ir))
-    return cands
+        cands += [(1, 2, 0), (1, 4, 0)]
+    if pair:
+        for tj in (4, 8, 16):
+            if tj <= 2 * max(spec.n_phi, 2):
+                cands += [(3, tj, 0), (3, tj, 3 * max(1, spec.n_r // 100))]
+    return sorted(set(cands))
 
 
 def tune_zone(zone, steps=40, cache_path=None, use_cache=True):

@@ -593,6 +593,7 @@ static zda::StepParams step_params(zda_zone &z)
     p.src_scale = (float)(0.5 / d.dz);
     p.des_k0 = d.design_k0;
     p.des_nk = z.nk;
+    p.pair_rows = zda::pair_rows_ok(z.tile_phi) ? z.tile_phi : 16;
     return p;
 }
 

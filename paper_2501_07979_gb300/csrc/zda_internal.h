@@ -102,6 +102,7 @@ struct StepParams {
     // part is stretched and the metric parts are divided by r~ (rm tables)
     int rpml_metric;
     Metric rm;
+    int pair_rows;                             // two-z-cell split kernels: phi rows per thread block (4, 8, 16, 32)
 };
 
 // kernels (zda_kernels.cu)
@@ -109,6 +110,7 @@ void launch_update_h(const StepParams &p, cudaStream_t s);
 void launch_update_e(const StepParams &p, int n, cudaStream_t s);
 // two z-cells per thread (zda_pair.cu): even n_z, even pml_z, wedge zones
 bool pair_kernels_apply(const StepParams &p);
+bool pair_rows_ok(int rows);
 void launch_update_h_pair(const StepParams &p, cudaStream_t s);
 void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s);   // writes the DFT history; see launch_dft_flush
 // Time-blocked running DFT of the split step (two z-cells per thread).

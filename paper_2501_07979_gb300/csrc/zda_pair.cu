@@ -18,8 +18,10 @@
 
 namespace zda {
 
-#define PX 16
-#define PY 16
+// Thread block: PY phi rows x (256 / PY) z-pairs.  PY is a template
+// parameter (4, 8, 16 or 32) chosen per zone by the tile tuner: zones with
+// few phi cells waste no rows with PY = 4 or 8, long z-columns coalesce
+// better with more z-pairs per block.
 
 struct C2 { float2 a, b; };                      // the pair (k, k+1)
 
@@ -49,9 +51,10 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-template <bool RM>
-__global__ void __launch_bounds__(PX * PY, RM ? 3 : 4) k_update_h_pair(const StepParams p)
+template <bool RM, int PY>
+__global__ void __launch_bounds__(256, RM ? 3 : 4) k_update_h_pair(const StepParams p)
 {
+    constexpr int PX = 256 / PY;
     const int kp = blockIdx.x * PX + threadIdx.x;
     const int j = blockIdx.y * PY + threadIdx.y;
     const int i = blockIdx.z;
@@ -187,9 +190,10 @@ __global__ void __launch_bounds__(PX * PY, RM ? 3 : 4) k_update_h_pair(const Ste
     if (ir >= 0) { st4(p.psi.hp_r + rx, ps_pr); st4(p.psi.hz_r + rx, ps_zr); }
 }
 
-template <bool RM>
-__global__ void __launch_bounds__(PX * PY, 2) k_update_e_pair(const StepParams p, const int n)
+template <bool RM, int PY>
+__global__ void __launch_bounds__(256, 2) k_update_e_pair(const StepParams p, const int n)
 {
+    constexpr int PX = 256 / PY;
     const int kp = blockIdx.x * PX + threadIdx.x;
     const int j = blockIdx.y * PY + threadIdx.y;
     const int i = blockIdx.z;
@@ -442,18 +446,44 @@ void launch_adjoint_source_rad(const StepParams &p, int n, cudaStream_t s)
 
 bool pair_kernels_apply(const StepParams &p) { return p.nz % 2 == 0 && p.pz % 2 == 0 && !p.bor; }
 
+template <int PY>
+static void launch_h_py(const StepParams &p, cudaStream_t s)
+{
+    constexpr int PX = 256 / PY;
+    dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
+    if (p.rpml_metric) k_update_h_pair<true, PY><<<g, b, 0, s>>>(p);
+    else k_update_h_pair<false, PY><<<g, b, 0, s>>>(p);
+}
+
+template <int PY>
+static void launch_e_py(const StepParams &p, int n, cudaStream_t s)
+{
+    constexpr int PX = 256 / PY;
+    dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
+    if (p.rpml_metric) k_update_e_pair<true, PY><<<g, b, 0, s>>>(p, n);
+    else k_update_e_pair<false, PY><<<g, b, 0, s>>>(p, n);
+}
+
+bool pair_rows_ok(int rows) { return rows == 4 || rows == 8 || rows == 16 || rows == 32; }
+
 void launch_update_h_pair(const StepParams &p, cudaStream_t s)
 {
-    dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
-    if (p.rpml_metric) k_update_h_pair<true><<<g, b, 0, s>>>(p);
-    else k_update_h_pair<false><<<g, b, 0, s>>>(p);
+    switch (p.pair_rows) {
+    case 4: launch_h_py<4>(p, s); break;
+    case 8: launch_h_py<8>(p, s); break;
+    case 32: launch_h_py<32>(p, s); break;
+    default: launch_h_py<16>(p, s); break;
+    }
 }
 
 void launch_update_e_pair(const StepParams &p, int n, cudaStream_t s)
 {
-    dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
-    if (p.rpml_metric) k_update_e_pair<true><<<g, b, 0, s>>>(p, n);
-    else k_update_e_pair<false><<<g, b, 0, s>>>(p, n);
+    switch (p.pair_rows) {
+    case 4: launch_e_py<4>(p, n, s); break;
+    case 8: launch_e_py<8>(p, n, s); break;
+    case 32: launch_e_py<32>(p, n, s); break;
+    default: launch_e_py<16>(p, n, s); break;
+    }
 }
 
 }  // namespace zda

@@ -200,7 +200,10 @@ class Zone:
         return out
 
     def set_kernel(self, variant=1, tile_phi=2, i_ranges=0):
-        """Time-step kernel: variant 1 fused (tile_phi 2 or 4), 0 split H/E."""
+        """Time-step kernel (zda_zone_set_kernel): 0 split H/E (tile_phi = phi
+        rows per block), 1 fused streaming (tile_phi 2 or 4), 2 split one cell
+        per thread, 3 fused TMA tiles (tile_phi 4, 8 or 16; i_ranges radius
+        ranges)."""
         check(_lib.lib().zda_zone_set_kernel(self.handle, int(variant), int(tile_phi), int(i_ranges)))
 
     def set_radial_pml(self, form):

@@ -23,7 +23,8 @@ FIELD_TOL = 1e-4
 GRAD_TOL = 1e-3
 
 
-KERNELS = {"split": (0, 2, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0),
+KERNELS = {"split": (0, 2, 0), "split_r4": (0, 4, 0), "split_r32": (0, 32, 0), "split1": (2, 2, 0),
+           "fused2": (1, 2, 0), "fused4": (1, 4, 0),
            "fused2_ir3": (1, 2, 3), "tile8": (3, 8, 0), "tile4": (3, 4, 0), "tile16": (3, 16, 0),
            "tile8_r5": (3, 8, 5)}
 
@@ -377,9 +378,10 @@ def test_divergent_run_reports_nonfinite():
         z.forward(_dev(np.zeros((spec.n_r_design, spec.n_phi))))
 
 
-def test_autotuner_times_candidates_and_applies_the_fastest(tmp_path):
+@pytest.mark.parametrize("which", ["wide", "lwir16"])
+def test_autotuner_times_candidates_and_applies_the_fastest(tmp_path, which):
     from paper_2501_07979_gb300.autotune import tune_zone, candidates
-    spec = zone_cfg2(n_steps=100)
+    spec = zone_cfg2(n_steps=100) if which == "wide" else zone_lwir(16, 100)
     z = _zone(spec)
     cache = str(tmp_path / "tiles.json")
     choice, times = tune_zone(z, steps=8, cache_path=cache)
@@ -393,19 +395,35 @@ def test_autotuner_times_candidates_and_applies_the_fastest(tmp_path):
 
 
 # ------------------------------------------------------------------ lens (all zones, one graph)
-def _lens_specs():
+def _lens_specs(n_zones=3):
+    """An axis zone and annular zones of uneven width and fold (n_zones = 3
+    or 8)."""
     base = dict(n_steps=500, filter_radius=0.2, beta=3.0, wavelengths=(0.9, 1.1), pulse_sigma=0.4,
                 pulse_t0=1.6, focal=12.0)
-    return [zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0, n_r=20, **base),
-            zone_tiny(r_lo=1.2, n_fold=12, n_phi=6, n_r=24, **base),
-            zone_tiny(r_lo=3.2, n_fold=24, n_phi=8, n_r=28, **base)]
+    if n_zones == 3:
+        return [zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0, n_r=20, **base),
+                zone_tiny(r_lo=1.2, n_fold=12, n_phi=6, n_r=24, **base),
+                zone_tiny(r_lo=3.2, n_fold=24, n_phi=8, n_r=28, **base)]
+    # interior widths 12, 16, 10, 22, 14, 18, 11, 20 cells (dr = 0.1), folds growing with radius
+    widths = (12, 16, 10, 22, 14, 18, 11, 20)
+    folds = (0, 12, 20, 27, 40, 44, 60, 66)
+    phis = (1, 6, 4, 8, 5, 8, 6, 7)
+    out, r = [], 0.0
+    for w, n, p in zip(widths, folds, phis):
+        if n == 0:
+            out.append(zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0, n_r=w + 4, **base))
+        else:
+            out.append(zone_tiny(r_lo=r - 0.4, n_fold=n, n_phi=p, n_r=w + 8, **base))
+        r += 0.1 * w
+    return out
 
 
+@pytest.mark.parametrize("n_zones", [3, 8])
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("kernel", ["split", "fused2"])
-def test_lens_equals_sum_of_zones_and_oracle(use_graph, kernel):
+def test_lens_equals_sum_of_zones_and_oracle(use_graph, kernel, n_zones):
     from paper_2501_07979_gb300.lens import Lens
-    specs = _lens_specs()
+    specs = _lens_specs(n_zones)
     rhos = [smoothed_rho(s.n_r_design, s.n_phi, 30 + z, mode="minmax") for z, s in enumerate(specs)]
     zones = [_zone(s) for s in specs]
     if kernel == "fused2":
