@@ -39,12 +39,18 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
-    ap.add_argument("--workload", default="zone", choices=["zone", "lwir", "rgb", "poly", "surrogate", "lens"],
+    ap.add_argument("--workload", default="zone",
+                    choices=["zone", "lwir", "rgb", "poly", "surrogate", "lens", "warmstart"],
                     help="zone: forward + adjoint FDTD iteration of the wide zone (headline); "
                          "lwir: the same on zone 16 of the paper's LWIR lens at its lambda/50 grid; "
                          "rgb / poly: zone 16 of the paper's visible lenses at lambda/36; "
                          "surrogate: U-Net inference, 128 x 128 patches, batch 256; "
-                         "lens: forward + adjoint of all 40 zones of a 400-lambda lens, zones sharded over ranks")
+                         "lens: forward + adjoint of all 40 zones of a 400-lambda lens, zones sharded over ranks; "
+                         "warmstart: seconds per zone TopOpt, surrogate warm start vs plain adjoint FDTD")
+    ap.add_argument("--ws-samples", type=int, default=4096, help="warmstart: FDTD training samples")
+    ap.add_argument("--ws-steps", type=int, default=830, help="warmstart: FDTD steps per run (data and TopOpt)")
+    ap.add_argument("--ws-iters", type=int, default=30, help="warmstart: plain FDTD TopOpt iterations")
+    ap.add_argument("--ws-train", type=int, default=3000, help="warmstart: training steps")
     ap.add_argument("--lens-time", type=float, default=20.0,
                     help="lens workload: simulated time per zone run, in lambda0 / c")
     ap.add_argument("--lens-graph", type=int, default=0, choices=[0, 1],
@@ -705,6 +711,105 @@ def run_lens(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ surrogate warm start
+WS_METRIC = "s per zone TopOpt to the plain method's best focal intensity: surrogate warm start vs plain FDTD"
+
+
+def run_warmstart(a):
+    """Surrogate warm start against plain adjoint FDTD on 128 x 128-pixel zones
+    (6.4 x 6.4 lambda, TiO2 on SiO2, 3 wavelengths) at several radii.  The
+    network (4-level U-Net, width 64, bf16 tensor-core kernels) is trained
+    once on FDTD data from zones at radii log-spaced over 50-2000 lambda; for
+    each target zone the plain method runs ws_iters Adam iterations of the
+    adjoint FDTD from rho = 0.5 (its best focal intensity is the target),
+    the warm start runs surrogate ascent and then adjoint-FDTD iterations until
+    it reaches 99 % of that target (at most ws_iters).  value = plain seconds /
+    warm seconds per zone, the one-off data and training time reported
+    beside it (and amortised over a 90-zone lens)."""
+    import numpy as np
+    import torch
+    from paper_2501_07979_gb300.warmstart import WarmStart
+    from zda_inputs import zone_patch, smoothed_rho
+    torch.cuda.set_device(0)
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    T = a.ws_steps
+    train_r = np.geomspace(50.0, 2000.0, 8)
+    targets = (120.0, 450.0, 1500.0)
+    ws = WarmStart(zone_patch(targets[0], T), batch=64, lens_width=16)
+    H, W = ws.H, ws.W
+    n_per = max(16, a.ws_samples // len(train_r) // 16 * 16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xs, Ms = [], []
+    for k, r in enumerate(train_r):
+        rhos = [smoothed_rho(H, W, 1000000 + k * n_per + i, sigma=1.0 + (i % 3), mode="minmax")
+                for i in range(n_per)]
+        X, M = ws.generate(rhos, spec=zone_patch(float(r), T))
+        Xs.append(X)
+        Ms.append(M)
+        ws.release_pools()
+    X = torch.cat(Xs)
+    M = torch.cat(Ms)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    n = X.shape[0]
+    perm = torch.randperm(n, generator=torch.Generator().manual_seed(5)).to(X.device)
+    X, M = X[perm], M[perm]
+    n_hold = max(64, n // 16)
+    ws.init_params(0)
+    t0 = time.perf_counter()
+    hist = ws.fit(X[n_hold:], M[n_hold:], steps=a.ws_train, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    err = ws.field_error(X[:n_hold], M[:n_hold])
+    zones = []
+    rho0 = np.full((H, W), 0.5)
+    for r in targets:
+        ws.set_target(zone_patch(r, T))
+        ws.zone.iteration(torch.tensor(rho0, dtype=torch.float32, device="cuda:0"))   # warm-up
+        torch.cuda.synchronize()
+        _, cold, t_cold = ws.fdtd_topopt(rho0, a.ws_iters)
+        target = max(cold)
+        k_cold = int(np.argmax(np.asarray(cold) >= 0.99 * target))
+        t_cold_to = t_cold * (k_cold + 1) / len(cold)
+        t0 = time.perf_counter()
+        rw, hs = ws.optimize_surrogate(rho0, steps=200, lr=0.02)
+        torch.cuda.synchronize()
+        t_sur = time.perf_counter() - t0
+        rho = rw
+        from paper_2501_07979_gb300.topopt import Adam
+        opt = Adam([rho.shape], lr=0.02)
+        rr = [np.asarray(rho, dtype=np.float64)]
+        warm = []
+        t0 = time.perf_counter()
+        for it in range(a.ws_iters):
+            I, g = ws.zone.iteration(torch.tensor(rr[0], dtype=torch.float32, device="cuda:0"))
+            warm.append(float(I))
+            if I >= 0.99 * target:
+                break
+            rr = opt.step(rr, [g.cpu().numpy()])
+        t_warm = time.perf_counter() - t0
+        zones.append({"r_mid": r, "plain_best_I": target, "plain_iters_to_99pct": k_cold + 1,
+                      "plain_s_to_99pct": t_cold_to, "plain_s_all": t_cold,
+                      "surrogate_ascent_s": t_sur, "surrogate_I_pred": hs[-1], "warm_first_fdtd_I": warm[0],
+                      "warm_fdtd_iters": len(warm), "warm_best_I": max(warm), "warm_s": t_sur + t_warm,
+                      "reached_99pct": max(warm) >= 0.99 * target})
+    sp = [z["plain_s_to_99pct"] / z["warm_s"] for z in zones]
+    line = {"metric": WS_METRIC, "value": float(np.median(sp)), "unit": "x (plain s / warm s per zone)",
+            "n_gpus": 1, "steps": len(targets), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32 FDTD", "data": "synthetic",
+            "config": {"workload": "surrogate warm start on 128x128-pixel zones (6.4 x 6.4 lambda), TiO2 on "
+                                   "SiO2, 3 wavelengths, %d FDTD steps per run" % T,
+                       "train_radii": [float(x) for x in train_r], "samples": n, "held_out": n_hold,
+                       "train_steps": a.ws_train, "plain_iters": a.ws_iters},
+            "data_generation_s": t_data, "training_s": t_train,
+            "one_off_per_zone_of_a_90_zone_lens_s": (t_data + t_train) / 90.0,
+            "held_out_field_error": err, "loss_first_last": [hist[0], hist[-1]],
+            "zones": zones, "speedup_per_zone": sp}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global WORKLOAD
     a = parse()
@@ -714,6 +819,12 @@ def main():
             run_nn_reference(a)
         else:
             run_nn(a)
+    elif a.workload == "warmstart":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "metric": WS_METRIC, "unavailable":
+                              "the comparison runs both arms (surrogate and plain FDTD) on the GPU"}), flush=True)
+        else:
+            run_warmstart(a)
     elif a.workload == "lens":
         if a.impl == "reference":
             print(json.dumps({"impl": "reference", "metric": LENS_METRIC, "unavailable":

@@ -46,15 +46,27 @@ class WarmStart:
         self.net = Surrogate(self.H, self.W, 1, 4 * self.Q, batch, device=device)
         self.lens_width = lens_width
         self.scale = None
-        self._pool = None
+        self._pools = {}
         self.seed = seed
 
+    def set_target(self, spec):
+        """Optimise another zone of the same design grid (the network is shared)."""
+        assert spec.n_r - spec.pml_r_in - spec.pml_r_out == self.H and spec.n_phi == self.W
+        self.spec = spec
+        self.zone = Zone(spec, device=self.device.index)
+
     # ------------------------------------------------------------ data
-    def _lens(self):
-        if self._pool is None:
-            zones = [Zone(self.spec, device=self.device.index) for _ in range(self.lens_width)]
-            self._pool = (zones, Lens(zones, use_graph=True))
-        return self._pool
+    def _lens(self, spec=None):
+        """A lens of lens_width identical zones (one graph launch runs them all)."""
+        spec = spec or self.spec
+        key = spec.to_json()
+        if key not in self._pools:
+            zones = [Zone(spec, device=self.device.index) for _ in range(self.lens_width)]
+            self._pools[key] = (zones, Lens(zones, use_graph=True))
+        return self._pools[key]
+
+    def release_pools(self):
+        self._pools = {}
 
     def _target(self, mon):
         torch = self.torch
@@ -62,11 +74,13 @@ class WarmStart:
         t = torch.stack([m.real, m.imag], dim=2)              # [Q][2][2][H][W]
         return t.reshape(4 * self.Q, self.H, self.W).permute(1, 2, 0)
 
-    def generate(self, rhos):
+    def generate(self, rhos, spec=None):
         """FDTD data for a list of densities: (X [n][H][W][1] = rho~, M [n][H][W][4Q]
-        unscaled monitor DFT channels)."""
+        unscaled monitor DFT channels).  spec: another zone of the same design
+        grid (e.g. at another radius) whose runs give the data; default the
+        target zone."""
         torch = self.torch
-        zones, lens = self._lens()
+        zones, lens = self._lens(spec)
         X, M = [], []
         for k in range(0, len(rhos), len(zones)):
             chunk = list(rhos[k:k + len(zones)])

@@ -59,3 +59,28 @@ def test_high_contrast_gradient_at_decay_against_gpu_central_differences():
         fd = (2 * np.sum(np.abs(z.forward(r + h * d)) ** 2) - 2 * np.sum(np.abs(z.forward(r - h * d)) ** 2)) / (2 * h)
         want = float((g * d).sum().item())
         assert abs(fd / want - 1) < 1e-3, (fd, want)
+
+
+def test_wide_zone_gradient_against_gpu_central_differences():
+    """The full wide zone (300x320x160, n = 4000, TiO2 on SiO2, 3 wavelengths,
+    filter + beta = 8 projection) run for 160000 steps (78.5 lambda0/c), where
+    its one-step-difference energy has fallen to 2.4e-5 of its peak (it rings
+    for long: a circulating guided mode of the high-index layer): the adjoint
+    gradient against central differences of the GPU forward along a seeded
+    random direction (seed 3) of all design pixels.  Measured (GB300): 6.8e-4
+    at 160000 steps, 1.2e-2 at 80000, 4.0e-2 at 20000.  A single pixel's
+    finite difference is below the FP32 forward's rounding at this size (a
+    pixel is 1e-5 of the zone and the conic filter spreads it over ~500
+    pixels), so the check is directional."""
+    from paper_2501_07979_gb300 import Zone
+    from zda_inputs import zone_cfg2, rho_for
+    spec = zone_cfg2(n_steps=160000)
+    z = Zone(spec, device=0)
+    r = torch.tensor(rho_for(spec, 2), dtype=torch.float32, device="cuda:0")
+    _, g = z.iteration(r)
+    u = torch.tensor(np.random.default_rng(3).standard_normal(tuple(r.shape)), dtype=torch.float32, device="cuda:0")
+    u = u / u.norm()
+    h = 0.1
+    fd = (2 * np.sum(np.abs(z.forward(r + h * u)) ** 2) - 2 * np.sum(np.abs(z.forward(r - h * u)) ** 2)) / (2 * h)
+    want = float((g * u).sum().item())
+    assert abs(fd / want - 1) < 1e-3, (fd, want)

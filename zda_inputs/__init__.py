@@ -175,6 +175,29 @@ def zone_visible(ell: int = 16, lens: str = "rgb", n_steps: int = 4000) -> ZoneS
         label="%s zone %d: %g lambda, lambda/36, n = %d" % (lens, ell, width, fold))
 
 
+def zone_patch(r_mid: float = 200.0, n_steps: int = 830, n_design: int = 128, n_phi: int = 128,
+               arc: float = 6.4) -> ZoneSpec:
+    """A surrogate-sized zone: n_design x n_phi design pixels at lambda/20
+    (6.4 x 6.4 lambda for 128 x 128) centred on radius r_mid, fold
+    n = round(2 pi r_mid / arc) so the wedge arc at r_mid is ~arc; the wide
+    zone's z stack (SiO2 substrate, 0.6 lambda TiO2 design layer, air, monitor
+    0.5 lambda above), three wavelengths 0.82 / 1.0 / 1.18, conic filter
+    R = 0.08, tanh projection beta = 8; 8-cell PMLs in r and z."""
+    pml = 8
+    dr = 0.05
+    nf = max(1, int(round(2.0 * math.pi * r_mid / arc)))
+    r_lo = r_mid - 0.5 * n_design * dr - pml * dr
+    return ZoneSpec(
+        r_lo=r_lo, n_r=n_design + 2 * pml, n_phi=n_phi, n_z=160, n_fold=nf, dr=dr, dz=dr,
+        pml_r_in=pml, pml_r_out=pml, pml_z=pml,
+        layer_k0=(0, 40, 52), layer_eps=(2.1, 1.0, 1.0),
+        design_k0=40, design_k1=52, eps_lo=1.0, eps_hi=5.76,
+        source_k=12, monitor_k=62, courant=0.5, n_steps=n_steps,
+        filter_radius=0.08, beta=8.0, eta=0.5,
+        wavelengths=(0.82, 1.0, 1.18), pulse_sigma=0.4, pulse_t0=1.6,
+        focal=300.0, label="surrogate patch zone at r = %g lambda (%dx%d design pixels)" % (r_mid, n_design, n_phi))
+
+
 def zone_tiny(**kw) -> ZoneSpec:
     """A small zone for oracle pins and quick parity cases (defaults: 24 r-cells
     with 4-cell PMLs, 8 phi cells, 40 z-cells, coarse lambda/10 grid)."""
