@@ -29,7 +29,7 @@ def candidates(spec):
     cands = [(2, 2, 0)]
     pair = spec.n_z % 2 == 0 and spec.pml_z % 2 == 0 and spec.n_fold > 0
     if pair:
-        cands += [(0, rows, 0) for rows in (4, 8, 16, 32) if rows <= 2 * max(spec.n_phi, 2)]
+        cands += [(0, rows, eb) for rows in (4, 8, 16, 32) if rows <= 2 * max(spec.n_phi, 2) for eb in (0, 3)]
     else:
         cands.append((0, 16, 0))
     if spec.n_fold > 0 and spec.n_z % 2 == 0 and spec.n_z <= 256:

@@ -594,6 +594,7 @@ static zda::StepParams step_params(zda_zone &z)
     p.des_k0 = d.design_k0;
     p.des_nk = z.nk;
     p.pair_rows = zda::pair_rows_ok(z.tile_phi) ? z.tile_phi : 16;
+    p.e_blocks = (z.variant == 0 && z.i_ranges == 3) ? 3 : 2;
     return p;
 }
 
@@ -1348,7 +1349,7 @@ zda_status zda_zone_get_kernel(const zda_zone *z, int *variant, int *tile_phi, i
     if (!z || !variant || !tile_phi || !i_ranges) return fail(ZDA_ERR_ARG, "null argument");
     *variant = (z->variant == 0 && !z->pair_kernels) ? 2 : z->variant;
     *tile_phi = z->tile_phi;
-    *i_ranges = z->variant == 1 ? auto_i_ranges(*z) : (z->variant == 3 ? tile_rchunks(*z) : 0);
+    *i_ranges = z->variant == 1 ? auto_i_ranges(*z) : (z->variant == 3 ? tile_rchunks(*z) : z->i_ranges);
     return ZDA_OK;
 }
 

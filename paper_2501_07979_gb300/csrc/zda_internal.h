@@ -103,6 +103,7 @@ struct StepParams {
     int rpml_metric;
     Metric rm;
     int pair_rows;                             // two-z-cell split kernels: phi rows per thread block (4, 8, 16, 32)
+    int e_blocks;                              // ... E update's thread blocks per SM (2 or 3)
 };
 
 // kernels (zda_kernels.cu)

@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(256, RM ? 3 : 4) k_update_h_pair(const StepPar
     if (ir >= 0) { st4(p.psi.hp_r + rx, ps_pr); st4(p.psi.hz_r + rx, ps_zr); }
 }
 
-template <bool RM, int PY>
-__global__ void __launch_bounds__(256, 2) k_update_e_pair(const StepParams p, const int n)
+template <bool RM, int PY, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_update_e_pair(const StepParams p, const int n)
 {
     constexpr int PX = 256 / PY;
     const int kp = blockIdx.x * PX + threadIdx.x;
@@ -455,13 +455,20 @@ static void launch_h_py(const StepParams &p, cudaStream_t s)
     else k_update_h_pair<false, PY><<<g, b, 0, s>>>(p);
 }
 
+// E update: 2 blocks per SM (120 registers, no spills) or 3 (80 registers, a
+// few spilled to local memory), chosen by the tuner
 template <int PY>
 static void launch_e_py(const StepParams &p, int n, cudaStream_t s)
 {
     constexpr int PX = 256 / PY;
     dim3 b(PX, PY), g((p.nz / 2 + PX - 1) / PX, (p.nphi + PY - 1) / PY, p.nr);
-    if (p.rpml_metric) k_update_e_pair<true, PY><<<g, b, 0, s>>>(p, n);
-    else k_update_e_pair<false, PY><<<g, b, 0, s>>>(p, n);
+    if (p.e_blocks == 3) {
+        if (p.rpml_metric) k_update_e_pair<true, PY, 3><<<g, b, 0, s>>>(p, n);
+        else k_update_e_pair<false, PY, 3><<<g, b, 0, s>>>(p, n);
+    } else {
+        if (p.rpml_metric) k_update_e_pair<true, PY, 2><<<g, b, 0, s>>>(p, n);
+        else k_update_e_pair<false, PY, 2><<<g, b, 0, s>>>(p, n);
+    }
 }
 
 bool pair_rows_ok(int rows) { return rows == 4 || rows == 8 || rows == 16 || rows == 32; }
