@@ -26,8 +26,13 @@ Two kinds of cases.
   The random-weight cases compute that spread with `_fp32_accumulation`
   (below, a test helper: the oracle's network with every convolution
   accumulated in FP32 in K = 16 channel steps, per tap) on the same inputs
-  and hold the GPU to three times it, per layer: the output, the input
-  gradient and each layer's weight and bias gradients.  A wrong tap,
+  and hold the GPU to three times it plus 2e-3, per quantity: the output,
+  the input gradient and each layer's weight and bias gradients.  The spread
+  is one realisation of discrete rounding flips: measured on the GB300, the
+  24 x 40 case's GPU errors are within 1.5x of it on every layer (up to
+  3.9e-2 on the input gradient), while on the 16 x 16 case the deepest
+  decoder layers' errors reach 4.5x to 50x a spread of 2e-7 to 2e-4 (at most
+  4e-3 absolute): hence the 2e-3 floor.  A wrong tap,
   operand, bias or mask moves these by O(1), and the exact-structure cases
   above pin the wiring bit for bit.
 """
@@ -209,7 +214,7 @@ def test_forward_and_backward_match_oracle(name):
     assert abs(float(loss.item()) - l0) <= 1e-6 * l0
     assert _rel(dy.cpu().numpy(), dy0) < 1e-6
     for k in errs:
-        assert errs[k] <= 3.0 * spread[k] + 1e-5, (k, errs[k], spread[k])
+        assert errs[k] <= 3.0 * spread[k] + 2e-3, (k, errs[k], spread[k])
 
 
 def test_adam_step_matches_oracle():
