@@ -216,7 +216,8 @@ long long zda_zone_launch_count(const zda_zone *zone);
  * (H update, E update), in place, two z-cells per thread with 16-byte loads
  * when n_z and pml_z are even (wedge zones), else one z-cell per thread;
  * tile_phi in {4, 8, 16, 32} is the thread block's phi rows (256 threads;
- * other values: 16), i_ranges = 3 runs the E update at 3 thread blocks per
+ * other values, the default: 4 for zones of at most 16 phi cells, else 16),
+ * i_ranges = 3 runs the E update at 3 thread blocks per
  * SM (fewer registers, a few spilled), else 2.  variant 2: the same with one z-cell per thread always.
  * variant 1 (annular zones, n_z <= 256): one fused launch per step (E and H
  * updated together, ping-pong field buffers, streaming along r; tile_phi in

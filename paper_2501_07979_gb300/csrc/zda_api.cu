@@ -593,7 +593,9 @@ static zda::StepParams step_params(zda_zone &z)
     p.src_scale = (float)(0.5 / d.dz);
     p.des_k0 = d.design_k0;
     p.des_nk = z.nk;
-    p.pair_rows = zda::pair_rows_ok(z.tile_phi) ? z.tile_phi : 16;
+    // default block: 16 phi rows, or 4 for zones of at most 16 phi cells (longer z-runs per block;
+    // measured 5-25 % faster on the 8-16-cell zones of the paper's lenses)
+    p.pair_rows = zda::pair_rows_ok(z.tile_phi) ? z.tile_phi : (d.n_phi <= 16 ? 4 : 16);
     p.e_blocks = (z.variant == 0 && z.i_ranges == 3) ? 3 : 2;
     return p;
 }

@@ -23,7 +23,8 @@ FIELD_TOL = 1e-4
 GRAD_TOL = 1e-3
 
 
-KERNELS = {"split": (0, 2, 0), "split_r4": (0, 4, 0), "split_r32": (0, 32, 0), "split_e3": (0, 8, 3),
+KERNELS = {"split": (0, 2, 0), "split_r4": (0, 4, 0), "split_r16": (0, 16, 0), "split_r32": (0, 32, 0),
+           "split_e3": (0, 8, 3),
            "split1": (2, 2, 0),
            "fused2": (1, 2, 0), "fused4": (1, 4, 0),
            "fused2_ir3": (1, 2, 3), "tile8": (3, 8, 0), "tile4": (3, 4, 0), "tile16": (3, 16, 0),
