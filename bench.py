@@ -33,7 +33,9 @@ UNIT = "Gcell-upd/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 3; surrogate workload: 300 forwards, so that the ~0.8 s timed "
+                         "region holds several 200 ms clock samples)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per run")
@@ -821,6 +823,8 @@ def main():
     global WORKLOAD
     a = parse()
     WORKLOAD = a.workload
+    if a.steps is None:
+        a.steps = 300 if (a.workload == "surrogate" and a.impl == "ours") else 3
     if a.workload == "surrogate":
         if a.impl == "reference":
             run_nn_reference(a)

@@ -37,7 +37,7 @@ def candidates(spec):
     if pair:
         for tj in (4, 8, 16):
             if tj <= 2 * max(spec.n_phi, 2):
-                cands += [(3, tj, 0), (3, tj, 3 * max(1, spec.n_r // 100))]
+                cands += [(3, tj, 0), (3, tj, max(1, spec.n_r // 30))]
     return sorted(set(cands))
 
 

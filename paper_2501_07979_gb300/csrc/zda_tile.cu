@@ -7,31 +7,37 @@
 // the six components (96 B) against 144 B for the split H / E launches,
 // which read the six components twice.
 //
-// Each CTA owns a tile of TI radii x TJ phi rows x 32 z-cells.  Its E update
-// needs H^{n+1/2} on the tile and on its low faces (i0-1, j0-1, k0-1); those
-// are recomputed here instead of being read from the neighbouring tiles
-// (which write them in the same launch).  So one thread issues the TMA
-// tensor copies (cp.async.bulk.tensor, one box per component) of
-//   E^n       radii i0-1 .. i0+TI, rows j0-1 .. j0+TJ, z k0-2 .. k0+33
-//   H^{n-1/2} radii i0-1 .. i0+TI-1, rows j0-1 .. j0+TJ-1, z k0-2 .. k0+31
-// into shared memory ([radius][row][z], z fastest; outside the grid the
-// copy fills zeros, which are the PEC values there), completing on one
-// mbarrier.  Tiles at the wedge's phi edges also fetch the wrapped row
-// (phi row n_phi-1 for j0-1, row 0 for n_phi) into a staging slab and copy
-// it, times the Bloch phase e^{-+i m tau}, into place.  Then
-//   phase H: every (radius, row, z-pair) of the H box: H^{n+1/2} in place
-//            in shared memory; tile sites also stored to the output buffer
-//            with their H-side CPML auxiliaries (which are ping-ponged too:
-//            halo sites read the old set, which their owner does not write);
-//   phase E: every tile site: E^{n+1} from the shared H and E boxes, E-side
-//            CPML in place (each site only by its owner), source, DFT
-//            history, stored to the output buffer.
-// Threads walk the sites of a phase with consecutive z-pairs on consecutive
-// lanes (16-byte shared loads, coalesced 16-byte global stores).  The wait
-// for the copies is bounded: on expiry the error word is set, the kernel
-// finishes without the data and waits (bounded) for its copies before
-// exiting.  Same scheme and arithmetic as the split step (zda_pair.cu);
-// results agree to FP32 rounding.
+// Each CTA owns a column of TJ phi rows x 32 z-cells and streams along r
+// over a range of radii [ib, ie).  Load group g(r) = {E^n at radius r+1,
+// H^{n-1/2} at radius r} is one set of TMA tensor copies
+// (cp.async.bulk.tensor, one box per component) of
+//   E^n       rows j0-1 .. j0+TJ,   z k0-2 .. k0+33
+//   H^{n-1/2} rows j0-1 .. j0+TJ-1, z k0-2 .. k0+31
+// into a ring of NSLOT slots in shared memory ([row][z], z fastest; outside
+// the grid the copy fills zeros, the PEC values there), completing on the
+// slot's mbarrier.  Tiles at the wedge's phi edges also fetch the wrapped
+// rows (phi row n_phi-1 below j0, row 0 above n_phi-1) into staging rows
+// and apply the Bloch phase e^{-+i m tau} when they read them.  Iteration r
+// runs two groups of warps side by side:
+//   H items: H^{n+1/2}(r) on the H box (the tile plus the row j0-1 and the
+//            z-cells k0-2, k0-1 below it, which the E update needs and the
+//            neighbouring tiles own), in place in shared memory; tile sites
+//            are also stored to the output buffer with their H-side CPML
+//            auxiliaries (ping-ponged too: halo sites read the old set,
+//            which their owner does not write);
+//   E items: E^{n+1}(r-1) from H^{n+1/2}(r-1), H^{n+1/2}(r-2) and E^n(r-1),
+//            E-side CPML in place (each site only by its owner), source,
+//            DFT history, stored to the output buffer.
+// Every cell takes the interior coefficient form; the CPML recursions and
+// the source add their terms where they apply, so warps that straddle a
+// CPML slab edge or the source plane do not run two versions of the update.
+// After iteration r thread 0 waits for g(r+1) and the block barrier
+// publishes it (and H(r)) to every thread; then g(r+NSLOT-2) is issued into
+// the slot of g(r-2), whose last reader was E(r-1).  Each wait is bounded
+// (polls and a 1 s deadline): on expiry the error word is set, every
+// thread leaves the loop at the barrier, and thread 0 waits (bounded) for
+// the copies still in flight before the CTA exits.  Same scheme as the
+// split step (zda_pair.cu); results agree to FP32 rounding.
 #include <cudaTypedefs.h>
 #include <algorithm>
 #include "zda_tile.h"
@@ -123,7 +129,7 @@ __device__ __forceinline__ float t_rcp(float x)          // hardware reciprocal,
     return y;
 }
 
-template <int TJ>
+template <int TJ, int NS>
 struct SG {                                                   // geometry of the radius-streamed tile step
     static constexpr int KP = TILE_KZ / 2;                    // z-pairs of a tile
     static constexpr int EZ = TILE_KZ + 4, HZ = TILE_KZ + 2;  // z extents of the slabs (from k0-2)
@@ -134,17 +140,17 @@ struct SG {                                                   // geometry of the
     // wrapped rows of edge tiles: E low, E high, H low (3 components each)
     static constexpr int E_OFF = 0, H_OFF = 3 * ES, WEL = H_OFF + 3 * HS, WEH = WEL + 3 * RW, WHL = WEH + 3 * RW;
     static constexpr int GROUP = WHL + 3 * RW;
-    static constexpr int NSLOT = 4;
+    static constexpr int NSLOT = NS;                       // ring of load groups (NS - 2 issued ahead)
     // threads: E items (row, pair 1..KP) | H items (row, pair 1..KP) | H z-halo items (row, pair 0)
     static constexpr int NE = TJ * KP, NH = HJ * KP, NHALO = HJ;
     static constexpr int NT = (NE + NH + NHALO + 31) / 32 * 32;
 };
 
-template <int TJ, int MINB>
-__global__ void __launch_bounds__(SG<TJ>::NT, MINB)
+template <int TJ, int NS, int MINB>
+__global__ void __launch_bounds__(SG<TJ, NS>::NT, MINB)
     k_tile_step(const __grid_constant__ TileMaps m, const TileParams tp, const int n, const int i_range)
 {
-    using G = SG<TJ>;
+    using G = SG<TJ, NS>;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_mem[G::NSLOT];
     __shared__ int abort_s;                                   // the error word was already set at entry
@@ -165,11 +171,12 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
     const bool whi = s_hi <= TJ + 1;
     const int x = 2 * (k0 - 2);
 
-    // load group g(r) = {E^n(r+1), H^{n-1/2}(r)}, r = r0-1 .. ie-1, in slot (r - r0 + 1) % NSLOT
-    auto slot_of = [&](int r) { return (r - r0 + 1) % G::NSLOT; };
-    auto parity_of = [&](int r) { return (uint32_t)(((r - r0 + 1) / G::NSLOT) & 1); };
+    // load group g(r) = {E^n(r+1), H^{n-1/2}(r)}, r = r0-1 .. ie-1, in slot (r - r0 + 1) mod NSLOT
+    auto slot_of = [&](int r) { return (unsigned)(r - r0 + 1) % (unsigned)G::NSLOT; };
+    auto parity_of = [&](int r) { return ((unsigned)(r - r0 + 1) / (unsigned)G::NSLOT) & 1u; };
+    auto group = [&](int r) { return sm + slot_of(r) * G::GROUP; };
     auto issue = [&](int r) {
-        const int sl = slot_of(r);
+        const unsigned sl = slot_of(r);
         const uint32_t g = base_s + (uint32_t)(sl * G::GROUP) * 8u;
         const uint32_t bar = s_addr(&bar_mem[sl]);
         uint32_t bytes = 3u * (G::EZ * G::EJ + G::HZ * G::HJ) * 8u;
@@ -187,6 +194,8 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
             if (whi) tma3(g + (G::WEH + c * G::RW) * 8u, &m.ew[c], x, 0, r + 1, bar);
         }
     };
+    // thread 0 alone waits for a group; the block barrier that follows publishes it to the others
+    auto wait_group = [&](int r) { return t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err); };
 
     if (tid == 0) {
         for (int s = 0; s < G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
@@ -197,12 +206,16 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
     }
     __syncthreads();
     if (abort_s) return;
-    // groups g(r0-1), g(r0), g(r0+1) now; g(r+2) after iteration r, into the slot of g(r-2)
-    if (tid == 0)
-        for (int r = r0 - 1; r < ie && r <= r0 + 1; ++r) issue(r);
-    int last_issued = min(ie - 1, r0 + 1);
-    // every thread observes the first group's completion (its E slab is read at iteration r0)
-    bool failed = !t_mbar_wait(s_addr(&bar_mem[slot_of(r0 - 1)]), parity_of(r0 - 1), tp.wait_limit, tp.err);
+    // groups g(r0-1) .. g(r0+NSLOT-3) now; g(r+NSLOT-2) after iteration r, into the slot of g(r-2)
+    constexpr int AHEAD = G::NSLOT - 2;
+    int last_issued = min(ie - 1, r0 + AHEAD - 1);
+    bool failed = false;
+    if (tid == 0) {
+        for (int r = r0 - 1; r <= last_issued; ++r) issue(r);
+        failed = !wait_group(r0 - 1);                         // E^n(r0): read by H(r0)
+        if (!failed && r0 < ie) failed = !wait_group(r0);     // E^n(r0+1), H(r0)
+    }
+    failed = __syncthreads_or(failed);
 
     const float2 zero = make_float2(0.f, 0.f);
     const float dt = p.dt;
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
         if (e_valid) {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (kze >= 0) { bzn[u] = __ldg(p.t.bz_n + ke + u); czn[u] = __ldg(p.t.cz_n + ke + u); }
+                if (kze >= 0) { bzn[u] = __ldg(p.t.bz_n + ke + u); czn[u] = __ldg(p.t.cz_n + ke + u) * p.inv_dz; }
                 an[u] = __ldg(p.t.a_n + ke + u); dn[u] = __ldg(p.t.d_n + ke + u);
                 ac[u] = __ldg(p.t.a_c + ke + u); dc[u] = __ldg(p.t.d_c + ke + u);
             }
@@ -239,6 +252,7 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
         const int dk0 = ke - p.des_k0;
         const bool e_hist = hs && e_valid &&
                             ((p.des && dk0 + 1 >= 0 && dk0 < p.des_nk) || (p.mon && (ke == p.mon_k || ke + 1 == p.mon_k)));
+        const float cdz = p.inv_dz, cdr = p.inv_dr;
         // per-radius values of the next E radius, loaded one iteration ahead
         auto rb_load = [&](int i, float &a, float &b, float &c) {
             if (e_valid && i >= 0 && i < nr) {
@@ -254,16 +268,15 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
         };
         rb_load(ib, nrbr, nrbp, nrbz);
         tab_load(ib, ntab);
-        for (int r = r0; r <= ie; ++r) {
+        for (int r = r0; r <= ie && !failed; ++r) {
             const int i = r - 1;                              // radius of this iteration's E update
             rbr = nrbr; rbp = nrbp; rbz = nrbz;
             tab = ntab;
             rb_load(i + 1, nrbr, nrbp, nrbz);
             tab_load(i + 1, ntab);
-            if (r < ie && !failed) failed = !t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err);
-            if (i >= ib && e_valid && !failed) {
-                const float2 *gq = sm + slot_of(i) * G::GROUP;     // H^{n+1/2}(i)
-                const float2 *gp = sm + slot_of(i - 1) * G::GROUP; // E^n(i), H^{n+1/2}(i-1)
+            if (i >= ib && e_valid) {
+                const float2 *gq = group(i);                  // H^{n+1/2}(i)
+                const float2 *gp = group(i - 1);              // E^n(i), H^{n+1/2}(i-1)
                 const C2 hr = lds4(gq + he_own), hp = lds4(gq + he_own + G::HS), hz = lds4(gq + he_own + 2 * G::HS);
                 const C2 hz_jm = lds4(gq + he_jm + 2 * G::HS), hr_jm = lds4(gq + he_jm);
                 const float2 hp_km = gq[he_own + G::HS - 1], hr_km = gq[he_own - 1];
@@ -280,91 +293,68 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
                 float2 *ER[2] = {&er.a, &er.b}, *EP[2] = {&ep.a, &ep.b}, *EZ[2] = {&ez.a, &ez.b};
                 C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
                 if (kze >= 0) { ps_r = ldg4(p.psi.er_z + zx); ps_p = ldg4(p.psi.ep_z + zx); }
-                float brn = 0.f, crn = 0.f;
-                if (ir >= 0) {
-                    ps_pr = ldg4(p.psi.ep_r + rx); ps_zr = ldg4(p.psi.ez_r + rx);
-                    brn = tab.z; crn = tab.w;
-                }
+                const float brn = tab.z, crn = tab.w, crn_dr = tab.w * cdr;
+                if (ir >= 0) { ps_pr = ldg4(p.psi.ep_r + rx); ps_zr = ldg4(p.psi.ez_r + rx); }
                 float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
                 float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
-                const bool fast = kze < 0 && ir < 0 && src_u < 0 && ke > 0 && i > 0;
-                if (fast) {
-                    // interior: coefficient form (no CPML, no source, not on a PEC face)
-                    const float cph_h = irh * p.inv_dphi, cph_n = irn * p.inv_dphi, cm = 0.5f * irn;
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const float cr = dt * t_rcp(an[u] + dn[u] * rbr), cp = dt * t_rcp(an[u] + dn[u] * rbp);
-                        const float cz = dt * t_rcp(ac[u] + dc[u] * rbz);
-                        float2 t = f_sub(HZk[u], HZJ[u]);     // E_r: (1/r) dH_z/dphi - dH_phi/dz
-                        float2 a = make_float2(cph_h * t.x, cph_h * t.y);
-                        a = f_axpy(-p.inv_dz, f_sub(HPk[u + 1], HPk[u]), a);
-                        *ER[u] = f_axpy(cr, a, *ER[u]);
-                        t = f_sub(HRk[u + 1], HRk[u]);        // E_phi: dH_r/dz - dH_z/dr
-                        a = make_float2(p.inv_dz * t.x, p.inv_dz * t.y);
-                        a = f_axpy(-p.inv_dr, f_sub(HZk[u], HZI[u]), a);
-                        *EP[u] = f_axpy(cp, a, *EP[u]);
-                        t = f_sub(HPk[u + 1], HPI[u]);        // E_z: (1/r) d(r H_phi)/dr - (1/r) dH_r/dphi
-                        a = make_float2(p.inv_dr * t.x, p.inv_dr * t.y);
-                        a = f_axpy(cm, f_add(HPk[u + 1], HPI[u]), a);
-                        a = f_axpy(-cph_n, f_sub(HRk[u + 1], HRJ[u]), a);
-                        *EZ[u] = f_axpy(cz, a, *EZ[u]);
-                    }
-                } else {
-                float2 sr = zero, sp = zero;                  // source of this radius
+                float2 jr = zero, jp = zero;                  // source current of this radius (cell src_u)
                 if (src_u >= 0) {
                     if (p.src_mode == SRC_PLANE_WAVE) {
-                        sr = c_scale(src_pn, src_amp);
-                        sp = make_float2(-src_ph.y * src_amp, src_ph.x * src_amp);
+                        jr = c_scale(src_pn, src_amp);
+                        jp = make_float2(-src_ph.y * src_amp, src_ph.x * src_amp);
                     } else {
-                        sr = c_mul(src_pn, p.src_rad[i]);
-                        sp = c_mul(src_ph, p.src_rad[nr + i]);
+                        jr = c_mul(src_pn, p.src_rad[i]);
+                        jp = c_mul(src_ph, p.src_rad[nr + i]);
                     }
                 }
+                // one coefficient form for every cell; the CPML recursions and the source
+                // add their terms where they apply (uniform across most warps)
+                const float cph_h = irh * p.inv_dphi, cph_n = irn * p.inv_dphi, cm = 0.5f * irn;
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
+                    const float cr = dt * t_rcp(an[u] + dn[u] * rbr), cp = dt * t_rcp(an[u] + dn[u] * rbp);
+                    const float cz = dt * t_rcp(ac[u] + dc[u] * rbz);
+                    // E_r: (1/r) dH_z/dphi - dH_phi/dz
+                    const float2 d_hp = f_sub(HPk[u + 1], HPk[u]);
+                    float2 t = f_sub(HZk[u], HZJ[u]);
+                    float2 a = make_float2(cph_h * t.x, cph_h * t.y);
+                    a = f_axpy(-cdz, d_hp, a);
                     const int kk = ke + u;
-                    const float2 jr = (u == src_u) ? sr : zero, jp = (u == src_u) ? sp : zero;
-                    if (kk > 0) {                             // E_r
-                        const float2 dph = c_scale(c_sub(HZk[u], HZJ[u]), irh * p.inv_dphi);
-                        float2 dz = c_scale(c_sub(HPk[u + 1], HPk[u]), p.inv_dz);
-                        if (kze >= 0) {
-                            *PR[u] = c_add(c_scale(*PR[u], bzn[u]), c_scale(dz, czn[u]));
-                            dz = c_add(dz, *PR[u]);
-                        }
-                        const float iee = t_rcp(an[u] + dn[u] * rbr);
-                        *ER[u] = c_add(*ER[u], c_scale(c_sub(c_sub(dph, dz), jr), dt * iee));
+                    if (kze >= 0 && kk > 0) {
+                        *PR[u] = f_axpy(czn[u], d_hp, c_scale(*PR[u], bzn[u]));
+                        a = f_sub(a, *PR[u]);
                     }
-                    if (i > 0 && kk > 0) {                    // E_phi
-                        float2 dz = c_scale(c_sub(HRk[u + 1], HRk[u]), p.inv_dz);
-                        float2 drr = c_scale(c_sub(HZk[u], HZI[u]), p.inv_dr);
-                        if (kze >= 0) {
-                            *PP[u] = c_add(c_scale(*PP[u], bzn[u]), c_scale(dz, czn[u]));
-                            dz = c_add(dz, *PP[u]);
-                        }
-                        if (ir >= 0) {
-                            *PPR[u] = c_add(c_scale(*PPR[u], brn), c_scale(drr, crn));
-                            drr = c_add(drr, *PPR[u]);
-                        }
-                        const float iee = t_rcp(an[u] + dn[u] * rbp);
-                        *EP[u] = c_add(*EP[u], c_scale(c_sub(c_sub(dz, drr), jp), dt * iee));
+                    // E_phi: dH_r/dz - dH_z/dr
+                    const float2 d_hr = f_sub(HRk[u + 1], HRk[u]), d_hzi = f_sub(HZk[u], HZI[u]);
+                    float2 b = make_float2(cdz * d_hr.x, cdz * d_hr.y);
+                    b = f_axpy(-cdr, d_hzi, b);
+                    const bool upd_p = kk > 0 && i > 0;
+                    if (kze >= 0 && upd_p) {
+                        *PP[u] = f_axpy(czn[u], d_hr, c_scale(*PP[u], bzn[u]));
+                        b = f_add(b, *PP[u]);
                     }
-                    if (i > 0) {                              // E_z
-                        float2 drr = c_add(c_scale(c_sub(HPk[u + 1], HPI[u]), p.inv_dr),
-                                           c_scale(c_add(HPk[u + 1], HPI[u]), 0.5f * irn));
-                        const float2 dph = c_scale(c_sub(HRk[u + 1], HRJ[u]), irn * p.inv_dphi);
-                        if (ir >= 0) {
-                            *PZR[u] = c_add(c_scale(*PZR[u], brn), c_scale(drr, crn));
-                            drr = c_add(drr, *PZR[u]);
-                        }
-                        const float iee = t_rcp(ac[u] + dc[u] * rbz);
-                        *EZ[u] = c_add(*EZ[u], c_scale(c_sub(drr, dph), dt * iee));
+                    if (ir >= 0 && upd_p) {
+                        *PPR[u] = f_axpy(crn_dr, d_hzi, c_scale(*PPR[u], brn));
+                        b = f_sub(b, *PPR[u]);
                     }
+                    if (u == src_u) { a = f_sub(a, jr); b = f_sub(b, jp); }
+                    if (kk > 0) *ER[u] = f_axpy(cr, a, *ER[u]);
+                    if (upd_p) *EP[u] = f_axpy(cp, b, *EP[u]);
+                    // E_z: (1/r) d(r H_phi)/dr - (1/r) dH_r/dphi
+                    t = f_sub(HPk[u + 1], HPI[u]);
+                    float2 c = make_float2(cdr * t.x, cdr * t.y);
+                    c = f_axpy(cm, f_add(HPk[u + 1], HPI[u]), c);
+                    if (ir >= 0 && i > 0) {
+                        *PZR[u] = f_axpy(crn, c, c_scale(*PZR[u], brn));
+                        c = f_add(c, *PZR[u]);
+                    }
+                    c = f_axpy(-cph_n, f_sub(HRk[u + 1], HRJ[u]), c);
+                    if (i > 0) *EZ[u] = f_axpy(cz, c, *EZ[u]);
                 }
-                }
-                const int c = i * si + je * sj + ke;
-                st4(tp.oE[0] + c, er);
-                st4(tp.oE[1] + c, ep);
-                st4(tp.oE[2] + c, ez);
+                const int o = i * si + je * sj + ke;
+                st4(tp.oE[0] + o, er);
+                st4(tp.oE[1] + o, ep);
+                st4(tp.oE[2] + o, ez);
                 if (kze >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
                 if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
                 if (e_hist) {                                 // history slot of the time-blocked DFT
@@ -384,12 +374,14 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
                     }
                 }
             }
-            // H(r) published; group g(r-2) free; a wait that gave up anywhere ends the loop for all
+            // g(r+1) landed (thread 0 waits); H(r) published; g(r-2) free.  A wait that
+            // gave up ends the loop for every thread.
+            if (tid == 0 && r + 1 < ie) failed = !wait_group(r + 1);
             if (__syncthreads_or(failed)) { failed = true; break; }
-            if (tid == 0 && r + 2 < ie) {
+            if (tid == 0 && r + AHEAD < ie) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(r + 2);
-                last_issued = r + 2;
+                issue(r + AHEAD);
+                last_issued = r + AHEAD;
             }
         }
     } else {
@@ -407,7 +399,7 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
         float bzh[2] = {0.f, 0.f}, czh[2] = {0.f, 0.f};
         if (h_valid && kzh >= 0) {
             bzh[0] = __ldg(p.t.bz_h + kh); bzh[1] = __ldg(p.t.bz_h + kh + 1);
-            czh[0] = __ldg(p.t.cz_h + kh); czh[1] = __ldg(p.t.cz_h + kh + 1);
+            czh[0] = __ldg(p.t.cz_h + kh) * p.inv_dz; czh[1] = __ldg(p.t.cz_h + kh + 1) * p.inv_dz;
         }
         // shared offsets within a group: own row (slab or wrapped-row staging), row + 1
         const int e_own = h_wlo ? G::WEL + 2 * ph : G::E_OFF + sh * G::EZ + 2 * ph;
@@ -417,19 +409,19 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
         const int h_rd = h_wlo ? G::WHL + 2 * ph : G::H_OFF + sh * G::HZ + 2 * ph;
         const int h_rcs = h_wlo ? G::RW : G::HS;
         const int h_wr = G::H_OFF + sh * G::HZ + 2 * ph;      // H^{n+1/2} always into the slab
+        const float k_z = dt * p.inv_dz, k_r = dt * p.inv_dr;
         float4 tab = make_float4(0.f, 0.f, 0.f, 0.f), ntab = tab;   // 1/r_r, 1/r_{r+1/2}, CPML b, c at r_{r+1/2}
         auto tab_load = [&](int r, float4 &t) {
             if (r >= 0 && r < nr)
                 t = make_float4(__ldg(p.t.inv_r_n + r), __ldg(p.t.inv_r_h + r), __ldg(p.t.br_h + r), __ldg(p.t.cr_h + r));
         };
         tab_load(r0, ntab);
-        for (int r = r0; r <= ie; ++r) {
+        for (int r = r0; r <= ie && !failed; ++r) {
             tab = ntab;
             tab_load(r + 1, ntab);
-            if (r < ie && !failed) failed = !t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err);
-            if (r < ie && h_valid && !failed) {
-                const float2 *gp = sm + slot_of(r - 1) * G::GROUP;  // E^n(r)
-                float2 *gc = sm + slot_of(r) * G::GROUP;            // E^n(r+1), H(r)
+            if (r < ie && h_valid) {
+                const float2 *gp = group(r - 1);              // E^n(r)
+                float2 *gc = group(r);                        // E^n(r+1), H(r)
                 const float irn = tab.x, irh = tab.y;
                 const int ir = (r < p.pr_in) ? r : ((r >= nr - p.pr_out) ? r - (nr - p.pr_in - p.pr_out) : -1);
                 const C2 er = lds4(gp + e_own), ep = lds4(gp + e_own + e_cs), ez = lds4(gp + e_own + 2 * e_cs);
@@ -462,9 +454,8 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
                     ps_p = ldg4(tp.psH_in[1] + zx);
                     if (h_wlo) { ps_r = cmul2(p.bloch_inv, ps_r); ps_p = cmul2(p.bloch_inv, ps_p); }
                 }
-                float brh = 0.f, crh = 0.f;
+                const float brh = tab.z, crh = tab.w * p.inv_dr;
                 if (ir >= 0) {
-                    brh = tab.z; crh = tab.w;
                     ps_pr = ldg4(tp.psH_in[2] + rx);
                     ps_zr = ldg4(tp.psH_in[3] + rx);
                     if (h_wlo) { ps_pr = cmul2(p.bloch_inv, ps_pr); ps_zr = cmul2(p.bloch_inv, ps_zr); }
@@ -472,65 +463,45 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
                 float2 *HR[2] = {&hr.a, &hr.b}, *HP[2] = {&hp.a, &hp.b}, *HZ[2] = {&hz.a, &hz.b};
                 float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
                 float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
-                if (kzh < 0 && ir < 0) {
-                    // interior: coefficient form (no CPML)
-                    const float k_phn = dt * irn * p.inv_dphi, k_z = dt * p.inv_dz, k_r = dt * p.inv_dr;
-                    const float k_m = 0.5f * dt * irh, k_phh = dt * irh * p.inv_dphi;
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        *HR[u] = f_axpy(-k_phn, f_sub(EZJ[u], EZ[u]), *HR[u]);
-                        *HR[u] = f_axpy(k_z, f_sub(EP[u + 1], EP[u]), *HR[u]);
-                        *HP[u] = f_axpy(-k_z, f_sub(ER[u + 1], ER[u]), *HP[u]);
-                        *HP[u] = f_axpy(k_r, f_sub(EZI[u], EZ[u]), *HP[u]);
-                        *HZ[u] = f_axpy(-k_r, f_sub(EPI[u], EP[u]), *HZ[u]);
-                        *HZ[u] = f_axpy(-k_m, f_add(EPI[u], EP[u]), *HZ[u]);
-                        *HZ[u] = f_axpy(k_phh, f_sub(ERJ[u], ER[u]), *HZ[u]);
-                    }
-                } else {
+                // one coefficient form for every cell; the CPML recursions add their terms where they apply
+                const float k_phn = dt * irn * p.inv_dphi, k_m = 0.5f * dt * irh, k_phh = dt * irh * p.inv_dphi;
+                const float c_m = 0.5f * irh * tab.w;
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    {                                         // H_r
-                        const float2 dph = c_scale(c_sub(EZJ[u], EZ[u]), irn * p.inv_dphi);
-                        float2 dz = c_scale(c_sub(EP[u + 1], EP[u]), p.inv_dz);
-                        if (kzh >= 0) {
-                            *PR[u] = c_add(c_scale(*PR[u], bzh[u]), c_scale(dz, czh[u]));
-                            dz = c_add(dz, *PR[u]);
-                        }
-                        *HR[u] = c_sub(*HR[u], c_scale(c_sub(dph, dz), dt));
+                    const float2 d_ep = f_sub(EP[u + 1], EP[u]), d_er = f_sub(ER[u + 1], ER[u]);
+                    const float2 d_ezi = f_sub(EZI[u], EZ[u]), d_epi = f_sub(EPI[u], EP[u]);
+                    const float2 s_epi = f_add(EPI[u], EP[u]);
+                    // H_r
+                    *HR[u] = f_axpy(-k_phn, f_sub(EZJ[u], EZ[u]), *HR[u]);
+                    *HR[u] = f_axpy(k_z, d_ep, *HR[u]);
+                    // H_phi
+                    *HP[u] = f_axpy(-k_z, d_er, *HP[u]);
+                    *HP[u] = f_axpy(k_r, d_ezi, *HP[u]);
+                    if (kzh >= 0) {
+                        *PR[u] = f_axpy(czh[u], d_ep, c_scale(*PR[u], bzh[u]));
+                        *PP[u] = f_axpy(czh[u], d_er, c_scale(*PP[u], bzh[u]));
+                        *HR[u] = f_axpy(dt, *PR[u], *HR[u]);
+                        *HP[u] = f_axpy(-dt, *PP[u], *HP[u]);
                     }
-                    {                                         // H_phi
-                        float2 dz = c_scale(c_sub(ER[u + 1], ER[u]), p.inv_dz);
-                        float2 drr = c_scale(c_sub(EZI[u], EZ[u]), p.inv_dr);
-                        if (kzh >= 0) {
-                            *PP[u] = c_add(c_scale(*PP[u], bzh[u]), c_scale(dz, czh[u]));
-                            dz = c_add(dz, *PP[u]);
-                        }
-                        if (ir >= 0) {
-                            *PPR[u] = c_add(c_scale(*PPR[u], brh), c_scale(drr, crh));
-                            drr = c_add(drr, *PPR[u]);
-                        }
-                        *HP[u] = c_sub(*HP[u], c_scale(c_sub(dz, drr), dt));
+                    // H_z
+                    *HZ[u] = f_axpy(-k_r, d_epi, *HZ[u]);
+                    *HZ[u] = f_axpy(-k_m, s_epi, *HZ[u]);
+                    *HZ[u] = f_axpy(k_phh, f_sub(ERJ[u], ER[u]), *HZ[u]);
+                    if (ir >= 0) {
+                        *PPR[u] = f_axpy(crh, d_ezi, c_scale(*PPR[u], brh));
+                        *PZR[u] = f_axpy(c_m, s_epi, f_axpy(crh, d_epi, c_scale(*PZR[u], brh)));
+                        *HP[u] = f_axpy(dt, *PPR[u], *HP[u]);
+                        *HZ[u] = f_axpy(-dt, *PZR[u], *HZ[u]);
                     }
-                    {                                         // H_z
-                        float2 drr = c_add(c_scale(c_sub(EPI[u], EP[u]), p.inv_dr),
-                                           c_scale(c_add(EPI[u], EP[u]), 0.5f * irh));
-                        const float2 dph = c_scale(c_sub(ERJ[u], ER[u]), irh * p.inv_dphi);
-                        if (ir >= 0) {
-                            *PZR[u] = c_add(c_scale(*PZR[u], brh), c_scale(drr, crh));
-                            drr = c_add(drr, *PZR[u]);
-                        }
-                        *HZ[u] = c_sub(*HZ[u], c_scale(c_sub(drr, dph), dt));
-                    }
-                }
                 }
                 st4(gc + h_wr, hr);
                 st4(gc + h_wr + G::HS, hp);
                 st4(gc + h_wr + 2 * G::HS, hz);
                 if (h_own && r >= ib) {
-                    const int c = r * si + jh * sj + kh;
-                    st4(tp.oH[0] + c, hr);
-                    st4(tp.oH[1] + c, hp);
-                    st4(tp.oH[2] + c, hz);
+                    const int o = r * si + jh * sj + kh;
+                    st4(tp.oH[0] + o, hr);
+                    st4(tp.oH[1] + o, hp);
+                    st4(tp.oH[2] + o, hz);
                     if (kzh >= 0) { st4(tp.psH_out[0] + zx, ps_r); st4(tp.psH_out[1] + zx, ps_p); }
                     if (ir >= 0) { st4(tp.psH_out[2] + rx, ps_pr); st4(tp.psH_out[3] + rx, ps_zr); }
                 }
@@ -539,8 +510,7 @@ __global__ void __launch_bounds__(SG<TJ>::NT, MINB)
         }
     }
     if (failed && tid == 0)                                   // copies still in flight
-        for (int r = max(r0 - 1, last_issued - 3); r <= last_issued; ++r)
-            t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err);
+        for (int r = max(r0 - 1, last_issued - G::NSLOT + 1); r <= last_issued; ++r) wait_group(r);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -559,16 +529,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-template <int TJ, int MINB>
+template <int TJ, int NS, int MINB>
 cudaError_t launch_shape(const TileMaps &m, const TileParams &tp, int n, int n_rchunks, cudaStream_t s)
 {
-    using G = SG<TJ>;
+    using G = SG<TJ, NS>;
     const size_t bytes = (size_t)G::NSLOT * G::GROUP * sizeof(float2) + 128;
     int dev = 0;
     cudaGetDevice(&dev);
     static unsigned attr_done = 0;                            // per device (bit), set once
     if (dev < 32 && !(attr_done & (1u << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_step<TJ, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tile_step<TJ, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
         if (e != cudaSuccess) return e;
         attr_done |= 1u << dev;
@@ -577,22 +547,33 @@ cudaError_t launch_shape(const TileMaps &m, const TileParams &tp, int n, int n_r
     const int nrc = std::max(1, std::min(n_rchunks, tp.p.nr));
     const int i_range = (tp.p.nr + nrc - 1) / nrc;
     dim3 g((unsigned)(nzc * njt), (unsigned)((tp.p.nr + i_range - 1) / i_range));
-    k_tile_step<TJ, MINB><<<g, G::NT, bytes, s>>>(m, tp, n, i_range);
+    k_tile_step<TJ, NS, MINB><<<g, G::NT, bytes, s>>>(m, tp, n, i_range);
     return cudaGetLastError();
 }
 
-template <int TJ>
-size_t shape_bytes() { return (size_t)SG<TJ>::NSLOT * SG<TJ>::GROUP * sizeof(float2) + 128; }
+// compiled shapes: phi rows, ring slots, thread blocks per SM the registers are sized for
+struct TileShape { int tj, ns, minb; };
+constexpr TileShape kShapes[] = {{4, 5, 3}, {8, 4, 2}, {16, 4, 1}};
+
+const TileShape *shape_of(int tj)
+{
+    for (const TileShape &t : kShapes)
+        if (t.tj == tj) return &t;
+    return nullptr;
+}
+
+template <int TJ, int NS>
+size_t shape_bytes() { return (size_t)SG<TJ, NS>::NSLOT * SG<TJ, NS>::GROUP * sizeof(float2) + 128; }
 
 }  // namespace
 
-bool tile_shape_ok(int tj) { return tj == 4 || tj == 8 || tj == 16; }
+bool tile_shape_ok(int tj) { return shape_of(tj) != nullptr; }
 
 size_t tile_smem_bytes(int tj)
 {
-    if (tj == 4) return shape_bytes<4>();
-    if (tj == 8) return shape_bytes<8>();
-    if (tj == 16) return shape_bytes<16>();
+    if (tj == 4) return shape_bytes<4, 5>();
+    if (tj == 8) return shape_bytes<8, 4>();
+    if (tj == 16) return shape_bytes<16, 4>();
     return 0;
 }
 
@@ -606,8 +587,11 @@ int tile_auto_rchunks(int tj, int nr, int nphi, int nz, int sms)
 {
     const int per_wave = sms * std::max(1, tile_blocks_per_sm(tj));
     const int tiles = ((nz + TILE_KZ - 1) / TILE_KZ) * ((nphi + tj - 1) / tj);
-    // about four waves of thread blocks (radius chunks streamed in parallel), at least 8 radii per chunk
-    int c = std::max(1, (4 * per_wave + tiles - 1) / std::max(tiles, 1));
+    // radius chunks of about 21 radii (the measured optimum on a 300-radius zone: shorter chunks
+    // recompute more halo radii, longer ones leave too few blocks to balance the SMs), at least four
+    // waves of thread blocks and at least 8 radii per chunk
+    const int waves4 = (4 * per_wave + tiles - 1) / std::max(tiles, 1);
+    const int c = std::max(waves4, (nr + 10) / 21);
     return std::max(1, std::min(c, nr / 8));
 }
 
@@ -644,9 +628,9 @@ bool encode_tile_maps(TileMaps *m, float2 *const E[3], float2 *const H[3], int n
 
 cudaError_t launch_tile_step(const TileMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s)
 {
-    if (tj == 4) return launch_shape<4, 3>(m, tp, n, n_rchunks, s);
-    if (tj == 8) return launch_shape<8, 2>(m, tp, n, n_rchunks, s);
-    if (tj == 16) return launch_shape<16, 1>(m, tp, n, n_rchunks, s);
+    if (tj == 4) return launch_shape<4, 5, 3>(m, tp, n, n_rchunks, s);
+    if (tj == 8) return launch_shape<8, 4, 2>(m, tp, n, n_rchunks, s);
+    if (tj == 16) return launch_shape<16, 4, 1>(m, tp, n, n_rchunks, s);
     return cudaErrorInvalidValue;
 }
 
