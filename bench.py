@@ -62,7 +62,8 @@ def parse():
                     help="r-PML form: 0 real-radius CPML (default), 1 stretched coordinates")
     ap.add_argument("--batch", type=int, default=256, help="surrogate workload: samples per forward")
     ap.add_argument("--kernel", default="default",
-                    choices=["default", "split", "split1", "fused2", "fused4", "tile4", "tile8", "tile16", "tuned"],
+                    choices=["default", "split", "split1", "fused2", "fused4", "tile4", "tile8", "tile16", "etile8",
+                             "etile16", "etile32", "tuned"],
                     help="time-step kernel (default: the library's choice for the zone; tuned: the tile tuner's "
                          "pick)")
     return ap.parse_args()
@@ -301,7 +302,8 @@ def run_ours(a):
     spec = workload(a.time_steps)
     zone = Zone(spec, device=local)
     kern = {"split": (0, 16, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0),
-            "tile4": (3, 4, 0), "tile8": (3, 8, 0), "tile16": (3, 16, 0)}.get(a.kernel)
+            "tile4": (3, 4, 0), "tile8": (3, 8, 0), "tile16": (3, 16, 0),
+            "etile8": (4, 8, 0), "etile16": (4, 16, 0), "etile32": (4, 32, 0)}.get(a.kernel)
     if kern is not None:
         zone.set_kernel(*kern)
     elif a.kernel == "tuned":
@@ -378,7 +380,7 @@ def run_ours(a):
     # the library's sampled launches of one time step (see Zone.timing)
     avg = [m / max(n_timed, 1) for m in ms3]
     rpml = zone.radial_pml()
-    pair = variant == 0 and spec.n_z % 2 == 0 and spec.pml_z % 2 == 0
+    pair = variant in (0, 4) and spec.n_z % 2 == 0 and spec.pml_z % 2 == 0
     if variant == 1:
         kernels = [("k_stream_step", algorithmic_bytes_stream(spec), avg[0]),
                    ("k_dft_step", algorithmic_bytes_dft(spec, nq), avg[2])]
@@ -389,8 +391,8 @@ def run_ours(a):
         # the DFT history is written by the E update; the flush (every 32 steps)
         # is timed on its own below
         kernels = [("k_update_h_pair", algorithmic_bytes_h(spec, rpml), avg[0]),
-                   ("k_update_e_pair", algorithmic_bytes_e(spec, nq, with_dft=False, history=True, rpml=rpml),
-                    avg[1])]
+                   ("k_tile_e" if variant == 4 else "k_update_e_pair",
+                    algorithmic_bytes_e(spec, nq, with_dft=False, history=True, rpml=rpml), avg[1])]
     else:
         kernels = [("k_update_h", algorithmic_bytes_h(spec, rpml), avg[0]),
                    ("k_update_e", algorithmic_bytes_e(spec, nq, rpml=rpml), avg[1])]
@@ -420,7 +422,8 @@ def run_ours(a):
                          "sampled_launches": n_timed, "other_kernels": others},
             "step_kernel": {"variant": {0: "split, two z-cells per thread", 1: "fused, streaming along r",
                                         2: "split, one z-cell per thread",
-                                        3: "fused, TMA-staged tiles streaming along r"}[variant],
+                                        3: "fused, TMA-staged tiles streaming along r",
+                                        4: "split, E half on TMA-staged tiles streaming along r"}[variant],
                             "tile_phi": tile_phi,
                             "i_ranges": i_ranges, "radial_pml": zone.radial_pml()},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,

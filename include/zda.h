@@ -212,22 +212,31 @@ zda_status zda_copy_design_dft(zda_zone *zone, int which, float *out_dev, void *
  * (for launch accounting in benchmarks). */
 long long zda_zone_launch_count(const zda_zone *zone);
 
-/* Time-step kernel of the zone.  variant 0 (default): two launches per step
- * (H update, E update), in place, two z-cells per thread with 16-byte loads
- * when n_z and pml_z are even (wedge zones), else one z-cell per thread;
- * tile_phi in {4, 8, 16, 32} is the thread block's phi rows (256 threads;
- * other values, the default: 4 for zones of at most 16 phi cells, else 16),
- * i_ranges = 3 runs the E update at 3 thread blocks per
- * SM (fewer registers, a few spilled), else 2.  variant 2: the same with one z-cell per thread always.
- * variant 1 (annular zones, n_z <= 256): one fused launch per step (E and H
- * updated together, ping-pong field buffers, streaming along r; tile_phi in
- * {2, 4} phi rows per thread block, i_ranges radius ranges per phi tile,
- * 0 = as many as fit in one wave).  variant 3 (annular zones, even n_z and
- * pml_z, real-radius r-PML): one fused launch per step on tiles of tile_phi
- * in {4, 8, 16} phi rows x 32 z-cells staged into shared memory by TMA tensor
- * copies, each thread block streaming over one of i_ranges radius ranges
- * (0 = about four waves of blocks).  All compute the same scheme; results
- * agree to FP32 rounding. */
+/* Time-step kernel of the zone (Eqs. 3-4 advanced one step).  variant 0:
+ * two launches per step (H update, E update), in place, two z-cells per
+ * thread with 16-byte loads when n_z and pml_z are even (wedge zones), else
+ * one z-cell per thread; tile_phi in {4, 8, 16, 32} is the thread block's
+ * phi rows (256 threads; other values: 4 for zones of at most 16 phi cells,
+ * else 16), i_ranges = 3 runs the E update at 3 thread blocks per SM (fewer
+ * registers, a few spilled), else 2.  variant 2: the same with one z-cell
+ * per thread always.  variant 4 (annular zones, even n_z and pml_z,
+ * real-radius r-PML): the split step with its E update on tiles of tile_phi
+ * in {8, 16, 32} phi rows x 32 z-cells whose H and E values are staged into
+ * shared memory by TMA tensor copies several radii ahead, each thread block
+ * streaming over one of i_ranges radius ranges (0 = radius ranges of about
+ * 21 radii).  variant 1 (annular zones, n_z <= 256): one fused launch per
+ * step (E and H updated together, ping-pong field buffers, streaming along
+ * r; tile_phi in {2, 4} phi rows per thread block, i_ranges radius ranges
+ * per phi tile, 0 = as many as fit in one wave).  variant 3 (annular zones,
+ * even n_z and pml_z, real-radius r-PML): one fused launch per step on
+ * tiles of tile_phi in {4, 8, 16} phi rows x 32 z-cells staged by TMA, each
+ * thread block streaming over one of i_ranges radius ranges (0 = about 21
+ * radii each).  Default at zone creation: variant 4 with 16 rows where it
+ * applies and the zone has at least 16 phi cells, else variant 0; selecting
+ * the stretched r-PML (form 1) on a zone that still has the default falls
+ * back to variant 0, while an explicit variant 1, 3 or 4 refuses it.  All
+ * compute the same scheme; results agree to FP32 rounding.  Variants 1, 3
+ * and 4 bound their device-side waits (zda_zone_set_wait_limit). */
 zda_status zda_zone_set_kernel(zda_zone *zone, int variant, int tile_phi, int i_ranges);
 zda_status zda_zone_get_kernel(const zda_zone *zone, int *variant, int *tile_phi, int *i_ranges);
 
@@ -258,12 +267,13 @@ zda_status zda_zone_get_radial_pml(const zda_zone *zone, int *form);
  * zda_adjoint needs a new zda_forward).  Used by the tile-shape tuner. */
 zda_status zda_zone_time_steps(zda_zone *zone, int steps, double *ms_out_host, void *stream);
 
-/* The fused step (variant 1) waits on shared-memory barriers for its staged
- * copies; every wait gives up after `polls` polls (default 4194304), sets an
- * error word and lets the kernel finish, and the call then returns
+/* The fused and tiled steps (variants 1, 3, 4) wait on shared-memory
+ * barriers for their staged copies; every wait gives up after `polls` polls
+ * (default 4194304; variants 3 and 4 also after one second), sets an error
+ * word and lets the kernel finish, and the call then returns
  * ZDA_ERR_TIMEOUT (zda_forward, zda_adjoint and zda_iteration synchronise
- * their stream to read it).  inject_timeout != 0 is for tests of that path:
- * each radius also waits on a barrier that nothing completes. */
+ * their stream to read it).  inject_timeout != 0 is for tests of that path
+ * (variant 1): each radius also waits on a barrier that nothing completes. */
 zda_status zda_zone_set_wait_limit(zda_zone *zone, int polls, int inject_timeout);
 
 /* Kernel timing with CUDA events recorded on the launching stream: with

@@ -24,8 +24,8 @@ def shape_key(spec):
 def candidates(spec):
     """(variant, tile_phi, i_ranges) choices for the zone: the split step's
     thread-block shape (phi rows x z-pairs, 256 threads), the one-cell split
-    step, the streaming fused step, and the TMA-tiled fused step's tile rows
-    and radius ranges."""
+    step, the streaming fused step, the TMA-tiled fused step's tile rows
+    and radius ranges, and the split step with its E half on TMA tiles."""
     cands = [(2, 2, 0)]
     pair = spec.n_z % 2 == 0 and spec.pml_z % 2 == 0 and spec.n_fold > 0
     if pair:
@@ -38,6 +38,9 @@ def candidates(spec):
         for tj in (4, 8, 16):
             if tj <= 2 * max(spec.n_phi, 2):
                 cands += [(3, tj, 0), (3, tj, max(1, spec.n_r // 30))]
+        for tj in (8, 16, 32):
+            if tj <= 2 * max(spec.n_phi, 2):
+                cands.append((4, tj, 0))
     return sorted(set(cands))
 
 

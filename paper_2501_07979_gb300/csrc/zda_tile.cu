@@ -146,6 +146,167 @@ struct SG {                                                   // geometry of the
     static constexpr int NT = (NE + NH + NHALO + 31) / 32 * 32;
 };
 
+// H^{n+1/2} around an E pair (ke, ke+1) at radius i: the pair's own values,
+// H_phi / H_r one cell below in z ([0]), the row below in phi (J) and the
+// radius below (I).
+struct HAround {
+    float2 HPk[3], HRk[3];                  // index u + 1 = cell u, [0] = cell ke - 1
+    float2 HZk[2], HZJ[2], HRJ[2], HZI[2], HPI[2];
+};
+
+// One E item: the z-pair (ke, ke+1) of phi row je, streamed along r.  Holds
+// the pair's per-z coefficients; update() applies Eq. 4 (E^{n+1} from the H
+// values around the pair) with the E-side CPML, the sheet source and the
+// history writes of the time-blocked DFT, and stores the results.  Every
+// cell takes the interior coefficient form; the CPML recursions and the
+// source add their terms where they apply, so warps that straddle a CPML
+// slab edge or the source plane do not run two versions of the update.
+struct EItem {
+    int je, ke, kze, src_u, dk0;
+    bool valid, hist;
+    float bzn[2], czn[2], an[2], dn[2], ac[2], dc[2];
+    float2 src_pn, src_ph;
+    float src_amp;
+    float2 *hs;
+    size_t plane, ndes;
+
+    __device__ __forceinline__ void init(const StepParams &p, int n, int je_, int ke_)
+    {
+        je = je_;
+        ke = ke_;
+        valid = je < p.nphi && ke < p.nz;
+        kze = (ke < p.pz) ? ke : ((ke >= p.nz - p.pz) ? ke - (p.nz - 2 * p.pz) : -1);
+        src_u = -1;
+        src_pn = src_ph = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) { bzn[u] = czn[u] = dn[u] = dc[u] = 0.f; an[u] = ac[u] = 1.f; }
+        if (valid) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (kze >= 0) { bzn[u] = __ldg(p.t.bz_n + ke + u); czn[u] = __ldg(p.t.cz_n + ke + u) * p.inv_dz; }
+                an[u] = __ldg(p.t.a_n + ke + u); dn[u] = __ldg(p.t.d_n + ke + u);
+                ac[u] = __ldg(p.t.a_c + ke + u); dc[u] = __ldg(p.t.d_c + ke + u);
+            }
+            if (p.src_mode != SRC_NONE && (ke == p.src_k || ke + 1 == p.src_k)) {
+                src_u = p.src_k - ke;
+                src_pn = p.t.ph_n[je];
+                src_ph = p.t.ph_h[je];
+            }
+        }
+        src_amp = p.src_mode == SRC_PLANE_WAVE ? __ldg(p.t.pulse + n) * p.src_scale : 0.f;
+        plane = (size_t)p.nr * p.nphi;
+        ndes = p.des ? plane * p.des_nk : 0;
+        hs = (p.dft_hist && (p.des || p.mon)) ? p.dft_hist + (size_t)(n % DFT_BLOCK) * p.dft_ne : nullptr;
+        dk0 = ke - p.des_k0;
+        hist = hs && valid && ((p.des && dk0 + 1 >= 0 && dk0 < p.des_nk) || (p.mon && (ke == p.mon_k || ke + 1 == p.mon_k)));
+    }
+
+    // per-radius values of an E radius: tab = (1/r_i, 1/r_{i+1/2}, CPML b, c at r_i), rb = rho-bar factors
+    __device__ __forceinline__ static float4 tab_at(const StepParams &p, int i)
+    {
+        return make_float4(__ldg(p.t.inv_r_n + i), __ldg(p.t.inv_r_h + i), __ldg(p.t.br_n + i), __ldg(p.t.cr_n + i));
+    }
+    __device__ __forceinline__ void rb_at(const StepParams &p, int i, float &a, float &b, float &c) const
+    {
+        const int ij = i * p.nphi + je;
+        a = __ldg(p.rb_r + ij); b = __ldg(p.rb_p + ij); c = __ldg(p.rb_z + ij);
+    }
+
+    // E^{n+1}(i) of the pair from E^n (er, ep, ez) and the H values h; stores E into oE
+    __device__ __forceinline__ void update(const StepParams &p, int i, const float4 &tab, float rbr, float rbp, float rbz,
+                                           const HAround &h, C2 er, C2 ep, C2 ez, float2 *const *oE) const
+    {
+        const float2 zero = make_float2(0.f, 0.f);
+        const int nr = p.nr, nphi = p.nphi, nz = p.nz;
+        const float dt = p.dt, cdz = p.inv_dz, cdr = p.inv_dr;
+        const float irn = tab.x, irh = tab.y, brn = tab.z, crn = tab.w, crn_dr = tab.w * cdr;
+        const int ir = (i < p.pr_in) ? i : ((i >= nr - p.pr_out) ? i - (nr - p.pr_in - p.pr_out) : -1);
+        const int ij = i * nphi + je;
+        const int zx = ij * (2 * p.pz) + (kze >= 0 ? kze : 0);
+        const int rx = ((ir >= 0 ? ir : 0) * nphi + je) * nz + ke;
+        float2 *ER[2] = {&er.a, &er.b}, *EP[2] = {&ep.a, &ep.b}, *EZ[2] = {&ez.a, &ez.b};
+        C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
+        if (kze >= 0) { ps_r = ldg4(p.psi.er_z + zx); ps_p = ldg4(p.psi.ep_z + zx); }
+        if (ir >= 0) { ps_pr = ldg4(p.psi.ep_r + rx); ps_zr = ldg4(p.psi.ez_r + rx); }
+        float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
+        float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
+        float2 jr = zero, jp = zero;                          // source current of this radius (cell src_u)
+        if (src_u >= 0) {
+            if (p.src_mode == SRC_PLANE_WAVE) {
+                jr = c_scale(src_pn, src_amp);
+                jp = make_float2(-src_ph.y * src_amp, src_ph.x * src_amp);
+            } else {
+                jr = c_mul(src_pn, p.src_rad[i]);
+                jp = c_mul(src_ph, p.src_rad[nr + i]);
+            }
+        }
+        const float cph_h = irh * p.inv_dphi, cph_n = irn * p.inv_dphi, cm = 0.5f * irn;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float cr = dt * t_rcp(an[u] + dn[u] * rbr), cp = dt * t_rcp(an[u] + dn[u] * rbp);
+            const float cz = dt * t_rcp(ac[u] + dc[u] * rbz);
+            const int kk = ke + u;
+            // E_r: (1/r) dH_z/dphi - dH_phi/dz
+            const float2 d_hp = f_sub(h.HPk[u + 1], h.HPk[u]);
+            float2 t = f_sub(h.HZk[u], h.HZJ[u]);
+            float2 a = make_float2(cph_h * t.x, cph_h * t.y);
+            a = f_axpy(-cdz, d_hp, a);
+            if (kze >= 0 && kk > 0) {
+                *PR[u] = f_axpy(czn[u], d_hp, c_scale(*PR[u], bzn[u]));
+                a = f_sub(a, *PR[u]);
+            }
+            // E_phi: dH_r/dz - dH_z/dr
+            const float2 d_hr = f_sub(h.HRk[u + 1], h.HRk[u]), d_hzi = f_sub(h.HZk[u], h.HZI[u]);
+            float2 b = make_float2(cdz * d_hr.x, cdz * d_hr.y);
+            b = f_axpy(-cdr, d_hzi, b);
+            const bool upd_p = kk > 0 && i > 0;
+            if (kze >= 0 && upd_p) {
+                *PP[u] = f_axpy(czn[u], d_hr, c_scale(*PP[u], bzn[u]));
+                b = f_add(b, *PP[u]);
+            }
+            if (ir >= 0 && upd_p) {
+                *PPR[u] = f_axpy(crn_dr, d_hzi, c_scale(*PPR[u], brn));
+                b = f_sub(b, *PPR[u]);
+            }
+            if (u == src_u) { a = f_sub(a, jr); b = f_sub(b, jp); }
+            if (kk > 0) *ER[u] = f_axpy(cr, a, *ER[u]);
+            if (upd_p) *EP[u] = f_axpy(cp, b, *EP[u]);
+            // E_z: (1/r) d(r H_phi)/dr - (1/r) dH_r/dphi
+            t = f_sub(h.HPk[u + 1], h.HPI[u]);
+            float2 c = make_float2(cdr * t.x, cdr * t.y);
+            c = f_axpy(cm, f_add(h.HPk[u + 1], h.HPI[u]), c);
+            if (ir >= 0 && i > 0) {
+                *PZR[u] = f_axpy(crn, c, c_scale(*PZR[u], brn));
+                c = f_add(c, *PZR[u]);
+            }
+            c = f_axpy(-cph_n, f_sub(h.HRk[u + 1], h.HRJ[u]), c);
+            if (i > 0) *EZ[u] = f_axpy(cz, c, *EZ[u]);
+        }
+        const int o = i * (nphi * nz) + je * nz + ke;        // a zone's field < 2^31 cells
+        st4(oE[0] + o, er);
+        st4(oE[1] + o, ep);
+        st4(oE[2] + o, ez);
+        if (kze >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
+        if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
+        if (hist) {                                           // history slot of the time-blocked DFT
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int dk = dk0 + u;
+                if (p.des && dk >= 0 && dk < p.des_nk) {
+                    const size_t e = (size_t)ij * p.des_nk + dk;
+                    hs[e] = *ER[u];
+                    hs[ndes + e] = *EP[u];
+                    hs[2 * ndes + e] = *EZ[u];
+                }
+                if (p.mon && ke + u == p.mon_k) {
+                    hs[3 * ndes + ij] = *ER[u];
+                    hs[3 * ndes + plane + ij] = *EP[u];
+                }
+            }
+        }
+    }
+};
+
 template <int TJ, int NS, int MINB>
 __global__ void __launch_bounds__(SG<TJ, NS>::NT, MINB)
     k_tile_step(const __grid_constant__ TileMaps m, const TileParams tp, const int n, const int i_range)
@@ -224,155 +385,41 @@ __global__ void __launch_bounds__(SG<TJ, NS>::NT, MINB)
     if (tid < G::NE) {
         // ================= E items: E^{n+1}(r-1) at iteration r, row se, pair pe (fixed)
         const int se = tid / G::KP + 1, pe = tid % G::KP + 1;
-        const int je = j0 - 1 + se, ke = k0 - 2 + 2 * pe;
-        const bool e_valid = je < nphi && ke < nz;
-        const int kze = (ke < p.pz) ? ke : ((ke >= nz - p.pz) ? ke - (nz - 2 * p.pz) : -1);
-        float bzn[2] = {0.f, 0.f}, czn[2] = {0.f, 0.f}, an[2] = {1.f, 1.f}, dn[2] = {0.f, 0.f},
-              ac[2] = {1.f, 1.f}, dc[2] = {0.f, 0.f};
-        float2 src_pn = zero, src_ph = zero;
-        int src_u = -1;                                       // which cell of the pair carries the source
-        if (e_valid) {
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                if (kze >= 0) { bzn[u] = __ldg(p.t.bz_n + ke + u); czn[u] = __ldg(p.t.cz_n + ke + u) * p.inv_dz; }
-                an[u] = __ldg(p.t.a_n + ke + u); dn[u] = __ldg(p.t.d_n + ke + u);
-                ac[u] = __ldg(p.t.a_c + ke + u); dc[u] = __ldg(p.t.d_c + ke + u);
-            }
-            if (p.src_mode != SRC_NONE && (ke == p.src_k || ke + 1 == p.src_k)) {
-                src_u = p.src_k - ke;
-                src_pn = p.t.ph_n[je];
-                src_ph = p.t.ph_h[je];
-            }
-        }
-        const float src_amp = p.src_mode == SRC_PLANE_WAVE ? __ldg(p.t.pulse + n) * p.src_scale : 0.f;
+        EItem it;
+        it.init(p, n, j0 - 1 + se, k0 - 2 + 2 * pe);
         const int he_own = G::H_OFF + se * G::HZ + 2 * pe, he_jm = G::H_OFF + (se - 1) * G::HZ + 2 * pe;
         const int ee_own = G::E_OFF + se * G::EZ + 2 * pe;
-        const size_t plane = (size_t)nr * nphi, ndes = p.des ? plane * p.des_nk : 0;
-        float2 *hs = (p.dft_hist && (p.des || p.mon)) ? p.dft_hist + (size_t)(n % DFT_BLOCK) * p.dft_ne : nullptr;
-        const int dk0 = ke - p.des_k0;
-        const bool e_hist = hs && e_valid &&
-                            ((p.des && dk0 + 1 >= 0 && dk0 < p.des_nk) || (p.mon && (ke == p.mon_k || ke + 1 == p.mon_k)));
-        const float cdz = p.inv_dz, cdr = p.inv_dr;
         // per-radius values of the next E radius, loaded one iteration ahead
-        auto rb_load = [&](int i, float &a, float &b, float &c) {
-            if (e_valid && i >= 0 && i < nr) {
-                const int ij = i * nphi + je;
-                a = __ldg(p.rb_r + ij); b = __ldg(p.rb_p + ij); c = __ldg(p.rb_z + ij);
-            }
-        };
         float rbr = 0.f, rbp = 0.f, rbz = 0.f, nrbr = 0.f, nrbp = 0.f, nrbz = 0.f;
-        float4 tab = make_float4(0.f, 0.f, 0.f, 0.f), ntab = tab;   // 1/r_i, 1/r_{i+1/2}, CPML b, c at r_i
-        auto tab_load = [&](int i, float4 &t) {
-            if (i >= 0 && i < nr)
-                t = make_float4(__ldg(p.t.inv_r_n + i), __ldg(p.t.inv_r_h + i), __ldg(p.t.br_n + i), __ldg(p.t.cr_n + i));
-        };
-        rb_load(ib, nrbr, nrbp, nrbz);
-        tab_load(ib, ntab);
+        float4 tab = make_float4(0.f, 0.f, 0.f, 0.f), ntab = tab;
+        if (ib < nr) {
+            ntab = EItem::tab_at(p, ib);
+            if (it.valid) it.rb_at(p, ib, nrbr, nrbp, nrbz);
+        }
         for (int r = r0; r <= ie && !failed; ++r) {
             const int i = r - 1;                              // radius of this iteration's E update
             rbr = nrbr; rbp = nrbp; rbz = nrbz;
             tab = ntab;
-            rb_load(i + 1, nrbr, nrbp, nrbz);
-            tab_load(i + 1, ntab);
-            if (i >= ib && e_valid) {
+            if (i + 1 >= 0 && i + 1 < nr) {
+                ntab = EItem::tab_at(p, i + 1);
+                if (it.valid) it.rb_at(p, i + 1, nrbr, nrbp, nrbz);
+            }
+            if (i >= ib && it.valid) {
                 const float2 *gq = group(i);                  // H^{n+1/2}(i)
                 const float2 *gp = group(i - 1);              // E^n(i), H^{n+1/2}(i-1)
+                HAround h;
                 const C2 hr = lds4(gq + he_own), hp = lds4(gq + he_own + G::HS), hz = lds4(gq + he_own + 2 * G::HS);
                 const C2 hz_jm = lds4(gq + he_jm + 2 * G::HS), hr_jm = lds4(gq + he_jm);
-                const float2 hp_km = gq[he_own + G::HS - 1], hr_km = gq[he_own - 1];
                 const C2 hz_im = lds4(gp + he_own + 2 * G::HS), hp_im = lds4(gp + he_own + G::HS);
-                C2 er = lds4(gp + ee_own), ep = lds4(gp + ee_own + G::ES), ez = lds4(gp + ee_own + 2 * G::ES);
-                const float irn = tab.x, irh = tab.y;
-                const int ir = (i < p.pr_in) ? i : ((i >= nr - p.pr_out) ? i - (nr - p.pr_in - p.pr_out) : -1);
-                const int ij = i * nphi + je;
-                const int zx = ij * (2 * p.pz) + (kze >= 0 ? kze : 0);
-                const int rx = ((ir >= 0 ? ir : 0) * nphi + je) * nz + ke;
-                const float2 HPk[3] = {hp_km, hp.a, hp.b}, HRk[3] = {hr_km, hr.a, hr.b};
-                const float2 HZk[2] = {hz.a, hz.b}, HZJ[2] = {hz_jm.a, hz_jm.b}, HRJ[2] = {hr_jm.a, hr_jm.b};
-                const float2 HZI[2] = {hz_im.a, hz_im.b}, HPI[2] = {hp_im.a, hp_im.b};
-                float2 *ER[2] = {&er.a, &er.b}, *EP[2] = {&ep.a, &ep.b}, *EZ[2] = {&ez.a, &ez.b};
-                C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
-                if (kze >= 0) { ps_r = ldg4(p.psi.er_z + zx); ps_p = ldg4(p.psi.ep_z + zx); }
-                const float brn = tab.z, crn = tab.w, crn_dr = tab.w * cdr;
-                if (ir >= 0) { ps_pr = ldg4(p.psi.ep_r + rx); ps_zr = ldg4(p.psi.ez_r + rx); }
-                float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
-                float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
-                float2 jr = zero, jp = zero;                  // source current of this radius (cell src_u)
-                if (src_u >= 0) {
-                    if (p.src_mode == SRC_PLANE_WAVE) {
-                        jr = c_scale(src_pn, src_amp);
-                        jp = make_float2(-src_ph.y * src_amp, src_ph.x * src_amp);
-                    } else {
-                        jr = c_mul(src_pn, p.src_rad[i]);
-                        jp = c_mul(src_ph, p.src_rad[nr + i]);
-                    }
-                }
-                // one coefficient form for every cell; the CPML recursions and the source
-                // add their terms where they apply (uniform across most warps)
-                const float cph_h = irh * p.inv_dphi, cph_n = irn * p.inv_dphi, cm = 0.5f * irn;
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const float cr = dt * t_rcp(an[u] + dn[u] * rbr), cp = dt * t_rcp(an[u] + dn[u] * rbp);
-                    const float cz = dt * t_rcp(ac[u] + dc[u] * rbz);
-                    // E_r: (1/r) dH_z/dphi - dH_phi/dz
-                    const float2 d_hp = f_sub(HPk[u + 1], HPk[u]);
-                    float2 t = f_sub(HZk[u], HZJ[u]);
-                    float2 a = make_float2(cph_h * t.x, cph_h * t.y);
-                    a = f_axpy(-cdz, d_hp, a);
-                    const int kk = ke + u;
-                    if (kze >= 0 && kk > 0) {
-                        *PR[u] = f_axpy(czn[u], d_hp, c_scale(*PR[u], bzn[u]));
-                        a = f_sub(a, *PR[u]);
-                    }
-                    // E_phi: dH_r/dz - dH_z/dr
-                    const float2 d_hr = f_sub(HRk[u + 1], HRk[u]), d_hzi = f_sub(HZk[u], HZI[u]);
-                    float2 b = make_float2(cdz * d_hr.x, cdz * d_hr.y);
-                    b = f_axpy(-cdr, d_hzi, b);
-                    const bool upd_p = kk > 0 && i > 0;
-                    if (kze >= 0 && upd_p) {
-                        *PP[u] = f_axpy(czn[u], d_hr, c_scale(*PP[u], bzn[u]));
-                        b = f_add(b, *PP[u]);
-                    }
-                    if (ir >= 0 && upd_p) {
-                        *PPR[u] = f_axpy(crn_dr, d_hzi, c_scale(*PPR[u], brn));
-                        b = f_sub(b, *PPR[u]);
-                    }
-                    if (u == src_u) { a = f_sub(a, jr); b = f_sub(b, jp); }
-                    if (kk > 0) *ER[u] = f_axpy(cr, a, *ER[u]);
-                    if (upd_p) *EP[u] = f_axpy(cp, b, *EP[u]);
-                    // E_z: (1/r) d(r H_phi)/dr - (1/r) dH_r/dphi
-                    t = f_sub(HPk[u + 1], HPI[u]);
-                    float2 c = make_float2(cdr * t.x, cdr * t.y);
-                    c = f_axpy(cm, f_add(HPk[u + 1], HPI[u]), c);
-                    if (ir >= 0 && i > 0) {
-                        *PZR[u] = f_axpy(crn, c, c_scale(*PZR[u], brn));
-                        c = f_add(c, *PZR[u]);
-                    }
-                    c = f_axpy(-cph_n, f_sub(HRk[u + 1], HRJ[u]), c);
-                    if (i > 0) *EZ[u] = f_axpy(cz, c, *EZ[u]);
-                }
-                const int o = i * si + je * sj + ke;
-                st4(tp.oE[0] + o, er);
-                st4(tp.oE[1] + o, ep);
-                st4(tp.oE[2] + o, ez);
-                if (kze >= 0) { st4(p.psi.er_z + zx, ps_r); st4(p.psi.ep_z + zx, ps_p); }
-                if (ir >= 0) { st4(p.psi.ep_r + rx, ps_pr); st4(p.psi.ez_r + rx, ps_zr); }
-                if (e_hist) {                                 // history slot of the time-blocked DFT
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int dk = dk0 + u;
-                        if (p.des && dk >= 0 && dk < p.des_nk) {
-                            const size_t e = (size_t)ij * p.des_nk + dk;
-                            hs[e] = *ER[u];
-                            hs[ndes + e] = *EP[u];
-                            hs[2 * ndes + e] = *EZ[u];
-                        }
-                        if (p.mon && ke + u == p.mon_k) {
-                            hs[3 * ndes + ij] = *ER[u];
-                            hs[3 * ndes + plane + ij] = *EP[u];
-                        }
-                    }
-                }
+                h.HPk[0] = gq[he_own + G::HS - 1]; h.HPk[1] = hp.a; h.HPk[2] = hp.b;
+                h.HRk[0] = gq[he_own - 1]; h.HRk[1] = hr.a; h.HRk[2] = hr.b;
+                h.HZk[0] = hz.a; h.HZk[1] = hz.b;
+                h.HZJ[0] = hz_jm.a; h.HZJ[1] = hz_jm.b;
+                h.HRJ[0] = hr_jm.a; h.HRJ[1] = hr_jm.b;
+                h.HZI[0] = hz_im.a; h.HZI[1] = hz_im.b;
+                h.HPI[0] = hp_im.a; h.HPI[1] = hp_im.b;
+                it.update(p, i, tab, rbr, rbp, rbz, h, lds4(gp + ee_own), lds4(gp + ee_own + G::ES),
+                          lds4(gp + ee_own + 2 * G::ES), tp.oE);
             }
             // g(r+1) landed (thread 0 waits); H(r) published; g(r-2) free.  A wait that
             // gave up ends the loop for every thread.
@@ -513,6 +560,145 @@ __global__ void __launch_bounds__(SG<TJ, NS>::NT, MINB)
         for (int r = max(r0 - 1, last_issued - G::NSLOT + 1); r <= last_issued; ++r) wait_group(r);
 }
 
+// ---------------------------------------------------------------- E update on TMA-staged tiles
+// The E half of the split step as a radius-streamed tile kernel: the split
+// H update (zda_pair.cu) has written H^{n+1/2}; this kernel reads it
+// together with E^n through a ring of TMA load groups, so its loads are in
+// flight several radii ahead of the arithmetic instead of one round trip per
+// thread, and updates E in place.  Load group g(r) = {H^{n+1/2}(r) rows
+// j0-1 .. j0+TJ-1 and z k0-2 .. k0+31, E^n(r) rows j0 .. j0+TJ-1 and z
+// k0 .. k0+31, and for the tile at phi row 0 the wrapped H row n_phi-1};
+// iteration r updates E(r) from g(r) and g(r-1).  After iteration r thread
+// 0 waits for g(r+1) and the block barrier publishes it; then g(r+NSLOT-1)
+// is issued into the slot of g(r-1).  The E box covers the tile's own cells
+// only (no other CTA writes them), so reading E^n and writing E^{n+1} in
+// the same buffer is safe; the group at r = ib-1 (the radius below the
+// range, read for its H) carries no E box.
+template <int TJ, int NS>
+struct SE {                                                   // geometry of the E tile kernel
+    static constexpr int KP = TILE_KZ / 2;                    // z-pairs of a tile
+    static constexpr int HZ = TILE_KZ + 2, HJ = TJ + 1;       // H slab: z from k0-2, rows from j0-1
+    static constexpr int al(int x) { return (x + 15) & ~15; } // 128-byte aligned regions (float2 units)
+    static constexpr int HS = al(HJ * HZ), ES = al(TJ * TILE_KZ), RW = al(HZ);
+    static constexpr int H_OFF = 0, E_OFF = 3 * HS, WHL = E_OFF + 3 * ES;
+    static constexpr int GROUP = WHL + 3 * RW;
+    static constexpr int NSLOT = NS;
+    static constexpr int NT = TJ * KP;                        // one E item (z-pair) per thread
+};
+
+template <int TJ, int NS, int MINB>
+__global__ void __launch_bounds__(SE<TJ, NS>::NT, MINB)
+    k_tile_e(const __grid_constant__ TileEMaps m, const TileParams tp, const int n, const int i_range)
+{
+    using G = SE<TJ, NS>;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT];
+    __shared__ int abort_s;
+    const uint32_t raw_s = s_addr(smem_raw);
+    const uint32_t base_s = (raw_s + 127u) & ~127u;
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + (base_s - raw_s));
+
+    const StepParams &p = tp.p;
+    const int nr = p.nr, nphi = p.nphi, nz = p.nz;
+    const int nzc = (nz + TILE_KZ - 1) / TILE_KZ;
+    const int k0 = (blockIdx.x % nzc) * TILE_KZ;
+    const int j0 = (blockIdx.x / nzc) * TJ;
+    const int ib = blockIdx.y * i_range, ie = min(nr, ib + i_range);
+    const int tid = threadIdx.x;
+    const bool wlo = j0 == 0;                                 // row j0-1 is the wrapped row n_phi-1
+    const int xh = 2 * (k0 - 2), xe = 2 * k0;
+
+    auto slot_of = [&](int r) { return (unsigned)(r - ib + 1) % (unsigned)G::NSLOT; };
+    auto parity_of = [&](int r) { return ((unsigned)(r - ib + 1) / (unsigned)G::NSLOT) & 1u; };
+    auto group = [&](int r) { return sm + slot_of(r) * G::GROUP; };
+    auto issue = [&](int r) {
+        const unsigned sl = slot_of(r);
+        const uint32_t g = base_s + (uint32_t)(sl * G::GROUP) * 8u;
+        const uint32_t bar = s_addr(&bar_mem[sl]);
+        const bool with_e = r >= ib;
+        uint32_t bytes = 3u * G::HZ * G::HJ * 8u;
+        if (with_e) bytes += 3u * TILE_KZ * TJ * 8u;
+        if (wlo) bytes += 3u * G::HZ * 8u;
+        t_mbar_expect_tx(bar, bytes);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            tma3(g + (G::H_OFF + c * G::HS) * 8u, &m.h[c], xh, j0 - 1, r, bar);
+            if (with_e) tma3(g + (G::E_OFF + c * G::ES) * 8u, &m.eo[c], xe, j0, r, bar);
+            if (wlo) tma3(g + (G::WHL + c * G::RW) * 8u, &m.hw[c], xh, nphi - 1, r, bar);
+        }
+    };
+    auto wait_group = [&](int r) { return t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err); };
+
+    if (tid == 0) {
+        for (int s = 0; s < G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
+        abort_s = *(volatile int *)tp.err;                    // an earlier launch gave up waiting: do nothing
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (abort_s) return;
+    // groups g(ib-1) .. g(ib+NSLOT-2) now (every slot); g(r+NSLOT-1) after iteration r
+    constexpr int AHEAD = G::NSLOT - 1;
+    int last_issued = min(ie - 1, ib - 1 + AHEAD);
+    bool failed = false;
+    if (tid == 0) {
+        for (int r = ib - 1; r <= last_issued; ++r) issue(r);
+        failed = !wait_group(ib - 1);
+        if (!failed && ib < ie) failed = !wait_group(ib);
+    }
+    failed = __syncthreads_or(failed);
+
+    const int se = tid / G::KP, pe = tid % G::KP;
+    EItem it;
+    it.init(p, n, j0 + se, k0 + 2 * pe);
+    const bool jm_wrap = wlo && se == 0;                      // row below is the wrapped row (Bloch phase)
+    const int h_own = G::H_OFF + (se + 1) * G::HZ + 2 + 2 * pe;
+    const int h_jm = jm_wrap ? G::WHL + 2 + 2 * pe : G::H_OFF + se * G::HZ + 2 + 2 * pe;
+    const int jm_cs = jm_wrap ? G::RW : G::HS;                // component stride of that row's region
+    const int e_own = G::E_OFF + se * TILE_KZ + 2 * pe;
+    float rbr = 0.f, rbp = 0.f, rbz = 0.f, nrbr = 0.f, nrbp = 0.f, nrbz = 0.f;
+    float4 tab = make_float4(0.f, 0.f, 0.f, 0.f), ntab = tab;
+    if (ib < ie) {
+        ntab = EItem::tab_at(p, ib);
+        if (it.valid) it.rb_at(p, ib, nrbr, nrbp, nrbz);
+    }
+    for (int r = ib; r < ie && !failed; ++r) {
+        rbr = nrbr; rbp = nrbp; rbz = nrbz;
+        tab = ntab;
+        if (r + 1 < ie) {                                     // next radius, one iteration ahead
+            ntab = EItem::tab_at(p, r + 1);
+            if (it.valid) it.rb_at(p, r + 1, nrbr, nrbp, nrbz);
+        }
+        if (it.valid) {
+            const float2 *gq = group(r);                      // H^{n+1/2}(r), E^n(r)
+            const float2 *gp = group(r - 1);                  // H^{n+1/2}(r-1)
+            HAround h;
+            const C2 hr = lds4(gq + h_own), hp = lds4(gq + h_own + G::HS), hz = lds4(gq + h_own + 2 * G::HS);
+            C2 hz_jm = lds4(gq + h_jm + 2 * jm_cs), hr_jm = lds4(gq + h_jm);
+            if (jm_wrap) { hz_jm = cmul2(p.bloch_inv, hz_jm); hr_jm = cmul2(p.bloch_inv, hr_jm); }
+            const C2 hz_im = lds4(gp + h_own + 2 * G::HS), hp_im = lds4(gp + h_own + G::HS);
+            h.HPk[0] = gq[h_own + G::HS - 1]; h.HPk[1] = hp.a; h.HPk[2] = hp.b;
+            h.HRk[0] = gq[h_own - 1]; h.HRk[1] = hr.a; h.HRk[2] = hr.b;
+            h.HZk[0] = hz.a; h.HZk[1] = hz.b;
+            h.HZJ[0] = hz_jm.a; h.HZJ[1] = hz_jm.b;
+            h.HRJ[0] = hr_jm.a; h.HRJ[1] = hr_jm.b;
+            h.HZI[0] = hz_im.a; h.HZI[1] = hz_im.b;
+            h.HPI[0] = hp_im.a; h.HPI[1] = hp_im.b;
+            it.update(p, r, tab, rbr, rbp, rbz, h, lds4(gq + e_own), lds4(gq + e_own + G::ES),
+                      lds4(gq + e_own + 2 * G::ES), tp.oE);
+        }
+        if (tid == 0 && r + 1 < ie) failed = !wait_group(r + 1);
+        if (__syncthreads_or(failed)) { failed = true; break; }
+        if (tid == 0 && r + AHEAD < ie) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(r + AHEAD);
+            last_issued = r + AHEAD;
+        }
+    }
+    if (failed && tid == 0)                                   // copies still in flight
+        for (int r = max(ib - 1, last_issued - G::NSLOT + 1); r <= last_issued; ++r) wait_group(r);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -561,6 +747,31 @@ const TileShape *shape_of(int tj)
         if (t.tj == tj) return &t;
     return nullptr;
 }
+
+template <int TJ, int NS, int MINB>
+cudaError_t launch_e_shape(const TileEMaps &m, const TileParams &tp, int n, int n_rchunks, cudaStream_t s)
+{
+    using G = SE<TJ, NS>;
+    const size_t bytes = (size_t)G::NSLOT * G::GROUP * sizeof(float2) + 128;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static unsigned attr_done = 0;                            // per device (bit), set once
+    if (dev < 32 && !(attr_done & (1u << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_e<TJ, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_done |= 1u << dev;
+    }
+    const int nzc = (tp.p.nz + TILE_KZ - 1) / TILE_KZ, njt = (tp.p.nphi + TJ - 1) / TJ;
+    const int nrc = std::max(1, std::min(n_rchunks, tp.p.nr));
+    const int i_range = (tp.p.nr + nrc - 1) / nrc;
+    dim3 g((unsigned)(nzc * njt), (unsigned)((tp.p.nr + i_range - 1) / i_range));
+    k_tile_e<TJ, NS, MINB><<<g, G::NT, bytes, s>>>(m, tp, n, i_range);
+    return cudaGetLastError();
+}
+
+template <int TJ, int NS>
+size_t e_shape_bytes() { return (size_t)SE<TJ, NS>::NSLOT * SE<TJ, NS>::GROUP * sizeof(float2) + 128; }
 
 template <int TJ, int NS>
 size_t shape_bytes() { return (size_t)SG<TJ, NS>::NSLOT * SG<TJ, NS>::GROUP * sizeof(float2) + 128; }
@@ -624,6 +835,63 @@ bool encode_tile_maps(TileMaps *m, float2 *const E[3], float2 *const H[3], int n
         }
     }
     return true;
+}
+
+bool tile_e_shape_ok(int tj) { return tj == 8 || tj == 16 || tj == 32; }
+
+size_t tile_e_smem_bytes(int tj)
+{
+    if (tj == 8) return e_shape_bytes<8, 6>();
+    if (tj == 16) return e_shape_bytes<16, 4>();
+    if (tj == 32) return e_shape_bytes<32, 4>();
+    return 0;
+}
+
+int tile_e_auto_rchunks(int tj, int nr, int nphi, int nz, int sms)
+{
+    const size_t b = tile_e_smem_bytes(tj);
+    const int per_wave = sms * std::max(1, b ? (int)std::min<size_t>(8, (227 * 1024) / (b + 1024)) : 1);
+    const int tiles = ((nz + TILE_KZ - 1) / TILE_KZ) * ((nphi + tj - 1) / tj);
+    // radius chunks of about 21 radii, at least four waves of thread blocks, at least 8 radii each
+    const int waves4 = (4 * per_wave + tiles - 1) / std::max(tiles, 1);
+    const int c = std::max(waves4, (nr + 10) / 21);
+    return std::max(1, std::min(c, nr / 8));
+}
+
+bool encode_tile_e_maps(TileEMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
+                        const char **why)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        *why = "the driver's cuTensorMapEncodeTiled is not available";
+        return false;
+    }
+    const cuuint64_t dims[3] = {2ull * (cuuint64_t)nz, (cuuint64_t)nphi, (cuuint64_t)nr};
+    const cuuint64_t strides[2] = {(cuuint64_t)nz * 8ull, (cuuint64_t)nphi * (cuuint64_t)nz * 8ull};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const cuuint32_t beo[3] = {2u * TILE_KZ, (cuuint32_t)tj, 1u};
+    const cuuint32_t bh[3] = {2u * (TILE_KZ + 2), (cuuint32_t)(tj + 1), 1u};
+    const cuuint32_t bhw[3] = {2u * (TILE_KZ + 2), 1u, 1u};
+    auto one = [&](CUtensorMap *t, void *base, const cuuint32_t *box) {
+        return enc(t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    for (int c = 0; c < 3; ++c) {
+        if (!one(&m->eo[c], E[c], beo) || !one(&m->h[c], H[c], bh) || !one(&m->hw[c], H[c], bhw)) {
+            *why = "cuTensorMapEncodeTiled refused the field layout";
+            return false;
+        }
+    }
+    return true;
+}
+
+cudaError_t launch_tile_e(const TileEMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s)
+{
+    if (tj == 8) return launch_e_shape<8, 6, 2>(m, tp, n, n_rchunks, s);
+    if (tj == 16) return launch_e_shape<16, 4, 2>(m, tp, n, n_rchunks, s);
+    if (tj == 32) return launch_e_shape<32, 4, 1>(m, tp, n, n_rchunks, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile_step(const TileMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s)

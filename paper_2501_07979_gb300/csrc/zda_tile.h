@@ -13,6 +13,12 @@ struct TileMaps {
     CUtensorMap e[3], ew[3], h[3], hw[3];
 };
 
+// Tensor maps for the E tile kernel (split step, E half): the tile's own E
+// box, the H slab (one row and two z-cells more below), the wrapped H row.
+struct TileEMaps {
+    CUtensorMap eo[3], h[3], hw[3];
+};
+
 struct TileParams {
     StepParams p;                 // tables, E-side CPML (updated in place), density, source, DFT history
     float2 *oE[3], *oH[3];        // destination buffer: E^{n+1}, H^{n+1/2}
@@ -33,5 +39,14 @@ int tile_auto_rchunks(int tj, int nr, int nphi, int nz, int sms);
 bool encode_tile_maps(TileMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
                       const char **why);
 cudaError_t launch_tile_step(const TileMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s);
+
+// E half of the split step on TMA-staged tiles of tj in {8, 16, 32} phi rows x 32 z-cells,
+// updating E in place; TileParams::oE = the field buffer's E, the H-side members unused
+bool tile_e_shape_ok(int tj);
+size_t tile_e_smem_bytes(int tj);
+int tile_e_auto_rchunks(int tj, int nr, int nphi, int nz, int sms);
+bool encode_tile_e_maps(TileEMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
+                        const char **why);
+cudaError_t launch_tile_e(const TileEMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s);
 
 }  // namespace zda

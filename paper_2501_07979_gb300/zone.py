@@ -203,7 +203,8 @@ class Zone:
         """Time-step kernel (zda_zone_set_kernel): 0 split H/E (tile_phi = phi
         rows per block), 1 fused streaming (tile_phi 2 or 4), 2 split one cell
         per thread, 3 fused TMA tiles (tile_phi 4, 8 or 16; i_ranges radius
-        ranges)."""
+        ranges), 4 split with the E half on TMA tiles (tile_phi 8, 16 or 32;
+        i_ranges radius ranges)."""
         check(_lib.lib().zda_zone_set_kernel(self.handle, int(variant), int(tile_phi), int(i_ranges)))
 
     def set_radial_pml(self, form):

@@ -28,15 +28,16 @@ KERNELS = {"split": (0, 2, 0), "split_r4": (0, 4, 0), "split_r16": (0, 16, 0), "
            "split1": (2, 2, 0),
            "fused2": (1, 2, 0), "fused4": (1, 4, 0),
            "fused2_ir3": (1, 2, 3), "tile8": (3, 8, 0), "tile4": (3, 4, 0), "tile16": (3, 16, 0),
-           "tile8_r5": (3, 8, 5)}
+           "tile8_r5": (3, 8, 5), "etile8": (4, 8, 0), "etile16": (4, 16, 0), "etile32": (4, 32, 0),
+           "etile16_r7": (4, 16, 7)}
 
 
 def _zone(spec, kernel=None):
     from paper_2501_07979_gb300 import Zone
     if kernel is not None and KERNELS[kernel][0] == 1 and (spec.n_z % 2 or spec.n_fold == 0):
         pytest.skip("the fused step needs an even n_z and an annular zone")
-    if kernel is not None and KERNELS[kernel][0] == 3 and (spec.n_z % 2 or spec.pml_z % 2 or spec.n_fold == 0):
-        pytest.skip("the tile step needs even n_z and pml_z and an annular zone")
+    if kernel is not None and KERNELS[kernel][0] in (3, 4) and (spec.n_z % 2 or spec.pml_z % 2 or spec.n_fold == 0):
+        pytest.skip("the tile kernels need even n_z and pml_z and an annular zone")
     z = Zone(spec, device=0)
     if kernel is not None:
         z.set_kernel(*KERNELS[kernel])
@@ -156,7 +157,8 @@ def test_forward_uniform_density(value):
     assert _rel(S, S_ref) < FIELD_TOL
 
 
-@pytest.mark.parametrize("kernel", ["fused2", "fused4", "split1", "tile4", "tile8", "tile16"])
+@pytest.mark.parametrize("kernel", ["fused2", "fused4", "split1", "tile4", "tile8", "tile16", "etile8", "etile16",
+                                    "etile32"])
 def test_fused_step_equals_split_step(kernel):
     """The fused single-launch step and the split H/E launches compute the
     same scheme: fields and DFTs agree to FP32 rounding on the wide-zone grid
@@ -205,7 +207,8 @@ GRAD_SPECS = {
 }
 
 
-@pytest.mark.parametrize("kernel", ["split", "split1", "fused2", "fused4", "tile8", "tile4", "tile8_r5"])
+@pytest.mark.parametrize("kernel", ["split", "split1", "fused2", "fused4", "tile8", "tile4", "tile8_r5", "etile16",
+                                    "etile8", "etile16_r7"])
 @pytest.mark.parametrize("name", list(GRAD_SPECS))
 def test_gradient_matches_oracle(name, kernel):
     spec = GRAD_SPECS[name]
@@ -297,7 +300,7 @@ def test_wide_zone_full_size_against_one_cell_wedge(n_steps):
     assert _rel(grad, np.repeat(g1 / spec.n_phi, spec.n_phi, axis=1)) < GRAD_TOL
 
 
-@pytest.mark.parametrize("kernel", ["split", "tile4"])
+@pytest.mark.parametrize("kernel", ["split", "tile4", "etile16"])
 def test_wide_zone_full_size_phi_varying_against_oracle(kernel):
     """The full 300x320x160 wide-zone grid with its seeded, phi-varying
     density (filter + projection, 3 wavelengths), 300 steps with the sheet
