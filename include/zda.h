@@ -232,7 +232,8 @@ long long zda_zone_launch_count(const zda_zone *zone);
  * tiles of tile_phi in {4, 8, 16} phi rows x 32 z-cells staged by TMA, each
  * thread block streaming over one of i_ranges radius ranges (0 = about 21
  * radii each).  Default at zone creation: variant 4 with 16 rows where it
- * applies and the zone has at least 16 phi cells, else variant 0; selecting
+ * applies and the zone gives at least four waves of its thread blocks (2 per
+ * SM) in radius ranges of about 21 radii, else variant 0; selecting
  * the stretched r-PML (form 1) on a zone that still has the default falls
  * back to variant 0, while an explicit variant 1, 3 or 4 refuses it.  All
  * compute the same scheme; results agree to FP32 rounding.  Variants 1, 3
