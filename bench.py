@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="surrogate workload: samples per forward")
     ap.add_argument("--kernel", default="default",
                     choices=["default", "split", "split1", "fused2", "fused4", "tile4", "tile8", "tile16", "etile8",
-                             "etile16", "etile32", "tuned"],
+                             "etile16", "etile32", "htile8", "htile16", "htile32", "tuned"],
                     help="time-step kernel (default: the library's choice for the zone; tuned: the tile tuner's "
                          "pick)")
     return ap.parse_args()
@@ -303,7 +303,8 @@ def run_ours(a):
     zone = Zone(spec, device=local)
     kern = {"split": (0, 16, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0),
             "tile4": (3, 4, 0), "tile8": (3, 8, 0), "tile16": (3, 16, 0),
-            "etile8": (4, 8, 0), "etile16": (4, 16, 0), "etile32": (4, 32, 0)}.get(a.kernel)
+            "etile8": (4, 8, 0), "etile16": (4, 16, 0), "etile32": (4, 32, 0),
+            "htile8": (5, 8, 0), "htile16": (5, 16, 0), "htile32": (5, 32, 0)}.get(a.kernel)
     if kern is not None:
         zone.set_kernel(*kern)
     elif a.kernel == "tuned":
@@ -380,7 +381,7 @@ def run_ours(a):
     # the library's sampled launches of one time step (see Zone.timing)
     avg = [m / max(n_timed, 1) for m in ms3]
     rpml = zone.radial_pml()
-    pair = variant in (0, 4) and spec.n_z % 2 == 0 and spec.pml_z % 2 == 0
+    pair = variant in (0, 4, 5) and spec.n_z % 2 == 0 and spec.pml_z % 2 == 0
     if variant == 1:
         kernels = [("k_stream_step", algorithmic_bytes_stream(spec), avg[0]),
                    ("k_dft_step", algorithmic_bytes_dft(spec, nq), avg[2])]
@@ -390,8 +391,8 @@ def run_ours(a):
     elif pair:
         # the DFT history is written by the E update; the flush (every 32 steps)
         # is timed on its own below
-        kernels = [("k_update_h_pair", algorithmic_bytes_h(spec, rpml), avg[0]),
-                   ("k_tile_e" if variant == 4 else "k_update_e_pair",
+        kernels = [("k_tile_h" if variant == 5 else "k_update_h_pair", algorithmic_bytes_h(spec, rpml), avg[0]),
+                   ("k_tile_e" if variant in (4, 5) else "k_update_e_pair",
                     algorithmic_bytes_e(spec, nq, with_dft=False, history=True, rpml=rpml), avg[1])]
     else:
         kernels = [("k_update_h", algorithmic_bytes_h(spec, rpml), avg[0]),
@@ -423,7 +424,8 @@ def run_ours(a):
             "step_kernel": {"variant": {0: "split, two z-cells per thread", 1: "fused, streaming along r",
                                         2: "split, one z-cell per thread",
                                         3: "fused, TMA-staged tiles streaming along r",
-                                        4: "split, E half on TMA-staged tiles streaming along r"}[variant],
+                                        4: "split, E half on TMA-staged tiles streaming along r",
+                                        5: "split, both halves on TMA-staged tiles streaming along r"}[variant],
                             "tile_phi": tile_phi,
                             "i_ranges": i_ranges, "radial_pml": zone.radial_pml()},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,

@@ -7,8 +7,9 @@ zone's shape (n_r, n_phi, n_z, PML widths) and r-PML form, so zones of the
 same shape in a lens (and later runs) reuse it without timing again.
 Candidates the zone refuses (the fused steps with the stretched r-PML) are
 skipped.  The candidates are the split step's thread-block shapes (4 to 32
-phi rows), the one-cell split step, the streaming fused step and the
-TMA-tiled fused step's tile rows and radius ranges.
+phi rows), the one-cell split step, the streaming fused step, the
+TMA-tiled fused step's tile rows and radius ranges, and the split step with
+its E half or both halves on TMA-staged tiles.
 """
 import json
 import os
@@ -25,7 +26,8 @@ def candidates(spec):
     """(variant, tile_phi, i_ranges) choices for the zone: the split step's
     thread-block shape (phi rows x z-pairs, 256 threads), the one-cell split
     step, the streaming fused step, the TMA-tiled fused step's tile rows
-    and radius ranges, and the split step with its E half on TMA tiles."""
+    and radius ranges, and the split step with its E half (or both halves)
+    on TMA tiles."""
     cands = [(2, 2, 0)]
     pair = spec.n_z % 2 == 0 and spec.pml_z % 2 == 0 and spec.n_fold > 0
     if pair:
@@ -40,7 +42,7 @@ def candidates(spec):
                 cands += [(3, tj, 0), (3, tj, max(1, spec.n_r // 30))]
         for tj in (8, 16, 32):
             if tj <= 2 * max(spec.n_phi, 2):
-                cands.append((4, tj, 0))
+                cands += [(4, tj, 0), (5, tj, 0)]
     return sorted(set(cands))
 
 

@@ -76,15 +76,19 @@ struct zda_zone {
     // time-step kernel: 0 = split H/E launches (default), 1 = fused single launch
     // streaming along r (bulk-copy ring), 3 = fused single launch on TMA-staged
     // tiles (tile_phi rows x 32 z-cells, streaming over i_ranges radius ranges), 4 = split
-    // step with the E half on TMA-staged tiles (tile_phi rows, i_ranges radius ranges)
+    // step with the E half on TMA-staged tiles (tile_phi rows, i_ranges radius ranges), 5 = split
+    // step with both halves on those tiles
     int variant = 0, tile_phi = 2, i_ranges = 0;
     zda::TileMaps tmaps[2];         // tensor maps of the two field buffers (variant 3)
     const char *tmaps_ws = nullptr; // the workspace and tile shape they were encoded for
     int tmaps_tj = 0;
     bool kernel_default = true;     // the creation-time choice, not one made by zda_zone_set_kernel
-    zda::TileEMaps emaps;           // tensor maps of the field buffer (variant 4)
+    zda::TileEMaps emaps;           // tensor maps of the field buffer (variants 4, 5)
     const char *emaps_ws = nullptr;
     int emaps_tj = 0;
+    zda::TileHMaps hmaps;           // tensor maps of the field buffer for the H half (variant 5)
+    const char *hmaps_ws = nullptr;
+    int hmaps_tj = 0;
     int wait_limit = 1 << 22, inject_timeout = 0;   // bounded mbarrier waits of the fused step
     bool pair_kernels = true;       // split step: two z-cells per thread where the grid allows
     int rpml = 0;                   // r-PML form (zda_zone_set_radial_pml)
@@ -538,7 +542,7 @@ static zda_status derive(zda_zone &z)
         z.di_max = z.dj_max = 0;
     }
     if (z.variant == 1 && (d.n_z > zda::fused_max_nz() || bor)) z.variant = 0;
-    if ((z.variant == 3 || z.variant == 4) && (bor || d.n_z % 2 || d.pml_z % 2)) z.variant = 0;
+    if ((z.variant == 3 || z.variant == 4 || z.variant == 5) && (bor || d.n_z % 2 || d.pml_z % 2)) z.variant = 0;
     compute_layout(z);
     z.tables_dirty = true;
     z.have_forward = false;
@@ -600,7 +604,7 @@ static zda::StepParams step_params(zda_zone &z)
     p.des_nk = z.nk;
     // default block: 16 phi rows, or 4 for zones of at most 16 phi cells (longer z-runs per block;
     // measured 5-25 % faster on the 8-16-cell zones of the paper's lenses)
-    p.pair_rows = (z.variant != 4 && zda::pair_rows_ok(z.tile_phi)) ? z.tile_phi : (d.n_phi <= 16 ? 4 : 16);
+    p.pair_rows = (z.variant < 4 && zda::pair_rows_ok(z.tile_phi)) ? z.tile_phi : (d.n_phi <= 16 ? 4 : 16);
     p.e_blocks = (z.variant == 0 && z.i_ranges == 3) ? 3 : 2;
     return p;
 }
@@ -807,8 +811,24 @@ static int tile_e_rchunks(const zda_zone &z)
     return zda::tile_e_auto_rchunks(z.tile_phi, z.d.n_r, z.d.n_phi, z.d.n_z, sms);
 }
 
+// tensor maps of the field buffer for the H tile kernel (variant 5)
+static zda_status tile_h_maps(zda_zone &z)
+{
+    if (z.hmaps_ws == z.ws && z.hmaps_tj == z.tile_phi) return ZDA_OK;
+    const zda_zone_desc &d = z.d;
+    const size_t ncell = (size_t)d.n_r * d.n_phi * d.n_z;
+    float2 *F = P<float2>(z, z.L.fields);
+    float2 *E[3] = {F, F + ncell, F + 2 * ncell}, *H[3] = {F + 3 * ncell, F + 4 * ncell, F + 5 * ncell};
+    const char *why = "";
+    if (!zda::encode_tile_h_maps(&z.hmaps, E, H, d.n_r, d.n_phi, d.n_z, z.tile_phi, &why))
+        return fail(ZDA_ERR_CUDA, std::string("H tile kernel: ") + why);
+    z.hmaps_ws = z.ws;
+    z.hmaps_tj = z.tile_phi;
+    return ZDA_OK;
+}
+
 // kernels with bounded device-side waits report a timeout through the error word
-static bool uses_waits(const zda_zone &z) { return z.variant == 1 || z.variant == 3 || z.variant == 4; }
+static bool uses_waits(const zda_zone &z) { return z.variant == 1 || z.variant >= 3; }
 
 static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
 {
@@ -893,7 +913,7 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
     const bool dft = pair && (p.des || p.mon);
     p.dft_ne = zda::dft_entries(p);
     if (!pair) p.dft_hist = nullptr;
-    const bool etile = pair && z.variant == 4;
+    const bool etile = pair && (z.variant == 4 || z.variant == 5), htile = pair && z.variant == 5;
     zda::TileParams etp{};
     int enrc = 1;
     if (etile) {
@@ -901,8 +921,15 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
         if (st) return st;
         const size_t ncell = (size_t)z.d.n_r * z.d.n_phi * z.d.n_z;
         float2 *F = P<float2>(z, z.L.fields);
+        if (htile) {
+            st = tile_h_maps(z);
+            if (st) return st;
+        }
         etp.p = p;
-        for (int c = 0; c < 3; ++c) etp.oE[c] = F + c * ncell;
+        for (int c = 0; c < 3; ++c) {
+            etp.oE[c] = F + c * ncell;
+            etp.oH[c] = F + (3 + c) * ncell;
+        }
         etp.err = P<int>(z, z.L.status) + 1;
         etp.wait_limit = z.wait_limit;
         enrc = tile_e_rchunks(z);
@@ -921,8 +948,14 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
             CUDA_TRY(cudaMemcpyAsync(z.ws + z.L.fields2, z.ws + z.L.fields,
                                      6 * (size_t)z.d.n_r * z.d.n_phi * z.d.n_z * sizeof(float2),
                                      cudaMemcpyDeviceToDevice, s));
-        if (pair) zda::launch_update_h_pair(p, s);
-        else zda::launch_update_h(p, s);
+        if (htile) {
+            cudaError_t e = zda::launch_tile_h(z.hmaps, etp, z.tile_phi, enrc, s);
+            if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("H tile kernel: ") + cudaGetErrorString(e));
+        } else if (pair) {
+            zda::launch_update_h_pair(p, s);
+        } else {
+            zda::launch_update_h(p, s);
+        }
         if (timed) CUDA_TRY(cudaEventRecord(z.ev[4 * slot + 1], s));
         if (etile) {
             cudaError_t e = zda::launch_tile_e(z.emaps, etp, n, z.tile_phi, enrc, s);
@@ -1318,15 +1351,15 @@ long long zda_zone_launch_count(const zda_zone *z) { return z ? z->launches : -1
 
 zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ranges)
 {
-    if (!z || variant < 0 || variant > 4 || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
+    if (!z || variant < 0 || variant > 5 || i_ranges < 0) return fail(ZDA_ERR_ARG, "bad kernel choice");
     z->kernel_default = false;
-    if (variant == 4) {                      // split step, E half on TMA-staged tiles streaming along r
+    if (variant == 4 || variant == 5) {      // split step, E half (4) or both halves (5) on TMA-staged tiles
         if (z->d.n_fold == 0) return fail(ZDA_ERR_ARG, "the axis zone (continuous axisymmetry) uses the split step");
         if (z->rpml) return fail(ZDA_ERR_ARG, "the E tile kernel implements the real-radius r-PML only");
         if (z->d.n_z % 2 || z->d.pml_z % 2) return fail(ZDA_ERR_ARG, "the E tile kernel needs even n_z and pml_z");
         if (!zda::tile_e_shape_ok(tile_phi)) return fail(ZDA_ERR_ARG, "E tile kernel: tile_phi must be 8, 16 or 32");
         z->pair_kernels = true;
-        z->variant = 4;
+        z->variant = variant;
         z->tile_phi = tile_phi;
         z->i_ranges = i_ranges;
         z->have_forward = false;
@@ -1370,7 +1403,7 @@ zda_status zda_zone_set_kernel(zda_zone *z, int variant, int tile_phi, int i_ran
 zda_status zda_zone_set_radial_pml(zda_zone *z, int form)
 {
     if (!z || (form != 0 && form != 1)) return fail(ZDA_ERR_ARG, "r-PML form must be 0 or 1");
-    if (form == 1 && (z->variant == 1 || z->variant == 3 || z->variant == 4)) {
+    if (form == 1 && (z->variant == 1 || z->variant >= 3)) {
         if (!z->kernel_default)
             return fail(ZDA_ERR_ARG, "the fused and tiled steps implement the real-radius r-PML only");
         z->variant = 0;                      // the default tiled step gives way to the split step
@@ -1442,7 +1475,7 @@ zda_status zda_zone_get_kernel(const zda_zone *z, int *variant, int *tile_phi, i
     *tile_phi = z->tile_phi;
     *i_ranges = z->variant == 1   ? auto_i_ranges(*z)
                 : z->variant == 3 ? tile_rchunks(*z)
-                : z->variant == 4 ? tile_e_rchunks(*z)
+                : z->variant >= 4 ? tile_e_rchunks(*z)
                                   : z->i_ranges;
     return ZDA_OK;
 }

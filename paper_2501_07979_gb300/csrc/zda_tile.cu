@@ -699,6 +699,219 @@ __global__ void __launch_bounds__(SE<TJ, NS>::NT, MINB)
         for (int r = max(ib - 1, last_issued - G::NSLOT + 1); r <= last_issued; ++r) wait_group(r);
 }
 
+// ---------------------------------------------------------------- H update on TMA-staged tiles
+// E^n around an H pair (kh, kh+1) at radius r: the pair's own values and
+// E_phi / E_r one cell above in z ([2]), the row above in phi (J) and the
+// radius above (I).
+struct EAround {
+    float2 EP[3], ER[3];                    // index u = cell u, [2] = cell kh + 2
+    float2 EZ[2], EZJ[2], ERJ[2], EZI[2], EPI[2];
+};
+
+// One H item: the z-pair (kh, kh+1) of phi row jh, streamed along r.
+// update() applies Eq. 3 (H^{n+1/2} from the E values around the pair) with
+// the H-side CPML in the same single coefficient form as the E items, and
+// stores H and the auxiliaries in place.
+struct HItem {
+    int jh, kh, kzh;
+    bool valid;
+    float bzh[2], czh[2];
+
+    __device__ __forceinline__ void init(const StepParams &p, int jh_, int kh_)
+    {
+        jh = jh_;
+        kh = kh_;
+        valid = jh < p.nphi && kh < p.nz;
+        kzh = (kh < p.pz) ? kh : ((kh >= p.nz - p.pz) ? kh - (p.nz - 2 * p.pz) : -1);
+        bzh[0] = bzh[1] = czh[0] = czh[1] = 0.f;
+        if (valid && kzh >= 0) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) { bzh[u] = __ldg(p.t.bz_h + kh + u); czh[u] = __ldg(p.t.cz_h + kh + u) * p.inv_dz; }
+        }
+    }
+
+    // per-radius values of an H radius: (1/r_r, 1/r_{r+1/2}, CPML b, c at r_{r+1/2})
+    __device__ __forceinline__ static float4 tab_at(const StepParams &p, int r)
+    {
+        return make_float4(__ldg(p.t.inv_r_n + r), __ldg(p.t.inv_r_h + r), __ldg(p.t.br_h + r), __ldg(p.t.cr_h + r));
+    }
+
+    __device__ __forceinline__ void update(const StepParams &p, int r, const float4 &tab, const EAround &e, C2 hr, C2 hp,
+                                           C2 hz, float2 *const *oH) const
+    {
+        const float2 zero = make_float2(0.f, 0.f);
+        const int nr = p.nr, nphi = p.nphi, nz = p.nz;
+        const float dt = p.dt, k_z = dt * p.inv_dz, k_r = dt * p.inv_dr;
+        const float irn = tab.x, irh = tab.y, brh = tab.z, crh = tab.w * p.inv_dr;
+        const int ir = (r < p.pr_in) ? r : ((r >= nr - p.pr_out) ? r - (nr - p.pr_in - p.pr_out) : -1);
+        const int zx = (r * nphi + jh) * (2 * p.pz) + (kzh >= 0 ? kzh : 0);
+        const int rx = ((ir >= 0 ? ir : 0) * nphi + jh) * nz + kh;
+        C2 ps_r = C2{zero, zero}, ps_p = C2{zero, zero}, ps_pr = C2{zero, zero}, ps_zr = C2{zero, zero};
+        if (kzh >= 0) { ps_r = ldg4(p.psi.hr_z + zx); ps_p = ldg4(p.psi.hp_z + zx); }
+        if (ir >= 0) { ps_pr = ldg4(p.psi.hp_r + rx); ps_zr = ldg4(p.psi.hz_r + rx); }
+        float2 *HR[2] = {&hr.a, &hr.b}, *HP[2] = {&hp.a, &hp.b}, *HZ[2] = {&hz.a, &hz.b};
+        float2 *PR[2] = {&ps_r.a, &ps_r.b}, *PP[2] = {&ps_p.a, &ps_p.b};
+        float2 *PPR[2] = {&ps_pr.a, &ps_pr.b}, *PZR[2] = {&ps_zr.a, &ps_zr.b};
+        const float k_phn = dt * irn * p.inv_dphi, k_m = 0.5f * dt * irh, k_phh = dt * irh * p.inv_dphi;
+        const float c_m = 0.5f * irh * tab.w;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float2 d_ep = f_sub(e.EP[u + 1], e.EP[u]), d_er = f_sub(e.ER[u + 1], e.ER[u]);
+            const float2 d_ezi = f_sub(e.EZI[u], e.EZ[u]), d_epi = f_sub(e.EPI[u], e.EP[u]);
+            const float2 s_epi = f_add(e.EPI[u], e.EP[u]);
+            // H_r: -(1/r) dE_z/dphi + dE_phi/dz
+            *HR[u] = f_axpy(-k_phn, f_sub(e.EZJ[u], e.EZ[u]), *HR[u]);
+            *HR[u] = f_axpy(k_z, d_ep, *HR[u]);
+            // H_phi: -dE_r/dz + dE_z/dr
+            *HP[u] = f_axpy(-k_z, d_er, *HP[u]);
+            *HP[u] = f_axpy(k_r, d_ezi, *HP[u]);
+            if (kzh >= 0) {
+                *PR[u] = f_axpy(czh[u], d_ep, c_scale(*PR[u], bzh[u]));
+                *PP[u] = f_axpy(czh[u], d_er, c_scale(*PP[u], bzh[u]));
+                *HR[u] = f_axpy(dt, *PR[u], *HR[u]);
+                *HP[u] = f_axpy(-dt, *PP[u], *HP[u]);
+            }
+            // H_z: -(1/r) d(r E_phi)/dr + (1/r) dE_r/dphi
+            *HZ[u] = f_axpy(-k_r, d_epi, *HZ[u]);
+            *HZ[u] = f_axpy(-k_m, s_epi, *HZ[u]);
+            *HZ[u] = f_axpy(k_phh, f_sub(e.ERJ[u], e.ER[u]), *HZ[u]);
+            if (ir >= 0) {
+                *PPR[u] = f_axpy(crh, d_ezi, c_scale(*PPR[u], brh));
+                *PZR[u] = f_axpy(c_m, s_epi, f_axpy(crh, d_epi, c_scale(*PZR[u], brh)));
+                *HP[u] = f_axpy(dt, *PPR[u], *HP[u]);
+                *HZ[u] = f_axpy(-dt, *PZR[u], *HZ[u]);
+            }
+        }
+        const int o = r * (nphi * nz) + jh * nz + kh;
+        st4(oH[0] + o, hr);
+        st4(oH[1] + o, hp);
+        st4(oH[2] + o, hz);
+        if (kzh >= 0) { st4(p.psi.hr_z + zx, ps_r); st4(p.psi.hp_z + zx, ps_p); }
+        if (ir >= 0) { st4(p.psi.hp_r + rx, ps_pr); st4(p.psi.hz_r + rx, ps_zr); }
+    }
+};
+
+// The H half of the split step as a radius-streamed tile kernel (the
+// counterpart of k_tile_e): load group g(r) = {E^n(r) rows j0 .. j0+TJ and
+// z k0 .. k0+33, H^{n-1/2}(r) over the tile's own cells, and for the tile
+// holding phi row n_phi-1 the wrapped E row 0}; iteration r updates H(r)
+// from g(r) and g(r+1) (E at the radius above), in place.  Groups run over
+// r = ib .. ie (the last one, read for its E only, carries no H box).
+template <int TJ, int NS>
+struct SH {
+    static constexpr int KP = TILE_KZ / 2;
+    static constexpr int EZ = TILE_KZ + 2, EJ = TJ + 1;       // E slab: z from k0, rows from j0
+    static constexpr int al(int x) { return (x + 15) & ~15; }
+    static constexpr int ES = al(EJ * EZ), HS = al(TJ * TILE_KZ), RW = al(EZ);
+    static constexpr int E_OFF = 0, H_OFF = 3 * ES, WEH = H_OFF + 3 * HS;
+    static constexpr int GROUP = WEH + 3 * RW;
+    static constexpr int NSLOT = NS;
+    static constexpr int NT = TJ * KP;
+};
+
+template <int TJ, int NS, int MINB>
+__global__ void __launch_bounds__(SH<TJ, NS>::NT, MINB)
+    k_tile_h(const __grid_constant__ TileHMaps m, const TileParams tp, const int i_range)
+{
+    using G = SH<TJ, NS>;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT];
+    __shared__ int abort_s;
+    const uint32_t raw_s = s_addr(smem_raw);
+    const uint32_t base_s = (raw_s + 127u) & ~127u;
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + (base_s - raw_s));
+
+    const StepParams &p = tp.p;
+    const int nr = p.nr, nphi = p.nphi, nz = p.nz;
+    const int nzc = (nz + TILE_KZ - 1) / TILE_KZ;
+    const int k0 = (blockIdx.x % nzc) * TILE_KZ;
+    const int j0 = (blockIdx.x / nzc) * TJ;
+    const int ib = blockIdx.y * i_range, ie = min(nr, ib + i_range);
+    const int tid = threadIdx.x;
+    const int s_hi = nphi - j0;                               // slab row of phi row n_phi (the wrapped row 0)
+    const bool whi = s_hi <= TJ;
+    const int x = 2 * k0;
+
+    auto slot_of = [&](int r) { return (unsigned)(r - ib) % (unsigned)G::NSLOT; };
+    auto parity_of = [&](int r) { return ((unsigned)(r - ib) / (unsigned)G::NSLOT) & 1u; };
+    auto group = [&](int r) { return sm + slot_of(r) * G::GROUP; };
+    auto issue = [&](int r) {
+        const unsigned sl = slot_of(r);
+        const uint32_t g = base_s + (uint32_t)(sl * G::GROUP) * 8u;
+        const uint32_t bar = s_addr(&bar_mem[sl]);
+        const bool with_h = r < ie;
+        uint32_t bytes = 3u * G::EZ * G::EJ * 8u;
+        if (with_h) bytes += 3u * TILE_KZ * TJ * 8u;
+        if (whi) bytes += 3u * G::EZ * 8u;
+        t_mbar_expect_tx(bar, bytes);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            tma3(g + (G::E_OFF + c * G::ES) * 8u, &m.e[c], x, j0, r, bar);
+            if (with_h) tma3(g + (G::H_OFF + c * G::HS) * 8u, &m.ho[c], x, j0, r, bar);
+            if (whi) tma3(g + (G::WEH + c * G::RW) * 8u, &m.ew[c], x, 0, r, bar);
+        }
+    };
+    auto wait_group = [&](int r) { return t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err); };
+
+    if (tid == 0) {
+        for (int s = 0; s < G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
+        abort_s = *(volatile int *)tp.err;                    // an earlier launch gave up waiting: do nothing
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (abort_s) return;
+    // groups g(ib) .. g(ib+NSLOT-1) now (every slot); g(r+NSLOT) after iteration r
+    int last_issued = min(ie, ib + G::NSLOT - 1);
+    bool failed = false;
+    if (tid == 0) {
+        for (int r = ib; r <= last_issued; ++r) issue(r);
+        failed = !wait_group(ib);
+        if (!failed) failed = !wait_group(ib + 1);            // ib + 1 <= ie always
+    }
+    failed = __syncthreads_or(failed);
+
+    const int se = tid / G::KP, pe = tid % G::KP;
+    HItem it;
+    it.init(p, j0 + se, k0 + 2 * pe);
+    const bool jp_wrap = whi && se + 1 == s_hi;               // row above is the wrapped row (Bloch phase)
+    const int e_own = G::E_OFF + se * G::EZ + 2 * pe;
+    const int e_up = jp_wrap ? G::WEH + 2 * pe : G::E_OFF + (se + 1) * G::EZ + 2 * pe;
+    const int up_cs = jp_wrap ? G::RW : G::ES;
+    const int h_own = G::H_OFF + se * TILE_KZ + 2 * pe;
+    float4 tab = make_float4(0.f, 0.f, 0.f, 0.f), ntab = HItem::tab_at(p, ib);
+    for (int r = ib; r < ie && !failed; ++r) {
+        tab = ntab;
+        if (r + 1 < ie) ntab = HItem::tab_at(p, r + 1);       // next radius, one iteration ahead
+        if (it.valid) {
+            const float2 *gq = group(r);                      // E^n(r), H^{n-1/2}(r)
+            const float2 *gn = group(r + 1);                  // E^n(r+1)
+            EAround e;
+            const C2 er = lds4(gq + e_own), ep = lds4(gq + e_own + G::ES), ez = lds4(gq + e_own + 2 * G::ES);
+            C2 ez_jp = lds4(gq + e_up + 2 * up_cs), er_jp = lds4(gq + e_up);
+            if (jp_wrap) { ez_jp = cmul2(p.bloch, ez_jp); er_jp = cmul2(p.bloch, er_jp); }
+            const C2 ez_ip = lds4(gn + e_own + 2 * G::ES), ep_ip = lds4(gn + e_own + G::ES);
+            e.EP[0] = ep.a; e.EP[1] = ep.b; e.EP[2] = gq[e_own + G::ES + 2];
+            e.ER[0] = er.a; e.ER[1] = er.b; e.ER[2] = gq[e_own + 2];
+            e.EZ[0] = ez.a; e.EZ[1] = ez.b;
+            e.EZJ[0] = ez_jp.a; e.EZJ[1] = ez_jp.b;
+            e.ERJ[0] = er_jp.a; e.ERJ[1] = er_jp.b;
+            e.EZI[0] = ez_ip.a; e.EZI[1] = ez_ip.b;
+            e.EPI[0] = ep_ip.a; e.EPI[1] = ep_ip.b;
+            it.update(p, r, tab, e, lds4(gq + h_own), lds4(gq + h_own + G::HS), lds4(gq + h_own + 2 * G::HS), tp.oH);
+        }
+        if (tid == 0 && r + 2 <= ie) failed = !wait_group(r + 2);
+        if (__syncthreads_or(failed)) { failed = true; break; }
+        if (tid == 0 && r + G::NSLOT <= ie) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(r + G::NSLOT);
+            last_issued = r + G::NSLOT;
+        }
+    }
+    if (failed && tid == 0)                                   // copies still in flight
+        for (int r = max(ib, last_issued - G::NSLOT + 1); r <= last_issued; ++r) wait_group(r);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -767,6 +980,28 @@ cudaError_t launch_e_shape(const TileEMaps &m, const TileParams &tp, int n, int 
     const int i_range = (tp.p.nr + nrc - 1) / nrc;
     dim3 g((unsigned)(nzc * njt), (unsigned)((tp.p.nr + i_range - 1) / i_range));
     k_tile_e<TJ, NS, MINB><<<g, G::NT, bytes, s>>>(m, tp, n, i_range);
+    return cudaGetLastError();
+}
+
+template <int TJ, int NS, int MINB>
+cudaError_t launch_h_shape(const TileHMaps &m, const TileParams &tp, int n_rchunks, cudaStream_t s)
+{
+    using G = SH<TJ, NS>;
+    const size_t bytes = (size_t)G::NSLOT * G::GROUP * sizeof(float2) + 128;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static unsigned attr_done = 0;                            // per device (bit), set once
+    if (dev < 32 && !(attr_done & (1u << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_h<TJ, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_done |= 1u << dev;
+    }
+    const int nzc = (tp.p.nz + TILE_KZ - 1) / TILE_KZ, njt = (tp.p.nphi + TJ - 1) / TJ;
+    const int nrc = std::max(1, std::min(n_rchunks, tp.p.nr));
+    const int i_range = (tp.p.nr + nrc - 1) / nrc;
+    dim3 g((unsigned)(nzc * njt), (unsigned)((tp.p.nr + i_range - 1) / i_range));
+    k_tile_h<TJ, NS, MINB><<<g, G::NT, bytes, s>>>(m, tp, i_range);
     return cudaGetLastError();
 }
 
@@ -884,6 +1119,42 @@ bool encode_tile_e_maps(TileEMaps *m, float2 *const E[3], float2 *const H[3], in
         }
     }
     return true;
+}
+
+bool encode_tile_h_maps(TileHMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
+                        const char **why)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        *why = "the driver's cuTensorMapEncodeTiled is not available";
+        return false;
+    }
+    const cuuint64_t dims[3] = {2ull * (cuuint64_t)nz, (cuuint64_t)nphi, (cuuint64_t)nr};
+    const cuuint64_t strides[2] = {(cuuint64_t)nz * 8ull, (cuuint64_t)nphi * (cuuint64_t)nz * 8ull};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const cuuint32_t be[3] = {2u * (TILE_KZ + 2), (cuuint32_t)(tj + 1), 1u};
+    const cuuint32_t bew[3] = {2u * (TILE_KZ + 2), 1u, 1u};
+    const cuuint32_t bho[3] = {2u * TILE_KZ, (cuuint32_t)tj, 1u};
+    auto one = [&](CUtensorMap *t, void *base, const cuuint32_t *box) {
+        return enc(t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    for (int c = 0; c < 3; ++c) {
+        if (!one(&m->e[c], E[c], be) || !one(&m->ew[c], E[c], bew) || !one(&m->ho[c], H[c], bho)) {
+            *why = "cuTensorMapEncodeTiled refused the field layout";
+            return false;
+        }
+    }
+    return true;
+}
+
+cudaError_t launch_tile_h(const TileHMaps &m, const TileParams &tp, int tj, int n_rchunks, cudaStream_t s)
+{
+    if (tj == 8) return launch_h_shape<8, 6, 2>(m, tp, n_rchunks, s);
+    if (tj == 16) return launch_h_shape<16, 4, 2>(m, tp, n_rchunks, s);
+    if (tj == 32) return launch_h_shape<32, 4, 1>(m, tp, n_rchunks, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile_e(const TileEMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s)

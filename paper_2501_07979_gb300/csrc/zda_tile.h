@@ -19,6 +19,12 @@ struct TileEMaps {
     CUtensorMap eo[3], h[3], hw[3];
 };
 
+// Tensor maps for the H tile kernel (split step, H half): the E slab (one row
+// and two z-cells more above), the wrapped E row, the tile's own H box.
+struct TileHMaps {
+    CUtensorMap e[3], ew[3], ho[3];
+};
+
 struct TileParams {
     StepParams p;                 // tables, E-side CPML (updated in place), density, source, DFT history
     float2 *oE[3], *oH[3];        // destination buffer: E^{n+1}, H^{n+1/2}
@@ -48,5 +54,10 @@ int tile_e_auto_rchunks(int tj, int nr, int nphi, int nz, int sms);
 bool encode_tile_e_maps(TileEMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
                         const char **why);
 cudaError_t launch_tile_e(const TileEMaps &m, const TileParams &tp, int n, int tj, int n_rchunks, cudaStream_t s);
+// H half of the split step on the same tiles (shapes and radius ranges as the E tile kernel),
+// updating H and the H-side CPML auxiliaries in place; TileParams::oH = the field buffer's H
+bool encode_tile_h_maps(TileHMaps *m, float2 *const E[3], float2 *const H[3], int nr, int nphi, int nz, int tj,
+                        const char **why);
+cudaError_t launch_tile_h(const TileHMaps &m, const TileParams &tp, int tj, int n_rchunks, cudaStream_t s);
 
 }  // namespace zda

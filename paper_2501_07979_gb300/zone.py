@@ -204,7 +204,7 @@ class Zone:
         rows per block), 1 fused streaming (tile_phi 2 or 4), 2 split one cell
         per thread, 3 fused TMA tiles (tile_phi 4, 8 or 16; i_ranges radius
         ranges), 4 split with the E half on TMA tiles (tile_phi 8, 16 or 32;
-        i_ranges radius ranges)."""
+        i_ranges radius ranges), 5 the same with both halves on TMA tiles."""
         check(_lib.lib().zda_zone_set_kernel(self.handle, int(variant), int(tile_phi), int(i_ranges)))
 
     def set_radial_pml(self, form):

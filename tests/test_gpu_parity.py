@@ -29,14 +29,15 @@ KERNELS = {"split": (0, 2, 0), "split_r4": (0, 4, 0), "split_r16": (0, 16, 0), "
            "fused2": (1, 2, 0), "fused4": (1, 4, 0),
            "fused2_ir3": (1, 2, 3), "tile8": (3, 8, 0), "tile4": (3, 4, 0), "tile16": (3, 16, 0),
            "tile8_r5": (3, 8, 5), "etile8": (4, 8, 0), "etile16": (4, 16, 0), "etile32": (4, 32, 0),
-           "etile16_r7": (4, 16, 7)}
+           "etile16_r7": (4, 16, 7), "htile8": (5, 8, 0), "htile16": (5, 16, 0), "htile32": (5, 32, 0),
+           "htile16_r7": (5, 16, 7)}
 
 
 def _zone(spec, kernel=None):
     from paper_2501_07979_gb300 import Zone
     if kernel is not None and KERNELS[kernel][0] == 1 and (spec.n_z % 2 or spec.n_fold == 0):
         pytest.skip("the fused step needs an even n_z and an annular zone")
-    if kernel is not None and KERNELS[kernel][0] in (3, 4) and (spec.n_z % 2 or spec.pml_z % 2 or spec.n_fold == 0):
+    if kernel is not None and KERNELS[kernel][0] in (3, 4, 5) and (spec.n_z % 2 or spec.pml_z % 2 or spec.n_fold == 0):
         pytest.skip("the tile kernels need even n_z and pml_z and an annular zone")
     z = Zone(spec, device=0)
     if kernel is not None:
@@ -158,7 +159,7 @@ def test_forward_uniform_density(value):
 
 
 @pytest.mark.parametrize("kernel", ["fused2", "fused4", "split1", "tile4", "tile8", "tile16", "etile8", "etile16",
-                                    "etile32"])
+                                    "etile32", "htile8", "htile16", "htile32"])
 def test_fused_step_equals_split_step(kernel):
     """The fused single-launch step and the split H/E launches compute the
     same scheme: fields and DFTs agree to FP32 rounding on the wide-zone grid
@@ -208,7 +209,7 @@ GRAD_SPECS = {
 
 
 @pytest.mark.parametrize("kernel", ["split", "split1", "fused2", "fused4", "tile8", "tile4", "tile8_r5", "etile16",
-                                    "etile8", "etile16_r7"])
+                                    "etile8", "etile16_r7", "htile16", "htile8", "htile16_r7"])
 @pytest.mark.parametrize("name", list(GRAD_SPECS))
 def test_gradient_matches_oracle(name, kernel):
     spec = GRAD_SPECS[name]
@@ -300,7 +301,7 @@ def test_wide_zone_full_size_against_one_cell_wedge(n_steps):
     assert _rel(grad, np.repeat(g1 / spec.n_phi, spec.n_phi, axis=1)) < GRAD_TOL
 
 
-@pytest.mark.parametrize("kernel", ["split", "tile4", "etile16"])
+@pytest.mark.parametrize("kernel", ["split", "tile4", "etile16", "htile16"])
 def test_wide_zone_full_size_phi_varying_against_oracle(kernel):
     """The full 300x320x160 wide-zone grid with its seeded, phi-varying
     density (filter + projection, 3 wavelengths), 300 steps with the sheet
