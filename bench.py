@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--radial-pml", type=int, default=0, choices=[0, 1],
                     help="r-PML form: 0 real-radius CPML (default), 1 stretched coordinates")
     ap.add_argument("--batch", type=int, default=256, help="surrogate workload: samples per forward")
+    ap.add_argument("--tile-ranges", type=int, default=0,
+                    help="radius ranges of the tile kernels chosen by --kernel (0: the library's rule)")
     ap.add_argument("--kernel", default="default",
                     choices=["default", "split", "split1", "fused2", "fused4", "tile4", "tile8", "tile16", "etile8",
                              "etile16", "etile32", "htile8", "htile16", "htile32", "tuned"],
@@ -70,6 +72,17 @@ def parse():
 
 
 WORKLOAD = "zone"
+
+
+def kernel_choice(a):
+    """(variant, tile_phi, i_ranges) of --kernel, or None for the library's default / the tuner."""
+    k = {"split": (0, 16, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0),
+         "tile4": (3, 4, 0), "tile8": (3, 8, 0), "tile16": (3, 16, 0),
+         "etile8": (4, 8, 0), "etile16": (4, 16, 0), "etile32": (4, 32, 0),
+         "htile8": (5, 8, 0), "htile16": (5, 16, 0), "htile32": (5, 32, 0)}.get(a.kernel)
+    if k is not None and k[0] >= 3 and a.tile_ranges > 0:
+        k = (k[0], k[1], a.tile_ranges)
+    return k
 
 
 def workload(n_steps):
@@ -301,10 +314,7 @@ def run_ours(a):
 
     spec = workload(a.time_steps)
     zone = Zone(spec, device=local)
-    kern = {"split": (0, 16, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0),
-            "tile4": (3, 4, 0), "tile8": (3, 8, 0), "tile16": (3, 16, 0),
-            "etile8": (4, 8, 0), "etile16": (4, 16, 0), "etile32": (4, 32, 0),
-            "htile8": (5, 8, 0), "htile16": (5, 16, 0), "htile32": (5, 32, 0)}.get(a.kernel)
+    kern = kernel_choice(a)
     if kern is not None:
         zone.set_kernel(*kern)
     elif a.kernel == "tuned":
@@ -635,6 +645,14 @@ def run_lens(a):
     owner = assign_zones(specs, world)
     mine = [z for z in range(len(specs)) if owner[z] == rank]
     zones = [Zone(specs[z], device=local) for z in mine]
+    kern = kernel_choice(a)
+    if kern is not None:                           # every zone that takes it (the axis zone keeps the split step)
+        from paper_2501_07979_gb300._lib import ZdaError
+        for zn in zones:
+            try:
+                zn.set_kernel(*kern)
+            except ZdaError:
+                pass
     lens = Lens(zones, use_graph=bool(a.lens_graph))
     rhos = [torch.tensor(rho_for(specs[z], 1000 + z), dtype=torch.float32, device="cuda:%d" % local) for z in mine]
     stream = torch.cuda.current_stream()
@@ -714,6 +732,7 @@ def run_lens(a):
                        "steps_per_run": [s.n_steps for s in specs], "graph": bool(a.lens_graph),
                        "zones_per_rank": [sum(1 for o in owner if o == r) for r in range(world)],
                        "first_iteration_s": first_s,
+                       "zone_kernels": sorted({"%d,%d,%d" % z.get_kernel() for z in zones}),
                        "l2": "no flush: the zones' field state (%.1f GB) exceeds the 129 MB L2" % (cells * 48 / 1e9)},
             "e2e": {"value": updates / float(te_t.item()) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": px, "d2h_bytes_per_step": px + 16 * lens.n_freq},
