@@ -378,6 +378,52 @@ zda_status zda_lens_focal_plane(zda_lens *lens, const double *pts_dev, int n_pts
 zda_status zda_lens_field_points(zda_lens *lens, const double *pts_dev, int n_pts, int n_phi_samples,
                                  double *field_dev, void *stream);
 
+/* Focal-spot evaluation after zda_lens_forward (section "Centimeter-scale
+ * metalens at long-wave infrared": the PSF and its full width at half
+ * maximum; the absolute focusing efficiency FE = the power inside a disc of
+ * radius 3 FWHM around the focus / the incident power on the lens aperture;
+ * the relative efficiency = the same / the power transmitted through the
+ * lens; Eq. 9's Strehl ratio SR = I(0) lambda^2 F^2 / (P_trans A), A = pi
+ * lens_radius^2).  All on the device: the PSF line I(x) = (n_top/2)
+ * (abs(E_x)^2 + abs(E_y)^2) at n_line >= 2 points x_i = i x_max /
+ * (n_line - 1) on the focal plane's x axis; the FWHM from its first sample
+ * below half of I(0) (linear interpolation with the sample before; NaN if
+ * none); per wavelength a disc of n_rad radii (k + 1/2) 3 FWHM / n_rad x
+ * n_ang angles, its power by the midpoint rule in r and the mean over the
+ * angles.  Fields from the lens-field transform of zda_lens_focal_plane with
+ * n_phi_samples (>= 8) azimuthal samples; P_trans as there.
+ * incident_host: n_lambda incident plane-wave intensities (n/2) abs(E)^2
+ * (zda_zone_incident_intensity).  out_host (n_lambda x 8 doubles): per
+ * wavelength FWHM, I(0), FE, relative FE, transmittance P_trans / P_inc,
+ * SR, disc power, P_trans.  line_dev (optional, n_lambda x n_line doubles,
+ * device) receives the PSF line.  At most 8 wavelengths; device scratch
+ * comes from cudaMallocAsync on `stream`, which the call synchronises. */
+zda_status zda_lens_evaluate(zda_lens *lens, double lens_radius, double focal, const double *incident_host,
+                             double n_top, int n_line, double x_max, int n_rad, int n_ang, int n_phi_samples,
+                             double *out_host, double *line_dev, void *stream);
+
+/* Incident plane-wave intensity of a reference run: after zda_forward of a
+ * zone whose layers and design are all the substrate (no interface, no
+ * lens), the phi-mean u of the monitor's E_r phasor over the radii between
+ * the r-PMLs, each row's Bloch phase e^{i m phi_j} removed, is half the
+ * plane-wave amplitude; out_host (n_lambda doubles) = (n_sub/2) abs(2 u)^2,
+ * n_sub = sqrt of the permittivity of the layer at k = 0.  Synchronises
+ * `stream`. */
+zda_status zda_zone_incident_intensity(zda_zone *zone, double *out_host, void *stream);
+
+/* Intensity (n_top/2)(abs(E_x)^2 + abs(E_y)^2) of field samples in the layout
+ * of zda_lens_focal_plane / zda_lens_field_points (E_x of every wavelength
+ * and point, then E_y; complex doubles): out_dev[l n_pts + p] (device). */
+zda_status zda_field_intensity(const double *field_dev, int n_lambda, int n_pts, double n_top, double *out_dev,
+                               void *stream);
+
+/* Encircled power of radially symmetric spots: for each of n_prof profiles
+ * I_dev[q n + k] sampled at the increasing radii radii_dev[k] (k < n),
+ * out_dev[q n + k] = the trapezoid-rule integral of I(r) 2 pi r from
+ * radii[0] to radii[k] (device arrays). */
+zda_status zda_encircled_power(const double *radii_dev, const double *I_dev, int n_prof, int n, double *out_dev,
+                               void *stream);
+
 /* Estimate of what the lens-field transforms above neglect for one zone
  * (host only, no device work).  They keep the azimuthal orders +-1 of the
  * zone's near field; the wedge's other orders m + j n (j != 0) reach a point

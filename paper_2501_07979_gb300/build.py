@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
-SOURCES = ["zda_kernels.cu", "zda_pair.cu", "zda_step.cu", "zda_tile.cu", "zda_api.cu", "zda_noalloc.cu", "zda_nn.cu", "zda_nn_conv.cu"]
+SOURCES = ["zda_kernels.cu", "zda_pair.cu", "zda_step.cu", "zda_tile.cu", "zda_api.cu", "zda_noalloc.cu", "zda_nn.cu", "zda_nn_conv.cu", "zda_eval.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -158,6 +158,22 @@ void launch_field_energy(const StepParams &p, const Fields &cur, const Fields &p
 void launch_fill_status_check(const float *x, size_t n, int *status, cudaStream_t s);
 void launch_lens_sum(const double2 *const *S, int nzones, int nq, double2 *out, int *status, cudaStream_t s);
 // cross != 0 (n_fold 1 or 2): the transmitted intensity keeps the +-1 cross term
+// focal-spot evaluation (zda_eval.cu); n_lambda <= ZDA_EVAL_MAX_LAMBDA
+#define ZDA_EVAL_MAX_LAMBDA 8
+struct EvalScalars {
+    double incident[ZDA_EVAL_MAX_LAMBDA], p_trans[ZDA_EVAL_MAX_LAMBDA], lambda[ZDA_EVAL_MAX_LAMBDA];
+    double area, focal, n_top;
+};
+void launch_eval_line_points(double *pts, int n_line, double x_max, cudaStream_t s);
+void launch_eval_fwhm(const double2 *field, int nl, int n_line, double x_max, double n_top, double *line, double *fw,
+                      double *i0, cudaStream_t s);
+void launch_eval_disc_points(const double *fw, int nl, int n_rad, int n_ang, double *pts, cudaStream_t s);
+void launch_eval_finish(const double2 *field, int nl, int n_rad, int n_ang, const double *fw, const double *i0,
+                        const EvalScalars &sc, double *out, cudaStream_t s);
+void launch_incident_intensity(const float2 *mon, int nl, int nr, int nphi, int i0, int i1, double dphi, double n_sub,
+                               double *out, cudaStream_t s);
+void launch_field_intensity(const double2 *field, int nl, int n, double n_top, double *out, cudaStream_t s);
+void launch_encircled_power(const double *r, const double *I, int n_prof, int n, double *out, cudaStream_t s);
 void launch_phi_means(const float2 *mon, const double2 *emph_n, const double2 *emph_h, int nq, int nr, int nphi,
                       int cross, double2 *umean, double *pt_row, cudaStream_t s);
 void launch_focal_plane(const double2 *umean, const double *rr, const double *wr, const double *rp, const double *wp,

@@ -1,19 +1,20 @@
-"""Focal-spot analysis helpers on CPU: encircled power of closed-form
-spots, FWHM of a Gaussian, and evaluate_lens (PSF, FWHM, focusing
-efficiencies, Strehl ratio of Eq. 9) on an ideal Airy spot."""
+"""The oracle's focal-spot evaluation pinned on CPU: encircled power of
+closed-form spots, FWHM of a Gaussian, and the evaluation (PSF, FWHM,
+focusing efficiencies, Strehl ratio of Eq. 9) of an ideal Airy spot.  The
+library's evaluation (zda_lens_evaluate) is held to this oracle on the GPU."""
 import math
 
 import numpy as np
 
-from paper_2501_07979_gb300.evaluate import encircled_power, fwhm
+import oracle as O
 
 
 def test_encircled_power_of_a_uniform_disk_and_a_gaussian():
     r = np.linspace(0, 2, 2001)
-    P = encircled_power(r, np.where(r <= 1.0, 1.0, 0.0))
+    P = O.encircled_power(r, np.where(r <= 1.0, 1.0, 0.0))
     assert abs(P[-1] - math.pi) < 5e-3                       # pi * 1^2 (edge sampled at dr = 1e-3)
     s = 0.3
-    Pg = encircled_power(r, np.exp(-r ** 2 / (2 * s * s)))
+    Pg = O.encircled_power(r, np.exp(-r ** 2 / (2 * s * s)))
     exact = 2 * math.pi * s * s * (1 - np.exp(-r ** 2 / (2 * s * s)))
     assert np.max(np.abs(Pg - exact)) < 1e-6
 
@@ -21,7 +22,7 @@ def test_encircled_power_of_a_uniform_disk_and_a_gaussian():
 def test_fwhm_of_a_gaussian():
     xs = np.linspace(0, 2, 2001)                  # profile from the peak outwards
     s = 0.25
-    assert abs(fwhm(xs, np.exp(-xs ** 2 / (2 * s * s))) - 2 * math.sqrt(2 * math.log(2)) * s) < 1e-5
+    assert abs(O.fwhm(xs, np.exp(-xs ** 2 / (2 * s * s))) - 2 * math.sqrt(2 * math.log(2)) * s) < 1e-5
 
 
 class _AiryLens:
@@ -42,28 +43,24 @@ class _AiryLens:
         amp = np.where(v == 0, 1.0, 2 * j1(np.where(v == 0, 1.0, v)) / np.where(v == 0, 1.0, v))
         return self.P[l] * math.pi * self.a ** 2 / (lam * self.F) ** 2 * amp ** 2
 
-    def focal_plane(self, pts, n_phi_samples=128):
+    def focal_plane(self, pts):
         pts = np.asarray(pts, dtype=np.float64).reshape(-1, 2)
         rho = np.hypot(pts[:, 0], pts[:, 1])
         ex = np.array([np.sqrt(2 * self.intensity(l, rho)) for l in range(len(self.lams))], dtype=complex)
         return ex, np.zeros_like(ex), self.P.copy()
 
-    def order_bound(self, pts):
-        return 0.0
 
-
-def test_evaluate_lens_on_an_airy_spot():
+def test_evaluate_spot_on_an_airy_spot():
     """FWHM = 1.029 lambda F / (2 a); the power within 3 FWHM is the Airy
     encircled energy 1 - J0(v)^2 - J1(v)^2; transmittance = P / (I_inc A);
     Strehl = 1 for the ideal spot (Eq. 9: I lambda^2 F^2 / (P A))."""
     import pytest
     special = pytest.importorskip("scipy.special")
-    from paper_2501_07979_gb300.evaluate import evaluate_lens
     lams, a, F = (0.9, 1.0), 100.0, 200.0
     P = (3.0, 2.0)
     lens = _AiryLens(lams, a, F, P)
     inc = np.array([1.0 / (math.pi * a * a), 0.5 / (math.pi * a * a)])       # incident powers 1 and 0.5
-    res, xs, I = evaluate_lens(lens, a, F, inc, n_rad=96, n_ang=4)
+    res, xs, I = O.evaluate_spot(lens.focal_plane, lams, a, F, inc, n_line=4 * 96, n_rad=96, n_ang=4)
     for l, r in enumerate(res):
         lam = lams[l]
         assert abs(r["fwhm"] - 1.0290 * lam * F / (2 * a)) < 2e-3 * r["fwhm"]
@@ -72,4 +69,3 @@ def test_evaluate_lens_on_an_airy_spot():
         assert abs(r["relative_efficiency"] - ee) < 2e-3, (r["relative_efficiency"], ee)
         assert abs(r["transmittance"] - P[l] / (inc[l] * math.pi * a * a)) < 1e-12
         assert abs(r["strehl"] - 1.0) < 1e-9
-        assert r["order_bound"] == 0.0

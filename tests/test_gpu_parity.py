@@ -489,6 +489,17 @@ def test_lens_focal_plane_matches_bruteforce_oracle():
         a, b = O.focal_plane_bruteforce(s, f["geom"], f["mon"], pts3)
         rx3, ry3 = rx3 + a, ry3 + b
     assert _rel(ex3, rx3) < 1e-4 and _rel(ey3, ry3) < 1e-4
+    # the xz map (x, h grid through the axis) = the oracle's intensity of the brute-force field
+    from paper_2501_07979_gb300.evaluate import xz_map
+    xs, hs = [0.0, 0.6, 1.2], [-1.0, 0.8]
+    M = xz_map(lens, xs, hs, n_top=1.2, n_phi_samples=256)
+    grid = [(x, 0.0, h) for h in hs for x in xs]
+    gx = gy = 0
+    for s, r in zip(specs, rhos):
+        f = O.forward(s, r)
+        a, b = O.focal_plane_bruteforce(s, f["geom"], f["mon"], grid)
+        gx, gy = gx + a, gy + b
+    assert _rel(M, O.spot_intensity(gx, gy, 1.2).reshape(M.shape)) < 2e-4
 
 
 def test_topopt_on_a_zone_increases_focal_intensity():
@@ -523,24 +534,47 @@ def _oracle_evaluation(specs, rhos, lens_radius, xs, pts_disc, inc):
     brute-force focal-plane field (every site of every wedge copy, all
     azimuthal orders) and its transmitted power, with the same quadrature as
     the library's evaluation."""
-    from paper_2501_07979_gb300.evaluate import intensity, fwhm
     fw = [O.forward(s, r) for s, r in zip(specs, rhos)]
     line = [O.focal_plane_bruteforce(s, f["geom"], f["mon"], np.stack([xs, 0 * xs], 1)) for s, f in zip(specs, fw)]
     ex = sum(a for a, _ in line)
     ey = sum(b for _, b in line)
     pt = sum(O.transmitted_power(s, f["geom"], f["mon"]) for s, f in zip(specs, fw))
-    I_line = intensity(ex, ey)
+    I_line = O.spot_intensity(ex, ey)
     lam = np.asarray(specs[0].wavelengths)
     out = []
     for l, (rr, pts) in enumerate(pts_disc):
         d = [O.focal_plane_bruteforce(s, f["geom"], f["mon"], pts) for s, f in zip(specs, fw)]
-        Id = intensity(sum(a for a, _ in d)[l], sum(b for _, b in d)[l]).reshape(len(rr), -1)
+        Id = O.spot_intensity(sum(a for a, _ in d)[l], sum(b for _, b in d)[l]).reshape(len(rr), -1)
         p_disc = float(np.sum(Id.mean(axis=1) * 2 * math.pi * rr) * (rr[1] - rr[0]))
         area = math.pi * lens_radius ** 2
-        out.append({"fwhm": fwhm(xs, I_line[l]), "focusing_efficiency": p_disc / (inc[l] * area),
+        out.append({"fwhm": O.fwhm(xs, I_line[l]), "focusing_efficiency": p_disc / (inc[l] * area),
                     "relative_efficiency": p_disc / pt[l], "transmittance": pt[l] / (inc[l] * area),
                     "strehl": float(I_line[l, 0] * lam[l] ** 2 * specs[0].focal ** 2 / (pt[l] * area))})
     return out
+
+
+def test_field_intensity_and_encircled_power_match_oracle():
+    """The library's intensity of field samples and its encircled power
+    (trapezoid rule) against the oracle's on seeded random inputs."""
+    import ctypes
+    from paper_2501_07979_gb300 import _lib
+    from paper_2501_07979_gb300.evaluate import encircled_power
+    rng = np.random.default_rng(7)
+    nl, n = 3, 257
+    f = rng.standard_normal((2, nl, n, 2))
+    field = torch.tensor(f, dtype=torch.float64, device="cuda:0")
+    out = torch.empty((nl, n), dtype=torch.float64, device="cuda:0")
+    rc = _lib.lib().zda_field_intensity(ctypes.c_void_p(field.data_ptr()), nl, n, 1.5, ctypes.c_void_p(out.data_ptr()),
+                                        None)
+    assert rc == 0
+    ex, ey = f[0, ..., 0] + 1j * f[0, ..., 1], f[1, ..., 0] + 1j * f[1, ..., 1]
+    assert np.allclose(out.cpu().numpy(), O.spot_intensity(ex, ey, 1.5), rtol=1e-14, atol=0)
+    r = np.sort(rng.uniform(0, 3, 101))
+    I = rng.uniform(0, 1, (4, 101))
+    got = encircled_power(r, I)
+    want = np.array([O.encircled_power(r, I[q]) for q in range(4)])
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-14)
+    assert np.allclose(encircled_power(r, I[1]), want[1], rtol=1e-12, atol=1e-14)
 
 
 def test_lens_evaluation_matches_bruteforce_oracle():
