@@ -393,23 +393,26 @@ zda_status zda_lens_field_points(zda_lens *lens, const double *pts_dev, int n_pt
  * angles.  Fields from the lens-field transform of zda_lens_focal_plane with
  * n_phi_samples (>= 8) azimuthal samples; P_trans as there.
  * incident_host: n_lambda incident plane-wave intensities (n/2) abs(E)^2
- * (zda_zone_incident_intensity).  out_host (n_lambda x 8 doubles): per
+ * (zda_zone_incident_intensity).  scratch_dev: caller-owned device memory,
+ * 256-byte aligned, of at least zda_lens_evaluate_scratch_bytes bytes (the
+ * library allocates nothing).  out_host (n_lambda x 8 doubles): per
  * wavelength FWHM, I(0), FE, relative FE, transmittance P_trans / P_inc,
  * SR, disc power, P_trans.  line_dev (optional, n_lambda x n_line doubles,
- * device) receives the PSF line.  At most 8 wavelengths; device scratch
- * comes from cudaMallocAsync on `stream`, which the call synchronises. */
+ * device) receives the PSF line.  At most 8 wavelengths.  Synchronises
+ * `stream`. */
+zda_status zda_lens_evaluate_scratch_bytes(const zda_lens *lens, int n_line, int n_rad, int n_ang, size_t *bytes);
 zda_status zda_lens_evaluate(zda_lens *lens, double lens_radius, double focal, const double *incident_host,
                              double n_top, int n_line, double x_max, int n_rad, int n_ang, int n_phi_samples,
-                             double *out_host, double *line_dev, void *stream);
+                             void *scratch_dev, size_t scratch_bytes, double *out_host, double *line_dev,
+                             void *stream);
 
 /* Incident plane-wave intensity of a reference run: after zda_forward of a
  * zone whose layers and design are all the substrate (no interface, no
  * lens), the phi-mean u of the monitor's E_r phasor over the radii between
  * the r-PMLs, each row's Bloch phase e^{i m phi_j} removed, is half the
- * plane-wave amplitude; out_host (n_lambda doubles) = (n_sub/2) abs(2 u)^2,
- * n_sub = sqrt of the permittivity of the layer at k = 0.  Synchronises
- * `stream`. */
-zda_status zda_zone_incident_intensity(zda_zone *zone, double *out_host, void *stream);
+ * plane-wave amplitude; out_dev (n_lambda doubles, device) = (n_sub/2)
+ * abs(2 u)^2, n_sub = sqrt of the permittivity of the layer at k = 0. */
+zda_status zda_zone_incident_intensity(zda_zone *zone, double *out_dev, void *stream);
 
 /* Intensity (n_top/2)(abs(E_x)^2 + abs(E_y)^2) of field samples in the layout
  * of zda_lens_focal_plane / zda_lens_field_points (E_x of every wavelength

@@ -97,9 +97,10 @@ SIGNATURES = {
     "zda_lens_launch_count": (ctypes.c_longlong, [_vp]),
     "zda_lens_focal_plane": (_i, [_vp, _vp, _i, _i, _vp, _dp, _vp]),
     "zda_lens_field_points": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "zda_lens_evaluate_scratch_bytes": (_i, [_vp, _i, _i, _i, ctypes.POINTER(ctypes.c_size_t)]),
     "zda_lens_evaluate": (_i, [_vp, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_double, _i, ctypes.c_double, _i,
-                               _i, _i, _dp, _vp, _vp]),
-    "zda_zone_incident_intensity": (_i, [_vp, _dp, _vp]),
+                               _i, _i, _vp, ctypes.c_size_t, _dp, _vp, _vp]),
+    "zda_zone_incident_intensity": (_i, [_vp, _vp, _vp]),
     "zda_field_intensity": (_i, [_vp, _i, _i, ctypes.c_double, _vp, _vp]),
     "zda_encircled_power": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
     "zda_zone_order_bound": (_i, [_vp, _vp, _i, _vp, _i, _i, ctypes.POINTER(ctypes.c_double)]),

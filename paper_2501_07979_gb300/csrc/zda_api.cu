@@ -1886,83 +1886,96 @@ zda_status zda_lens_field_points(zda_lens *L, const double *pts_dev, int n_pts, 
     return lens_field(L, pts_dev, 3, n_pts, n_phi_samples, field_dev, nullptr, stream);
 }
 
-zda_status zda_lens_evaluate(zda_lens *L, double lens_radius, double focal, const double *incident_host, double n_top,
-                             int n_line, double x_max, int n_rad, int n_ang, int n_phi_samples, double *out_host,
-                             double *line_dev, void *stream)
+// device scratch of zda_lens_evaluate: line points, line field, disc points, disc field, FWHM, I(0),
+// results (256-byte aligned pieces)
+struct EvalScratch {
+    size_t lp, lf, dp, df, fw, i0, out, total;
+};
+
+static EvalScratch eval_scratch(int nl, int n_line, int n_rad, int n_ang)
 {
-    if (!L || !incident_host || !out_host || !(lens_radius > 0) || !(focal > 0) || !(n_top > 0) || n_line < 2 ||
-        !(x_max > 0) || n_rad < 1 || n_ang < 1 || n_phi_samples < 8)
-        return fail(ZDA_ERR_ARG, "bad argument");
-    if (!L->have_forward) return fail(ZDA_ERR_STATE, "the lens evaluation needs a preceding zda_lens_forward");
-    const int nl = L->nq / 2;
-    if (nl > ZDA_EVAL_MAX_LAMBDA) return fail(ZDA_ERR_ARG, "the lens evaluation takes at most 8 wavelengths");
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t nd = (size_t)nl * n_rad * n_ang;
+    EvalScratch e{};
     size_t off = 0;
     auto take = [&](size_t b) {
         const size_t o = off;
         off += (b + 255) & ~(size_t)255;
         return o;
     };
-    const size_t o_lp = take((size_t)2 * n_line * 8), o_lf = take((size_t)2 * nl * n_line * 16),
-                 o_dp = take(2 * nd * 8), o_df = take((size_t)2 * nl * nd * 16), o_fw = take((size_t)nl * 8),
-                 o_i0 = take((size_t)nl * 8), o_out = take((size_t)8 * nl * 8);
-    char *scr = nullptr;
-    CUDA_TRY(cudaMallocAsync((void **)&scr, off, s));
-    auto body = [&]() -> zda_status {
-        double *lp = (double *)(scr + o_lp), *dp = (double *)(scr + o_dp);
-        double *fw = (double *)(scr + o_fw), *i0 = (double *)(scr + o_i0), *out = (double *)(scr + o_out);
-        zda::launch_eval_line_points(lp, n_line, x_max, s);
-        std::vector<double> pt(nl, 0.0);
-        zda_status st = lens_field(L, lp, 2, n_line, n_phi_samples, (double *)(scr + o_lf), pt.data(), stream);
-        if (st) return st;
-        zda::launch_eval_fwhm((const double2 *)(scr + o_lf), nl, n_line, x_max, n_top, line_dev, fw, i0, s);
-        zda::launch_eval_disc_points(fw, nl, n_rad, n_ang, dp, s);
-        CUDA_TRY(cudaGetLastError());
-        st = lens_field(L, dp, 2, (int)nd, n_phi_samples, (double *)(scr + o_df), nullptr, stream);
-        if (st) return st;
-        zda::EvalScalars sc{};
-        const std::vector<double> &lam = L->zones[0]->lambda;
-        for (int l = 0; l < nl; ++l) {
-            sc.incident[l] = incident_host[l];
-            sc.p_trans[l] = pt[l];
-            sc.lambda[l] = lam[l];
-        }
-        sc.area = M_PI * lens_radius * lens_radius;
-        sc.focal = focal;
-        sc.n_top = n_top;
-        zda::launch_eval_finish((const double2 *)(scr + o_df), nl, n_rad, n_ang, fw, i0, sc, out, s);
-        CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaMemcpyAsync(out_host, out, (size_t)8 * nl * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        return ZDA_OK;
-    };
-    const zda_status st = body();
-    cudaFreeAsync(scr, s);
-    cudaStreamSynchronize(s);
-    return st;
+    const size_t nd = (size_t)nl * n_rad * n_ang;
+    e.lp = take((size_t)2 * n_line * 8);
+    e.lf = take((size_t)2 * nl * n_line * 16);
+    e.dp = take(2 * nd * 8);
+    e.df = take((size_t)2 * nl * nd * 16);
+    e.fw = take((size_t)nl * 8);
+    e.i0 = take((size_t)nl * 8);
+    e.out = take((size_t)8 * nl * 8);
+    e.total = off;
+    return e;
 }
 
-zda_status zda_zone_incident_intensity(zda_zone *z, double *out_host, void *stream)
+zda_status zda_lens_evaluate_scratch_bytes(const zda_lens *L, int n_line, int n_rad, int n_ang, size_t *bytes)
 {
-    if (!z || !out_host) return fail(ZDA_ERR_ARG, "null argument");
+    if (!L || !bytes || n_line < 2 || n_rad < 1 || n_ang < 1) return fail(ZDA_ERR_ARG, "bad argument");
+    *bytes = eval_scratch(L->nq / 2, n_line, n_rad, n_ang).total;
+    return ZDA_OK;
+}
+
+zda_status zda_lens_evaluate(zda_lens *L, double lens_radius, double focal, const double *incident_host, double n_top,
+                             int n_line, double x_max, int n_rad, int n_ang, int n_phi_samples, void *scratch_dev,
+                             size_t scratch_bytes, double *out_host, double *line_dev, void *stream)
+{
+    if (!L || !incident_host || !out_host || !scratch_dev || !(lens_radius > 0) || !(focal > 0) || !(n_top > 0) ||
+        n_line < 2 || !(x_max > 0) || n_rad < 1 || n_ang < 1 || n_phi_samples < 8)
+        return fail(ZDA_ERR_ARG, "bad argument");
+    if (!L->have_forward) return fail(ZDA_ERR_STATE, "the lens evaluation needs a preceding zda_lens_forward");
+    const int nl = L->nq / 2;
+    if (nl > ZDA_EVAL_MAX_LAMBDA) return fail(ZDA_ERR_ARG, "the lens evaluation takes at most 8 wavelengths");
+    const EvalScratch e = eval_scratch(nl, n_line, n_rad, n_ang);
+    if (scratch_bytes < e.total) return fail(ZDA_ERR_ARG, "scratch smaller than zda_lens_evaluate_scratch_bytes");
+    if ((uintptr_t)scratch_dev % 256) return fail(ZDA_ERR_ARG, "scratch must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *scr = static_cast<char *>(scratch_dev);
+    const size_t nd = (size_t)nl * n_rad * n_ang;
+    double *lp = (double *)(scr + e.lp), *dp = (double *)(scr + e.dp);
+    double *fw = (double *)(scr + e.fw), *i0 = (double *)(scr + e.i0), *out = (double *)(scr + e.out);
+    zda::launch_eval_line_points(lp, n_line, x_max, s);
+    std::vector<double> pt(nl, 0.0);
+    zda_status st = lens_field(L, lp, 2, n_line, n_phi_samples, (double *)(scr + e.lf), pt.data(), stream);
+    if (st) return st;
+    zda::launch_eval_fwhm((const double2 *)(scr + e.lf), nl, n_line, x_max, n_top, line_dev, fw, i0, s);
+    zda::launch_eval_disc_points(fw, nl, n_rad, n_ang, dp, s);
+    CUDA_TRY(cudaGetLastError());
+    st = lens_field(L, dp, 2, (int)nd, n_phi_samples, (double *)(scr + e.df), nullptr, stream);
+    if (st) return st;
+    zda::EvalScalars sc{};
+    const std::vector<double> &lam = L->zones[0]->lambda;
+    for (int l = 0; l < nl; ++l) {
+        sc.incident[l] = incident_host[l];
+        sc.p_trans[l] = pt[l];
+        sc.lambda[l] = lam[l];
+    }
+    sc.area = M_PI * lens_radius * lens_radius;
+    sc.focal = focal;
+    sc.n_top = n_top;
+    zda::launch_eval_finish((const double2 *)(scr + e.df), nl, n_rad, n_ang, fw, i0, sc, out, s);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out_host, out, (size_t)8 * nl * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return ZDA_OK;
+}
+
+zda_status zda_zone_incident_intensity(zda_zone *z, double *out_dev, void *stream)
+{
+    if (!z || !out_dev) return fail(ZDA_ERR_ARG, "null argument");
     if (!z->have_forward) return fail(ZDA_ERR_STATE, "the incident intensity needs a preceding zda_forward");
     const zda_zone_desc &d = z->d;
     const int nl = z->nq / 2;
-    if (nl > ZDA_EVAL_MAX_LAMBDA) return fail(ZDA_ERR_ARG, "at most 8 wavelengths");
     const int i0 = d.pml_r_in, i1 = d.n_r - d.pml_r_out;
     if (i1 <= i0) return fail(ZDA_ERR_ARG, "no radius between the r-PMLs");
-    cudaStream_t s = (cudaStream_t)stream;
-    double *dev = nullptr;
-    CUDA_TRY(cudaMallocAsync((void **)&dev, (size_t)nl * sizeof(double), s));
     const double dphi = d.n_fold == 0 ? 0.0 : 2.0 * M_PI / d.n_fold / d.n_phi;
     zda::launch_incident_intensity(P<float2>(*z, z->L.mon), nl, d.n_r, d.n_phi, i0, i1, dphi,
-                                   std::sqrt(layer_eps_at(d, 0)), dev, s);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dev, (size_t)nl * sizeof(double), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(dev, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(ZDA_ERR_CUDA, std::string("incident intensity: ") + cudaGetErrorString(e));
+                                   std::sqrt(layer_eps_at(d, 0)), out_dev, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
     return ZDA_OK;
 }
 

@@ -110,7 +110,7 @@ __global__ void k_eval_finish(const double2 *field, int nl, int n_rad, int n_ang
 __global__ void k_incident_intensity(const float2 *mon, int nl, int nr, int nphi, int i0, int i1, double dphi,
                                      double n_sub, double *out)
 {
-    const int l = threadIdx.x;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl) return;
     const size_t plane = (size_t)nr * nphi;
     const float2 *er = mon + (size_t)l * 2 * plane;        // [q][c][i][j], c = 0: E_r
@@ -185,7 +185,7 @@ void launch_eval_finish(const double2 *field, int nl, int n_rad, int n_ang, cons
 void launch_incident_intensity(const float2 *mon, int nl, int nr, int nphi, int i0, int i1, double dphi, double n_sub,
                                double *out, cudaStream_t s)
 {
-    k_incident_intensity<<<1, 32, 0, s>>>(mon, nl, nr, nphi, i0, i1, dphi, n_sub, out);
+    k_incident_intensity<<<(nl + 31) / 32, 32, 0, s>>>(mon, nl, nr, nphi, i0, i1, dphi, n_sub, out);
 }
 
 void launch_field_intensity(const double2 *field, int nl, int n, double n_top, double *out, cudaStream_t s)

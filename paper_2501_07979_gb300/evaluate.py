@@ -37,10 +37,9 @@ def incident_intensity(spec, device=0):
                        filter_radius=0.0, beta=0.0)
     z = Zone(ref, device=device)
     z.forward(torch.zeros((z.n_r_design, ref.n_phi), dtype=torch.float32, device=z.device))
-    nl = z.n_freq // 2
-    out = (ctypes.c_double * nl)()
-    check(_lib.lib().zda_zone_incident_intensity(z.handle, out, _stream()))
-    return np.array(out[:])
+    out = torch.empty(z.n_freq // 2, dtype=torch.float64, device=z.device)
+    check(_lib.lib().zda_zone_incident_intensity(z.handle, _dptr(out), _stream()))
+    return out.cpu().numpy()
 
 
 def evaluate_lens(lens, lens_radius, focal, incident, n_top=1.0, n_rad=48, n_ang=8, n_phi_samples=128):
@@ -54,12 +53,18 @@ def evaluate_lens(lens, lens_radius, focal, incident, n_top=1.0, n_rad=48, n_ang
     nl = lam.size
     n_line, x_max = 4 * n_rad, 4.0 * float(lam.max())
     inc = np.ascontiguousarray(np.asarray(incident, dtype=np.float64)[:nl])
-    line = torch.empty((nl, n_line), dtype=torch.float64, device=lens.zones[0].device)
+    dev = lens.zones[0].device
+    line = torch.empty((nl, n_line), dtype=torch.float64, device=dev)
+    nb = ctypes.c_size_t()
+    check(_lib.lib().zda_lens_evaluate_scratch_bytes(lens.handle, int(n_line), int(n_rad), int(n_ang),
+                                                     ctypes.byref(nb)))
+    scratch = torch.empty(nb.value + 256, dtype=torch.uint8, device=dev)
+    base = (scratch.data_ptr() + 255) // 256 * 256           # 256-byte aligned start
     out = (ctypes.c_double * (8 * nl))()
     check(_lib.lib().zda_lens_evaluate(lens.handle, float(lens_radius), float(focal),
                                        inc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(n_top), int(n_line),
-                                       x_max, int(n_rad), int(n_ang), int(n_phi_samples), out, _dptr(line),
-                                       _stream()))
+                                       x_max, int(n_rad), int(n_ang), int(n_phi_samples), ctypes.c_void_p(base),
+                                       nb.value, out, _dptr(line), _stream()))
     xs = np.linspace(0.0, x_max, n_line)              # the sample positions the library used
     o = np.array(out[:]).reshape(nl, 8)
     b_line = lens.order_bound(np.stack([xs, 0 * xs], 1))
