@@ -74,6 +74,20 @@ def parse():
 WORKLOAD = "zone"
 
 
+def whole_step(gcells_per_gpu, peak_gbs, kernels, per_step):
+    """The whole step against the HBM roofline: frac_96B = Gcell-upd/s x 96 B
+    (one read and one write of the six field components, the one-step
+    minimum) / peak; frac_step_bytes = the step kernels' algorithmic bytes
+    per step (the DFT flush's per launch / 32) / their summed event time per
+    step / peak.  kernels: (name, bytes per launch, ms per launch);
+    per_step: name -> ms per step."""
+    step_bytes = sum(b / 32 if nm == "k_dft_flush" else b for nm, b, _ in kernels)
+    step_ms = sum(per_step.values())
+    return {"frac_96B": gcells_per_gpu * 96.0 / peak_gbs,
+            "algorithmic_bytes_per_step": step_bytes, "kernel_ms_per_step": step_ms,
+            "frac_step_bytes": step_bytes / (step_ms * 1e-3) / 1e9 / peak_gbs}
+
+
 def kernel_choice(a):
     """(variant, tile_phi, i_ranges) of --kernel, or None for the library's default / the tuner."""
     k = {"split": (0, 16, 0), "split1": (2, 2, 0), "fused2": (1, 2, 0), "fused4": (1, 4, 0),
@@ -416,6 +430,7 @@ def run_ours(a):
     ach_main = b_main / (main_ms * 1e-3) / 1e9
     others = [{"kernel": nm, "achieved": b / (t * 1e-3) / 1e9, "frac": b / (t * 1e-3) / 1e9 / peak,
                "avg_launch_ms": t, "algorithmic_bytes_per_launch": b} for nm, b, t in kernels[1:]]
+    whole = whole_step(value / world, peak, kernels, per_step)
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
@@ -431,6 +446,7 @@ def run_ours(a):
                          "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": b_main, "avg_launch_ms": main_ms,
                          "sampled_launches": n_timed, "other_kernels": others},
+            "whole_step": whole,
             "step_kernel": {"variant": {0: "split, two z-cells per thread", 1: "fused, streaming along r",
                                         2: "split, one z-cell per thread",
                                         3: "fused, TMA-staged tiles streaming along r",

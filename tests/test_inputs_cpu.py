@@ -23,3 +23,21 @@ def test_smoothed_density_is_seeded_and_in_range():
     assert a.min() == 0.0 and a.max() == 1.0
     d = smoothed_rho(20, 12, 5, mode="binary")
     assert set(np.unique(d)) <= {0.0, 1.0}
+
+
+def test_bench_whole_step_fractions():
+    """bench.py's whole-step roofline figures: 96 B per cell-update against
+    the peak, and the step kernels' bytes over their time (the DFT flush
+    counted once per 32 steps)."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(os.path.dirname(__file__), "..", "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    kernels = [("k_tile_e", 1.2e9, 0.2), ("k_update_h_pair", 1.2e9, 0.2), ("k_dft_flush", 3.2e9, 0.4)]
+    per_step = {"k_tile_e": 0.2, "k_update_h_pair": 0.2, "k_dft_flush": 0.4 / 32}
+    w = bench.whole_step(40.0, 6000.0, kernels, per_step)
+    assert abs(w["frac_96B"] - 40.0 * 96 / 6000.0) < 1e-15
+    assert abs(w["algorithmic_bytes_per_step"] - (2.4e9 + 1e8)) < 1.0
+    assert abs(w["kernel_ms_per_step"] - 0.4125) < 1e-12
+    assert abs(w["frac_step_bytes"] - 2.5e9 / 0.4125e-3 / 1e9 / 6000.0) < 1e-12
