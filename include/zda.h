@@ -273,8 +273,9 @@ zda_status zda_zone_time_steps(zda_zone *zone, int steps, double *ms_out_host, v
  * (default 4194304; variants 3 and 4 also after one second), sets an error
  * word and lets the kernel finish, and the call then returns
  * ZDA_ERR_TIMEOUT (zda_forward, zda_adjoint and zda_iteration synchronise
- * their stream to read it).  inject_timeout != 0 is for tests of that path
- * (variant 1): each radius also waits on a barrier that nothing completes. */
+ * their stream to read it).  inject_timeout != 0 is for tests of that path:
+ * variant 1 also waits, per radius, on a barrier that nothing completes;
+ * variants 3, 4 and 5 once per thread block before their first radius. */
 zda_status zda_zone_set_wait_limit(zda_zone *zone, int polls, int inject_timeout);
 
 /* Kernel timing with CUDA events recorded on the launching stream: with

@@ -755,6 +755,7 @@ static zda::TileParams tile_params(zda_zone &z, const zda::StepParams &p, int pa
     }
     t.err = P<int>(z, z.L.status) + 1;
     t.wait_limit = z.wait_limit;
+    t.inject_timeout = z.inject_timeout;
     return t;
 }
 
@@ -932,6 +933,7 @@ static zda_status time_loop(zda_zone &z, zda::StepParams &p, cudaStream_t s)
         }
         etp.err = P<int>(z, z.L.status) + 1;
         etp.wait_limit = z.wait_limit;
+        etp.inject_timeout = z.inject_timeout;
         enrc = tile_e_rchunks(z);
     }
     for (int n = 0; n < z.d.n_steps; ++n) {

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(SG<TJ, NS>::NT, MINB)
 {
     using G = SG<TJ, NS>;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT];
+    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT + 1];   // + one that nothing completes (tests)
     __shared__ int abort_s;                                   // the error word was already set at entry
     const uint32_t raw_s = s_addr(smem_raw);
     const uint32_t base_s = (raw_s + 127u) & ~127u;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(SG<TJ, NS>::NT, MINB)
     auto wait_group = [&](int r) { return t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err); };
 
     if (tid == 0) {
-        for (int s = 0; s < G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
+        for (int s = 0; s <= G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
         // an earlier launch of this run gave up waiting: do nothing (the host reports the error)
         abort_s = *(volatile int *)tp.err;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -373,7 +373,8 @@ __global__ void __launch_bounds__(SG<TJ, NS>::NT, MINB)
     bool failed = false;
     if (tid == 0) {
         for (int r = r0 - 1; r <= last_issued; ++r) issue(r);
-        failed = !wait_group(r0 - 1);                         // E^n(r0): read by H(r0)
+        if (tp.inject_timeout) failed = !t_mbar_wait(s_addr(&bar_mem[G::NSLOT]), 0, tp.wait_limit, tp.err);
+        if (!failed) failed = !wait_group(r0 - 1);            // E^n(r0): read by H(r0)
         if (!failed && r0 < ie) failed = !wait_group(r0);     // E^n(r0+1), H(r0)
     }
     failed = __syncthreads_or(failed);
@@ -592,7 +593,7 @@ __global__ void __launch_bounds__(SE<TJ, NS>::NT, MINB)
 {
     using G = SE<TJ, NS>;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT];
+    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT + 1];   // + one that nothing completes (tests)
     __shared__ int abort_s;
     const uint32_t raw_s = s_addr(smem_raw);
     const uint32_t base_s = (raw_s + 127u) & ~127u;
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(SE<TJ, NS>::NT, MINB)
     auto wait_group = [&](int r) { return t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err); };
 
     if (tid == 0) {
-        for (int s = 0; s < G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
+        for (int s = 0; s <= G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
         abort_s = *(volatile int *)tp.err;                    // an earlier launch gave up waiting: do nothing
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -643,7 +644,8 @@ __global__ void __launch_bounds__(SE<TJ, NS>::NT, MINB)
     bool failed = false;
     if (tid == 0) {
         for (int r = ib - 1; r <= last_issued; ++r) issue(r);
-        failed = !wait_group(ib - 1);
+        if (tp.inject_timeout) failed = !t_mbar_wait(s_addr(&bar_mem[G::NSLOT]), 0, tp.wait_limit, tp.err);
+        if (!failed) failed = !wait_group(ib - 1);
         if (!failed && ib < ie) failed = !wait_group(ib);
     }
     failed = __syncthreads_or(failed);
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(SH<TJ, NS>::NT, MINB)
 {
     using G = SH<TJ, NS>;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT];
+    __shared__ __align__(8) uint64_t bar_mem[G::NSLOT + 1];   // + one that nothing completes (tests)
     __shared__ int abort_s;
     const uint32_t raw_s = s_addr(smem_raw);
     const uint32_t base_s = (raw_s + 127u) & ~127u;
@@ -854,7 +856,7 @@ __global__ void __launch_bounds__(SH<TJ, NS>::NT, MINB)
     auto wait_group = [&](int r) { return t_mbar_wait(s_addr(&bar_mem[slot_of(r)]), parity_of(r), tp.wait_limit, tp.err); };
 
     if (tid == 0) {
-        for (int s = 0; s < G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
+        for (int s = 0; s <= G::NSLOT; ++s) t_mbar_init(s_addr(&bar_mem[s]), 1);
         abort_s = *(volatile int *)tp.err;                    // an earlier launch gave up waiting: do nothing
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -866,7 +868,8 @@ __global__ void __launch_bounds__(SH<TJ, NS>::NT, MINB)
     bool failed = false;
     if (tid == 0) {
         for (int r = ib; r <= last_issued; ++r) issue(r);
-        failed = !wait_group(ib);
+        if (tp.inject_timeout) failed = !t_mbar_wait(s_addr(&bar_mem[G::NSLOT]), 0, tp.wait_limit, tp.err);
+        if (!failed) failed = !wait_group(ib);
         if (!failed) failed = !wait_group(ib + 1);            // ib + 1 <= ie always
     }
     failed = __syncthreads_or(failed);

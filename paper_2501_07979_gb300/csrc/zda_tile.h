@@ -32,6 +32,7 @@ struct TileParams {
     float2 *psH_out[4];           // ... at n+1/2 (the other set)
     int *err;                     // error word: a bounded wait gave up
     int wait_limit;               // polls of the tile's mbarrier before giving up
+    int inject_timeout;           // tests: thread 0 first waits on a barrier that nothing completes
 };
 
 // tile shapes compiled: tj in {4, 8, 16} phi rows, 32 z-cells; each thread block streams

@@ -358,13 +358,15 @@ def test_adjoint_before_forward_is_a_state_error():
         z.adjoint(np.ones(z.n_freq, complex))
 
 
-def test_fused_wait_timeout_is_reported_and_context_survives():
-    """The fused step's barrier waits are bounded: with a barrier that nothing
-    completes and a short limit the call returns ZDA_ERR_TIMEOUT instead of
-    hanging, and the same zone then runs normally."""
+@pytest.mark.parametrize("kernel,name", [("fused2", "tiny"), ("tile4", "ragged_tile"), ("etile16", "ragged_tile"),
+                                         ("htile16", "ragged_tile")])
+def test_fused_wait_timeout_is_reported_and_context_survives(kernel, name):
+    """The fused and tiled steps' barrier waits are bounded: with a barrier
+    that nothing completes and a short limit the call returns ZDA_ERR_TIMEOUT
+    instead of hanging, and the same zone then runs normally."""
     from paper_2501_07979_gb300 import ZdaError
-    spec = RAGGED["tiny"].replace(n_steps=3)
-    z = _zone(spec, "fused2")
+    spec = RAGGED[name].replace(n_steps=3)
+    z = _zone(spec, kernel)
     r = _dev(rho_for(spec, 1))
     z.set_wait_limit(200, inject_timeout=True)
     with pytest.raises(ZdaError, match="ZDA_ERR_TIMEOUT"):
