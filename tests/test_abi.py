@@ -149,3 +149,17 @@ def test_filter_radius_beyond_the_tap_limit_is_refused(libpath):
     assert b"taps" in L.zda_last_error()
     neg = zone_tiny(pml_r_in=-2)
     assert L.zda_filter_project_noalloc(ctypes.byref(make_desc(neg)), x, x, None) == _lib.ERR_ARG
+
+
+def test_evaluation_calls_check_their_arguments_before_any_device_work(libpath):
+    from paper_2501_07979_gb300 import _lib
+    L = _lib.load(libpath)
+    out = (ctypes.c_double * 16)()
+    inc = (ctypes.c_double * 2)(1.0, 1.0)
+    nb = ctypes.c_size_t()
+    assert L.zda_lens_evaluate_scratch_bytes(None, 8, 4, 4, ctypes.byref(nb)) == _lib.ERR_ARG
+    assert L.zda_lens_evaluate(None, 10.0, 20.0, inc, 1.0, 8, 4.0, 4, 4, 64, None, 0, out, None, None) == _lib.ERR_ARG
+    assert L.zda_zone_incident_intensity(None, None, None) == _lib.ERR_ARG
+    assert L.zda_field_intensity(None, 1, 1, 1.0, None, None) == _lib.ERR_ARG
+    assert L.zda_encircled_power(None, None, 1, 0, None, None) == _lib.ERR_ARG
+    assert b"bad argument" in L.zda_last_error() or b"null" in L.zda_last_error()
