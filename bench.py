@@ -333,7 +333,8 @@ def run_ours(a):
         zone.set_kernel(*kern)
     elif a.kernel == "tuned":
         from paper_2501_07979_gb300.autotune import tune_zone
-        tune_zone(zone, cache_path=os.path.join(ROOT, "gpurun_out", "tiles.json"), use_cache=False)
+        import tempfile
+        tune_zone(zone, cache_path=os.path.join(tempfile.gettempdir(), "zda_bench_tiles.json"), use_cache=False)
     if a.radial_pml:
         zone.set_radial_pml(a.radial_pml)
     variant, tile_phi, i_ranges = zone.get_kernel()
