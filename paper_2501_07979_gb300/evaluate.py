@@ -52,7 +52,9 @@ def evaluate_lens(lens, lens_radius, focal, incident, n_top=1.0, n_rad=48, n_ang
     lam = np.asarray(lens.zones[0].spec.wavelengths, dtype=np.float64)
     nl = lam.size
     n_line, x_max = 4 * n_rad, 4.0 * float(lam.max())
-    inc = np.ascontiguousarray(np.asarray(incident, dtype=np.float64)[:nl])
+    inc = np.ascontiguousarray(np.asarray(incident, dtype=np.float64).ravel()[:nl])
+    if inc.size != nl:
+        raise ValueError("incident: one intensity per wavelength (%d) expected" % nl)
     dev = lens.zones[0].device
     line = torch.empty((nl, n_line), dtype=torch.float64, device=dev)
     nb = ctypes.c_size_t()
