@@ -41,3 +41,21 @@ def test_bench_whole_step_fractions():
     assert abs(w["algorithmic_bytes_per_step"] - (2.4e9 + 1e8)) < 1.0
     assert abs(w["kernel_ms_per_step"] - 0.4125) < 1e-12
     assert abs(w["frac_step_bytes"] - 2.5e9 / 0.4125e-3 / 1e9 / 6000.0) < 1e-12
+
+
+def test_tuner_candidates_follow_the_kernels_constraints():
+    """The tile kernels (variants 3-5) are offered only where they run
+    (annular zone, even n_z and z-PML); the split step's block shapes never
+    exceed twice the phi cells; the wide zone gets every family."""
+    from paper_2501_07979_gb300.autotune import candidates
+    from zda_inputs import zone_cfg2, zone_tiny
+    wide = candidates(zone_cfg2(n_steps=10))
+    fams = {v for v, _, _ in wide}
+    assert fams == {0, 1, 2, 3, 4, 5}
+    assert {(4, 16, 0), (5, 16, 0), (3, 4, 0)} <= set(wide)
+    axis = candidates(zone_tiny(r_lo=0.0, n_fold=0, n_phi=1, pml_r_in=0))
+    assert all(v in (0, 2) for v, _, _ in axis)
+    odd = candidates(zone_tiny(n_z=45))
+    assert all(v not in (3, 4, 5) for v, _, _ in odd)
+    narrow = candidates(zone_tiny(n_phi=3))
+    assert all(t <= 6 for v, t, _ in narrow if v in (0, 3, 4, 5))
