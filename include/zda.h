@@ -224,7 +224,9 @@ long long zda_zone_launch_count(const zda_zone *zone);
  * in {8, 16, 32} phi rows x 32 z-cells whose H and E values are staged into
  * shared memory by TMA tensor copies several radii ahead, each thread block
  * streaming over one of i_ranges radius ranges (0 = radius ranges of about
- * 21 radii).  variant 1 (annular zones, n_z <= 256): one fused launch per
+ * 21 radii).  variant 5 (as variant 4): both halves of the split step on
+ * those tiles (the H update stages E^n of two radii and H^{n-1/2}).
+ * variant 1 (annular zones, n_z <= 256): one fused launch per
  * step (E and H updated together, ping-pong field buffers, streaming along
  * r; tile_phi in {2, 4} phi rows per thread block, i_ranges radius ranges
  * per phi tile, 0 = as many as fit in one wave).  variant 3 (annular zones,
