@@ -69,3 +69,18 @@ def test_evaluate_spot_on_an_airy_spot():
         assert abs(r["relative_efficiency"] - ee) < 2e-3, (r["relative_efficiency"], ee)
         assert abs(r["transmittance"] - P[l] / (inc[l] * math.pi * a * a)) < 1e-12
         assert abs(r["strehl"] - 1.0) < 1e-9
+
+
+def test_fwhm_edge_cases_and_disc_samples():
+    """A profile that never falls below half has no FWHM (NaN, as the
+    library returns); the crossing is interpolated between the samples that
+    bracket it; the disc samples sit at (k + 1/2) 3 w / n_rad, n_ang angles."""
+    xs = np.linspace(0, 1, 11)
+    assert math.isnan(O.fwhm(xs, np.ones(11)))
+    I = np.array([1.0, 0.8, 0.4, 0.1])
+    # half = 0.5 between x = 1 (0.8) and x = 2 (0.4): 1 + 0.3 / 0.4 = 1.75
+    assert abs(O.fwhm(np.arange(4.0), I) - 3.5) < 1e-15
+    rr, pts = O.disc_points(0.2, 4, 3)
+    assert np.allclose(rr, (np.arange(4) + 0.5) * 0.6 / 4)
+    assert pts.shape == (12, 2)
+    assert np.allclose(np.hypot(pts[:, 0], pts[:, 1]).reshape(4, 3), rr[:, None])
